@@ -1,0 +1,221 @@
+"""Seeded synthetic workloads for the GSW-MTP focus-array loop.
+
+This module only draws inputs: focus positions, target intensities, the
+pupil amplitude profile and an initial phase.  It holds none of the method's
+arithmetic (no DFT rows, no propagation, no weighting), so that the CUDA
+library's tests and the FP64 oracle can be fed the very same arrays.
+
+The paper measures on no public dataset; every workload here is synthetic and
+follows the geometry of its simulations (phase-only SLM pupil, Fourier lens,
+foci at arbitrary positions with chosen relative intensities; Table 1 and the
+"Results and discussion" section of arXiv 2206.12661).  Shared optics of all
+workloads: pixel pitch 8 um, wavelength 532 nm, focal length 200 mm.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PITCH = 8e-6
+WAVELENGTH = 532e-9
+FOCAL_LENGTH = 0.2
+
+
+@dataclass
+class Workload:
+    """One hologram problem: pupil size, optics, foci, targets, A and phi0."""
+    name: str
+    nx: int
+    ny: int
+    pitch_x: float
+    pitch_y: float
+    wavelength: float
+    focal_length: float
+    focus_xy: np.ndarray          # [K][2] float64, metres in the focal plane
+    target: np.ndarray            # [K] float32, relative target intensities
+    amplitude: np.ndarray         # [ny][nx] float32
+    phi0: np.ndarray              # [ny][nx] float32, radians in [-pi, pi)
+    n_iter: int
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_foci(self) -> int:
+        return int(self.focus_xy.shape[0])
+
+
+def spot_size(n: int, pitch: float = PITCH, wavelength: float = WAVELENGTH,
+              focal_length: float = FOCAL_LENGTH) -> float:
+    """Diffraction-limited spot size lambda*f/(N*p) of an N-pixel aperture."""
+    return wavelength * focal_length / (n * pitch)
+
+
+def gaussian_amplitude(nx: int, ny: int, pitch_x: float = PITCH, pitch_y: float = PITCH,
+                       waist_frac: float = 0.4) -> np.ndarray:
+    """Gaussian beam profile exp(-(u^2/wx^2 + v^2/wy^2)), waist = waist_frac * aperture."""
+    u = (np.arange(nx) - (nx - 1) / 2.0) * pitch_x
+    v = (np.arange(ny) - (ny - 1) / 2.0) * pitch_y
+    wx = waist_frac * nx * pitch_x
+    wy = waist_frac * ny * pitch_y
+    a = np.exp(-(v[:, None] ** 2 / wy ** 2 + u[None, :] ** 2 / wx ** 2))
+    return a.astype(np.float32)
+
+
+def uniform_phase(rng: np.random.Generator, nx: int, ny: int) -> np.ndarray:
+    return rng.uniform(-np.pi, np.pi, size=(ny, nx)).astype(np.float32)
+
+
+def jittered_grid(rng: np.random.Generator, cols: int, rows: int, pitch_x: float,
+                  pitch_y: float, jitter: float = 0.3, count: int | None = None) -> np.ndarray:
+    """cols x rows grid centred on the optical axis, each focus moved by U(+-jitter*pitch)."""
+    gx = (np.arange(cols) - (cols - 1) / 2.0) * pitch_x
+    gy = (np.arange(rows) - (rows - 1) / 2.0) * pitch_y
+    xx, yy = np.meshgrid(gx, gy)
+    pts = np.stack([xx.ravel(), yy.ravel()], axis=1)
+    pts[:, 0] += rng.uniform(-jitter, jitter, size=pts.shape[0]) * pitch_x
+    pts[:, 1] += rng.uniform(-jitter, jitter, size=pts.shape[0]) * pitch_y
+    if count is not None and count < pts.shape[0]:
+        pts = pts[np.sort(rng.choice(pts.shape[0], size=count, replace=False))]
+    return pts.astype(np.float64)
+
+
+def poisson_disk(rng: np.random.Generator, width: float, height: float, min_dist: float,
+                 tries: int = 30) -> np.ndarray:
+    """Bridson's Poisson-disk sampling of a width x height box centred at the origin."""
+    cell = min_dist / math.sqrt(2.0)
+    gw = int(math.ceil(width / cell))
+    gh = int(math.ceil(height / cell))
+    grid = -np.ones((gh, gw), dtype=np.int64)
+    pts: list[tuple[float, float]] = []
+    active: list[int] = []
+
+    def put(p):
+        pts.append(p)
+        idx = len(pts) - 1
+        grid[int(p[1] / cell), int(p[0] / cell)] = idx
+        active.append(idx)
+
+    put((rng.uniform(0, width), rng.uniform(0, height)))
+    r2 = min_dist * min_dist
+    while active:
+        j = int(rng.integers(len(active)))
+        base = pts[active[j]]
+        placed = False
+        for _ in range(tries):
+            ang = rng.uniform(0, 2 * math.pi)
+            rad = rng.uniform(min_dist, 2 * min_dist)
+            p = (base[0] + rad * math.cos(ang), base[1] + rad * math.sin(ang))
+            if not (0 <= p[0] < width and 0 <= p[1] < height):
+                continue
+            cx, cy = int(p[0] / cell), int(p[1] / cell)
+            ok = True
+            for yy in range(max(cy - 2, 0), min(cy + 3, gh)):
+                for xx in range(max(cx - 2, 0), min(cx + 3, gw)):
+                    q = grid[yy, xx]
+                    if q >= 0:
+                        dx = pts[q][0] - p[0]
+                        dy = pts[q][1] - p[1]
+                        if dx * dx + dy * dy < r2:
+                            ok = False
+                            break
+                if not ok:
+                    break
+            if ok:
+                put(p)
+                placed = True
+                break
+        if not placed:
+            active[j] = active[-1]
+            active.pop()
+    arr = np.asarray(pts, dtype=np.float64)
+    arr[:, 0] -= width / 2.0
+    arr[:, 1] -= height / 2.0
+    return arr
+
+
+def _make(name, nx, ny, foci, target, rng, n_iter, meta, pitch=PITCH):
+    return Workload(name=name, nx=nx, ny=ny, pitch_x=pitch, pitch_y=pitch,
+                    wavelength=WAVELENGTH, focal_length=FOCAL_LENGTH,
+                    focus_xy=np.ascontiguousarray(foci, dtype=np.float64),
+                    target=np.ascontiguousarray(target, dtype=np.float32),
+                    amplitude=gaussian_amplitude(nx, ny, pitch, pitch),
+                    phi0=uniform_phase(rng, nx, ny), n_iter=n_iter, meta=meta)
+
+
+def grid_workload(n: int = 256, cols: int = 10, rows: int = 10, n_iter: int = 50, seed: int = 1,
+                  uniform_targets: bool = True, name: str | None = None) -> Workload:
+    """Pupil n x n, cols x rows jittered grid at pitch 3 spots, Gaussian A (256^2 / 10x10 / 50 it)."""
+    rng = np.random.default_rng(seed)
+    s = spot_size(n)
+    foci = jittered_grid(rng, cols, rows, 3 * s, 3 * s)
+    k = foci.shape[0]
+    t = np.ones(k) if uniform_targets else rng.uniform(0.5, 1.0, k)
+    return _make(name or f"grid{n}x{n}_{k}foci", n, n, foci, t, rng, n_iter,
+                 {"layout": "jittered grid", "pitch_spots": 3, "jitter": 0.3, "seed": seed})
+
+
+def poisson_workload(n: int = 1024, n_foci: int = 1000, roi: float = 2.0e-3, n_iter: int = 100,
+                     seed: int = 2, name: str | None = None) -> Workload:
+    """Pupil n x n, n_foci Poisson-disk foci (min spacing 3 spots) in a roi x roi box, t ~ U[0.5,1].
+
+    A 400 um square cannot hold 1000 foci at a 3-spot (39 um) spacing; the
+    ROI is widened to 2.0 mm, which keeps the pupil, the focus count and the
+    spacing (the cost of the loop does not depend on where the foci sit).
+    """
+    rng = np.random.default_rng(seed)
+    s = spot_size(n)
+    pts = poisson_disk(rng, roi, roi, 3 * s)
+    if pts.shape[0] < n_foci:
+        raise ValueError(f"ROI {roi} m holds only {pts.shape[0]} foci at spacing {3 * s}")
+    pts = pts[np.sort(rng.choice(pts.shape[0], size=n_foci, replace=False))]
+    t = rng.uniform(0.5, 1.0, n_foci)
+    return _make(name or f"poisson{n}x{n}_{n_foci}foci", n, n, pts, t, rng, n_iter,
+                 {"layout": "Poisson disk", "roi_m": roi, "min_spacing_spots": 3, "seed": seed})
+
+
+def rect_workload(nx: int = 1920, ny: int = 1152, cols: int = 50, rows: int = 50, n_iter: int = 50,
+                  seed: int = 3, name: str | None = None) -> Workload:
+    """Pupil nx x ny, cols x rows grid at isotropic pitch 3*max(sx, sy), jitter 0.3, t = 1."""
+    rng = np.random.default_rng(seed)
+    pitch = 3 * max(spot_size(nx), spot_size(ny))
+    foci = jittered_grid(rng, cols, rows, pitch, pitch)
+    t = np.ones(foci.shape[0])
+    w = _make(name or f"rect{nx}x{ny}_{foci.shape[0]}foci", nx, ny, foci, t, rng, n_iter,
+              {"layout": "jittered grid", "pitch_m": pitch, "seed": seed})
+    return w
+
+
+def batch_workloads(count: int = 256, sizes=(512, 768, 1024), k_min: int = 16, k_max: int = 4096,
+                    n_iter: int = 50, seed: int = 5) -> list[Workload]:
+    """Uneven batch: N drawn from sizes, K log-uniform in [k_min, k_max], jittered grid foci."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(sizes[int(rng.integers(len(sizes)))])
+        k = int(round(math.exp(rng.uniform(math.log(k_min), math.log(k_max)))))
+        side = int(math.ceil(math.sqrt(k)))
+        s = spot_size(n)
+        foci = jittered_grid(rng, side, side, 3 * s, 3 * s, count=k)
+        t = rng.uniform(0.5, 1.0, k)
+        out.append(_make(f"batch{i}_{n}x{n}_{k}foci", n, n, foci, t, rng, n_iter,
+                         {"layout": "jittered grid", "seed": seed, "index": i}))
+    return out
+
+
+NAMED = {
+    "pupil256_grid100_uniform": lambda: grid_workload(256, 10, 10, n_iter=50, seed=1,
+                                                      name="pupil256_grid100_uniform"),
+    "pupil1024_poisson1000": lambda: poisson_workload(1024, 1000, n_iter=100, seed=2,
+                                                      name="pupil1024_poisson1000"),
+    "pupil1920x1152_grid2500": lambda: rect_workload(1920, 1152, 50, 50, n_iter=50, seed=3,
+                                                     name="pupil1920x1152_grid2500"),
+    "pupil1024_grid400_adam": lambda: grid_workload(1024, 20, 20, n_iter=200, seed=4,
+                                                    uniform_targets=False,
+                                                    name="pupil1024_grid400_adam"),
+}
+
+
+def named(name: str) -> Workload:
+    """A single-hologram workload by name (see NAMED)."""
+    return NAMED[name]()

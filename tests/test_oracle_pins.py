@@ -1,0 +1,362 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself: each one checks it against an
+FFT, a brute-force sum, a closed form, an energy identity, an invariance, an
+independent restatement of a different algorithm, finite differences or a
+published test vector.  A dropped term, a sign flip, a transposed operand or
+a wrong index in the oracle fails at least one of them.
+"""
+import cmath
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+LAM, F, P = 532e-9, 0.2, 8e-6
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def rand_field(rng, ny, nx):
+    return rng.uniform(0.2, 1.0, (ny, nx)) * np.exp(1j * rng.uniform(-np.pi, np.pi, (ny, nx)))
+
+
+# ------------------------------------------------ Eq. 2 vs zero-padded FFT
+@pytest.mark.parametrize("centred", [False, True])
+def test_forward_equals_zero_padded_fft(centred):
+    """Unit optics (p = 1, lambda f = M), integer foci: MTP = fft2(zero-pad(E, M)) at the foci."""
+    rng = np.random.default_rng(11)
+    ny, nx, M = 20, 24, 64
+    E = rand_field(rng, ny, nx)
+    qx = rng.integers(0, M, 37)
+    qy = rng.integers(0, M, 37)
+    qx[:3] = [0, M - 1, 5]
+    qy[:3] = [0, M - 1, 5]
+    if centred:
+        ux, uy = O.pupil_coords(nx, 1.0), O.pupil_coords(ny, 1.0)
+    else:
+        ux, uy = np.arange(nx, dtype=float), np.arange(ny, dtype=float)
+    fx = O.dft_rows(qx.astype(float), ux, M)
+    fy = O.dft_rows(qy.astype(float), uy, M)
+    theta = O.forward(E, fx, fy)
+    pad = np.zeros((M, M), complex)
+    pad[:ny, :nx] = E
+    expect = np.fft.fft2(pad)[qy, qx]
+    if centred:  # a shifted origin multiplies each focus by a known phase factor
+        cx, cy = (nx - 1) / 2.0, (ny - 1) / 2.0
+        expect = expect * np.exp(2j * np.pi * (qx * cx + qy * cy) / M)
+    assert rel(theta, expect) < 1e-12
+
+
+def test_adjoint_equals_inverse_fft():
+    """Adjoint at integer foci = M^2 ifft2 of the foci placed on the M x M grid, cropped."""
+    rng = np.random.default_rng(12)
+    ny, nx, M = 18, 22, 32
+    K = 29
+    qx = rng.integers(0, M, K)
+    qy = rng.integers(0, M, K)
+    qx[0], qy[0] = qx[1], qy[1]  # a duplicated focus adds
+    theta = rng.normal(size=K) + 1j * rng.normal(size=K)
+    fx = O.dft_rows(qx.astype(float), np.arange(nx, dtype=float), M)
+    fy = O.dft_rows(qy.astype(float), np.arange(ny, dtype=float), M)
+    got = O.adjoint(theta, fx, fy)
+    grid = np.zeros((M, M), complex)
+    np.add.at(grid, (qy, qx), theta)
+    expect = (M * M * np.fft.ifft2(grid))[:ny, :nx]
+    assert got.shape == (ny, nx)
+    assert rel(got, expect) < 1e-12
+
+
+# ------------------------------------------------ brute force on tiny pupils
+def test_brute_force_tiny():
+    """Direct non-separated sum of exp(-i 2 pi (x u + y v)/(lambda f)) over the pupil."""
+    rng = np.random.default_rng(13)
+    ny, nx, K = 4, 5, 3
+    E = rand_field(rng, ny, nx)
+    xy = rng.uniform(-3e-3, 3e-3, (K, 2))
+    fx, fy = O.plan_matrices(nx, ny, P, 1.5 * P, LAM, F, xy)
+    theta = O.forward(E, fx, fy)
+    c = rng.normal(size=K) + 1j * rng.normal(size=K)
+    back = O.adjoint(c, fx, fy)
+    for k in range(K):
+        s = 0j
+        for n in range(ny):
+            for m in range(nx):
+                u = (m - (nx - 1) / 2) * P
+                v = (n - (ny - 1) / 2) * 1.5 * P
+                s += E[n, m] * cmath.exp(-2j * math.pi * (xy[k, 0] * u + xy[k, 1] * v) / (LAM * F))
+        assert abs(theta[k] - s) <= 1e-12 * abs(s) + 1e-13
+    for n in range(ny):
+        for m in range(nx):
+            u = (m - (nx - 1) / 2) * P
+            v = (n - (ny - 1) / 2) * 1.5 * P
+            s = sum(c[k] * cmath.exp(2j * math.pi * (xy[k, 0] * u + xy[k, 1] * v) / (LAM * F))
+                    for k in range(K))
+            assert abs(back[n, m] - s) <= 1e-12 * abs(s) + 1e-13
+
+
+# ------------------------------------------------ single focus closed form
+def test_single_focus_linear_ramp():
+    """K = 1: after one cycle phi is arg(Theta_0) plus the linear ramp to the focus, |Theta| = sum A."""
+    rng = np.random.default_rng(14)
+    ny, nx = 12, 16
+    x0, y0 = 1.3e-3, -0.7e-3
+    A = O.default_amplitude(nx, ny, P, P)
+    phi0 = rng.uniform(-np.pi, np.pi, (ny, nx))
+    fx, fy = O.plan_matrices(nx, ny, P, P, LAM, F, [[x0, y0]])
+    theta0 = O.forward(O.pupil_field(A, phi0), fx, fy)
+    out = O.gsw(A, phi0, fx, fy, np.array([1.0]), n_iter=1)
+    u = (np.arange(nx) - (nx - 1) / 2) * P
+    v = (np.arange(ny) - (ny - 1) / 2) * P
+    ramp = np.angle(theta0[0]) + 2 * np.pi * (x0 * u[None, :] + y0 * v[:, None]) / (LAM * F)
+    assert np.max(np.abs(np.exp(1j * out["phi"]) - np.exp(1j * ramp))) < 1e-9
+    assert abs(np.abs(out["theta"][0]) - A.sum()) < 1e-12 * A.sum()
+    assert abs(out["xi"] - 1.0) < 1e-12
+
+
+# ------------------------------------------------ Parseval / Bessel
+def test_parseval_and_bessel():
+    rng = np.random.default_rng(15)
+    N = 16
+    E = rand_field(rng, N, N)
+    q = np.arange(N, dtype=float)
+    qx, qy = np.meshgrid(q, q)
+    fx = O.dft_rows(qx.ravel(), O.pupil_coords(N, 1.0), N)
+    fy = O.dft_rows(qy.ravel(), O.pupil_coords(N, 1.0), N)
+    theta = O.forward(E, fx, fy)
+    energy = np.sum(np.abs(E) ** 2)
+    assert abs(np.sum(np.abs(theta) ** 2) - N * N * energy) < 1e-11 * N * N * energy
+    sub = rng.choice(N * N, 40, replace=False)
+    assert np.sum(np.abs(theta[sub]) ** 2) <= N * N * energy * (1 + 1e-12)
+
+
+# ------------------------------------------------ adjoint identity
+def test_adjoint_identity():
+    rng = np.random.default_rng(16)
+    ny, nx, K = 33, 40, 17
+    E = rand_field(rng, ny, nx)
+    c = rng.normal(size=K) + 1j * rng.normal(size=K)
+    fx, fy = O.plan_matrices(nx, ny, P, P, LAM, F, rng.uniform(-4e-3, 4e-3, (K, 2)))
+    lhs = np.vdot(c, O.forward(E, fx, fy))        # <P E, c>
+    rhs = np.vdot(O.adjoint(c, fx, fy), E)        # <E, P^H c>
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+# ------------------------------------------------ statistics by hand
+def test_intensity_accuracy_by_hand():
+    # t = (1,1) -> (1/2,1/2); I = (1,3) -> (1/4,3/4): xi = 1 - sqrt(1/8)/sqrt(5/8) = 1 - 1/sqrt(5)
+    assert abs(O.intensity_accuracy([1, 1], [1, 3]) - (1 - 1 / math.sqrt(5))) < 1e-15
+    assert O.intensity_accuracy([2, 5, 1], [4, 10, 2]) == pytest.approx(1.0, abs=1e-15)
+
+
+def test_uniformity_by_hand():
+    # r = (0.6, 0.9, 1.5): U = 1 - 0.9/2.1
+    assert O.uniformity([1, 1, 1], [0.2, 0.3, 0.5]) == pytest.approx(1 - 0.9 / 2.1, abs=1e-15)
+
+
+def test_weight_update_by_hand():
+    w = O.generalized_weights([1.0, 1.0], [1, 1], [1, 3])
+    assert w == pytest.approx([math.sqrt(2.0), math.sqrt(2.0 / 3.0)], abs=1e-15)
+    f = O.focused_field(np.array([2.0, 0.5]), np.array([1.0, 3.0]), np.array([1j, -2.0]))
+    assert f == pytest.approx([2 * 0.5 * 1j, 0.5 * math.sqrt(0.75) * -1.0], abs=1e-15)
+
+
+# ------------------------------------------------ invariances of the loop
+def _small_problem(seed=17, ny=14, nx=18, K=6):
+    rng = np.random.default_rng(seed)
+    A = O.default_amplitude(nx, ny, P, P)
+    phi0 = rng.uniform(-np.pi, np.pi, (ny, nx))
+    xy = rng.uniform(-2e-3, 2e-3, (K, 2))
+    t = rng.uniform(0.5, 1.0, K)
+    return rng, A, phi0, xy, t
+
+
+def phase_dist(a, b, weight=None):
+    d = np.abs(np.exp(1j * a) - np.exp(1j * b))
+    return float(np.max(d if weight is None else d * weight))
+
+
+def test_scale_invariance():
+    _, A, phi0, xy, t = _small_problem()
+    fx, fy = O.plan_matrices(A.shape[1], A.shape[0], P, P, LAM, F, xy)
+    a = O.gsw(A, phi0, fx, fy, t, 6)
+    b = O.gsw(3.7 * A, phi0, fx, fy, 0.2 * t, 6, w0=np.full(len(t), 5.0))
+    assert phase_dist(a["phi"], b["phi"]) < 1e-9
+    assert abs(a["xi"] - b["xi"]) < 1e-12
+
+
+def test_translation_invariance():
+    _, A, phi0, xy, t = _small_problem(18)
+    ny, nx = A.shape
+    dx, dy = 0.37e-3, -0.21e-3
+    u = O.pupil_coords(nx, P)[None, :]
+    v = O.pupil_coords(ny, P)[:, None]
+    ramp = 2 * np.pi * (dx * u + dy * v) / (LAM * F)
+    fx, fy = O.plan_matrices(nx, ny, P, P, LAM, F, xy)
+    fx2, fy2 = O.plan_matrices(nx, ny, P, P, LAM, F, xy + [dx, dy])
+    a = O.gsw(A, phi0, fx, fy, t, 5, record=True)
+    b = O.gsw(A, phi0 + ramp, fx2, fy2, t, 5, record=True)
+    for pa, pb in zip(a["phis"], b["phis"]):
+        assert phase_dist(pa + ramp, pb) < 1e-8
+
+
+def test_mirror_invariance():
+    _, A, phi0, xy, t = _small_problem(19)
+    ny, nx = A.shape
+    fx, fy = O.plan_matrices(nx, ny, P, P, LAM, F, xy)
+    fx2, fy2 = O.plan_matrices(nx, ny, P, P, LAM, F, xy * [-1.0, 1.0])
+    a = O.gsw(A, phi0, fx, fy, t, 5)
+    b = O.gsw(A[:, ::-1], phi0[:, ::-1], fx2, fy2, t, 5)
+    assert phase_dist(a["phi"][:, ::-1], b["phi"]) < 1e-9
+
+
+def test_uniform_targets_reduce_to_textbook_gsw():
+    """Uniform I~: the generalized weights give Di Leonardo's weighted GS.
+
+    The textbook loop below is written independently: a dense K x (ny*nx)
+    propagation matrix of the full 2D exponent, weights updated with the mean
+    focus amplitude, w <- w <|V|> / |V_k|.  The two differ in w by a global
+    factor only, which arg() does not see.
+    """
+    rng, A, phi0, xy, _ = _small_problem(20, K=7)
+    ny, nx = A.shape
+    t = np.ones(len(xy))
+    fx, fy = O.plan_matrices(nx, ny, P, P, LAM, F, xy)
+    ours = O.gsw(A, phi0, fx, fy, t, 8)
+    u = (np.arange(nx) - (nx - 1) / 2) * P
+    v = (np.arange(ny) - (ny - 1) / 2) * P
+    vv, uu = np.meshgrid(v, u, indexing="ij")
+    H = np.exp(-2j * np.pi * (np.outer(xy[:, 0], uu.ravel()) + np.outer(xy[:, 1], vv.ravel()))
+               / (LAM * F))
+    phi = phi0.ravel().copy()
+    w = np.ones(len(xy))
+    for _ in range(8):
+        V = H @ (A.ravel() * np.exp(1j * phi))
+        w = w * np.mean(np.abs(V)) / np.abs(V)
+        phi = np.angle(H.conj().T @ (w * V / np.abs(V)))
+    assert phase_dist(ours["phi"].ravel(), phi, A.ravel()) < 1e-8
+
+
+def test_gs_is_unweighted():
+    """weighting=False keeps w = 1 and matches the weighted loop's first iteration."""
+    _, A, phi0, xy, t = _small_problem(21)
+    fx, fy = O.plan_matrices(A.shape[1], A.shape[0], P, P, LAM, F, xy)
+    gs = O.gsw(A, phi0, fx, fy, t, 4, weighting=False)
+    assert np.all(gs["w"] == 1.0)
+    gsw1 = O.gsw(A, phi0, fx, fy, t, 1)
+    gs1 = O.gsw(A, phi0, fx, fy, t, 1, weighting=False)
+    assert phase_dist(gs1["phi"], gsw1["phi"]) > 1e-6  # the update does change the phase
+
+
+def test_threshold_stops_before_update():
+    _, A, phi0, xy, t = _small_problem(22)
+    fx, fy = O.plan_matrices(A.shape[1], A.shape[0], P, P, LAM, F, xy)
+    full = O.gsw(A, phi0, fx, fy, t, 30)
+    xs = full["xi_hist"]
+    thr = 0.5 * (xs[3] + xs[4]) if xs[4] > xs[3] else xs[3] - 1e-9
+    stop = O.gsw(A, phi0, fx, fy, t, 30, threshold=thr)
+    j = int(np.argmax(xs > thr))
+    assert stop["iters"] == j
+    assert len(stop["xi_hist"]) == j + 1
+
+
+# ------------------------------------------------ the paper's convergence claim
+def test_paper_convergence_9x9():
+    """Table 1 optics, 9x9 foci with various intensities: generalized weighting reaches xi >= 0.99
+    within a few tens of iterations, plain GS stays below 0.9 after 100 (Fig. 2(h) discussion).
+
+    The paper reaches 0.99 at iteration 16 with targets and an initial guess
+    it does not give; with seeded U[0.5,1] targets, a random initial phase and
+    a Gaussian beam the oracle gets there near iteration 24, so the bound is 40.
+    """
+    rng = np.random.default_rng(23)
+    n, pitch, lam, f = 1000, 12.5e-6, 785e-9, 0.25
+    gap = 20 * 3.45e-6
+    g = (np.arange(9) - 4) * gap
+    xx, yy = np.meshgrid(g, g)
+    xy = np.stack([xx.ravel(), yy.ravel()], 1)
+    t = rng.uniform(0.5, 1.0, 81)
+    A = O.default_amplitude(n, n, pitch, pitch)
+    phi0 = rng.uniform(-np.pi, np.pi, (n, n))
+    fx, fy = O.plan_matrices(n, n, pitch, pitch, lam, f, xy)
+    gsw = O.gsw(A, phi0, fx, fy, t, 40)
+    gs = O.gsw(A, phi0, fx, fy, t, 100, weighting=False)
+    first = int(np.argmax(np.append(gsw["xi_hist"], gsw["xi"]) >= 0.99))
+    assert 0 < first <= 40
+    assert gs["xi"] < 0.9
+
+
+# ------------------------------------------------ gradient by finite differences
+@pytest.mark.parametrize("ny,nx,K,subset", [(16, 16, 5, None), (64, 64, 8, 48)])
+def test_phase_gradient_finite_differences(ny, nx, K, subset):
+    rng = np.random.default_rng(24 + K)
+    A = O.default_amplitude(nx, ny, P, P)
+    phi = rng.uniform(-np.pi, np.pi, (ny, nx))
+    xy = rng.uniform(-2e-3, 2e-3, (K, 2))
+    t = rng.uniform(0.5, 1.0, K)
+    fx, fy = O.plan_matrices(nx, ny, P, P, LAM, F, xy)
+
+    def loss(p):
+        return O.intensity_loss(t, np.abs(O.forward(O.pupil_field(A, p), fx, fy)) ** 2)
+
+    I = np.abs(O.forward(O.pupil_field(A, phi), fx, fy)) ** 2
+    g = O.phase_gradient(A, phi, fx, fy, O.intensity_loss_grad_I(t, I))
+    idx = range(ny * nx) if subset is None else rng.choice(ny * nx, subset, replace=False)
+    h = 1e-6
+    num, ana = [], []
+    for i in idx:
+        d = np.zeros(ny * nx)
+        d[i] = h
+        d = d.reshape(ny, nx)
+        num.append((loss(phi + d) - loss(phi - d)) / (2 * h))
+        ana.append(g.ravel()[i])
+    assert rel(ana, num) < 1e-6
+
+
+def test_loss_grad_I_finite_differences():
+    rng = np.random.default_rng(30)
+    t = rng.uniform(0.5, 1, 9)
+    I = rng.uniform(0.1, 2, 9)
+    g = O.intensity_loss_grad_I(t, I)
+    h = 1e-7
+    for k in range(9):
+        d = np.zeros(9)
+        d[k] = h
+        fd = (O.intensity_loss(t, I + d) - O.intensity_loss(t, I - d)) / (2 * h)
+        assert abs(fd - g[k]) < 1e-7 * max(1.0, abs(g[k]))
+
+
+# ------------------------------------------------ generator against its published vector
+def test_splitmix64_published_vector():
+    with open(os.path.join(GOLDEN, "splitmix64.json")) as fh:
+        gold = json.load(fh)
+    state = gold["seed"]
+    for expect in gold["outputs"]:
+        assert O.splitmix64(state) == expect
+        state = (state + 0x9E3779B97F4A7C15) & ((1 << 64) - 1)
+
+
+def test_default_phase_uses_stream_order():
+    with open(os.path.join(GOLDEN, "splitmix64.json")) as fh:
+        gold = json.load(fh)
+    phi = O.default_phase(5, 1, gold["seed"]).ravel()
+    expect = [(v >> 11) / 2.0 ** 53 * 2 * np.pi - np.pi for v in gold["outputs"]]
+    assert np.allclose(phi, expect, rtol=0, atol=1e-15)
+    big = O.default_phase(32, 32, 7)
+    assert big.min() >= -np.pi and big.max() < np.pi
+    assert abs(big.mean()) < 0.2
+
+
+def test_default_amplitude_profile():
+    A = O.default_amplitude(101, 81, 1.0, 2.0, 0.4)
+    assert A[40, 50] == 1.0                        # centre pixel of an odd aperture
+    wx, wy = 0.4 * 101, 0.4 * 81 * 2.0
+    assert A[40, 50 + 10] == pytest.approx(math.exp(-(10 / wx) ** 2), rel=1e-14)
+    assert A[40 + 7, 50] == pytest.approx(math.exp(-(14 / wy) ** 2), rel=1e-14)
