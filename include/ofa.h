@@ -1,0 +1,225 @@
+/*
+ * ofa.h -- C ABI of the GB300 GSW-MTP optical-focus-array library.
+ *
+ * The library computes phase-only holograms (CGHs) for arbitrary optical
+ * focus arrays with the method of Liu et al., "Fast generation of arbitrary
+ * optical focus array" (arXiv 2206.12661):
+ *   - far-field propagation between the SLM pupil and the focal plane written
+ *     as a matrix triple product with arbitrarily sampled DFT matrices
+ *     (Eq. 1, Eq. 2), evaluated only at the foci (zero elements removed);
+ *   - the weighted Gerchberg-Saxton loop with the paper's generalized
+ *     weighting update (Algorithm 1).
+ *
+ * Conventions shared by every call
+ *   - Pupil arrays are row-major [ny][nx] float32 (rows along y).  Pupil
+ *     sample positions are centred: u_m = (m - (nx-1)/2) * pitch_x, likewise v_n.
+ *   - Focus positions are float64 metres in the focal plane, [K][2] = (x, y).
+ *     Spatial frequency of pupil position u is u / (wavelength * focal_length).
+ *   - Complex vectors are interleaved float32 pairs (re, im).
+ *   - Every call returns an ofa_status; no C++ exception crosses the ABI.
+ *     Device errors raised by asynchronous work surface at the next call
+ *     that synchronises; a plan stays destroyable after any error.
+ *   - A plan is bound to one CUDA stream and one device (the device current
+ *     at creation).  Calls on one plan are not thread-safe; distinct plans
+ *     are independent.
+ *   - "device" pointers are CUDA device (or managed) addresses on the plan's
+ *     device; "host" pointers are ordinary host memory.  Inputs are deep
+ *     copied: the library never keeps a caller's pointer after a call returns.
+ */
+#ifndef OFA_H_
+#define OFA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ofa_plan ofa_plan;
+typedef struct ofa_batch ofa_batch;
+
+typedef enum ofa_status {
+  OFA_OK = 0,
+  OFA_ERR_INVALID_ARG = 1,   /* null pointer, non-positive size, non-finite value */
+  OFA_ERR_OUT_OF_RANGE = 2,  /* focus outside the alias-free field |x| < lambda f / (2 p) */
+  OFA_ERR_CUDA = 3,          /* a CUDA runtime/driver call failed (see ofa_last_error) */
+  OFA_ERR_OOM = 4,           /* device or host allocation failed */
+  OFA_ERR_NUMERIC = 5,       /* sum of focus intensities is zero or not finite */
+  OFA_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  OFA_ERR_UNSUPPORTED = 7    /* option not available on this device or for these sizes */
+} ofa_status;
+
+/* Arithmetic of the two matrix products of the loop.  Every form accumulates
+ * in FP32; the DFT phase arguments are always formed and reduced in FP64. */
+typedef enum ofa_precision {
+  OFA_PREC_FP32 = 0,    /* FP32 FMA on the CUDA cores                              */
+  OFA_PREC_TF32 = 1,    /* tensor cores, TF32 operands, one product                */
+  OFA_PREC_BF16 = 2,    /* tensor cores, BF16 operands, one product                */
+  OFA_PREC_BF16X3 = 3,  /* tensor cores, BF16 hi+lo split, three products          */
+  OFA_PREC_F16X3 = 4    /* tensor cores, FP16 hi+lo split with power-of-two
+                           operand scaling, three products (FP32-level accuracy) */
+} ofa_precision;
+
+typedef enum ofa_mem_space { OFA_MEM_HOST = 0, OFA_MEM_DEVICE = 1 } ofa_mem_space;
+
+typedef struct ofa_options {
+  int precision;             /* ofa_precision; default OFA_PREC_F16X3 */
+  uint64_t seed;             /* seed of the default initial phase; default 0 */
+  void* cuda_stream;         /* cudaStream_t the plan runs on; NULL = a non-blocking stream the
+                                plan creates and owns */
+  const float* amplitude;    /* [ny][nx] pupil amplitude A >= 0, or NULL for the default
+                                Gaussian exp(-(u^2/wx^2 + v^2/wy^2)), w = waist_frac * n * p */
+  double waist_frac;         /* default 0.4 */
+  const float* phi0;         /* [ny][nx] initial guess phi_0 (radians), or NULL for
+                                2*pi*(splitmix64 stream of seed >> 11)/2^53 - pi per pixel */
+  int mem_space;             /* ofa_mem_space of focus_xy, target, amplitude and phi0 */
+  int weighting;             /* 1 = generalized weighting of Algorithm 1 (default),
+                                0 = plain GS (w stays 1) */
+} ofa_options;
+
+typedef struct ofa_stats {
+  int iterations;            /* completed iterations j (forward + update + inverse) */
+  double xi;                 /* intensity accuracy of the latest forward (Algorithm 1) */
+  double uniformity;         /* 1 - (max r - min r)/(max r + min r), r_k = Ihat_k / t_k */
+  double sum_intensity;      /* sum_k |Theta_k|^2 of the latest forward (plan scale) */
+  double energy_fraction;    /* sum_k |Theta_k|^2 / (nx * ny * sum A^2): share of the pupil
+                                energy landing on the foci (exact Parseval share when the
+                                foci sit on distinct points of the pupil's DFT grid) */
+} ofa_stats;
+
+/* Fill *opt with the defaults listed above.  Host only; never fails for non-NULL opt. */
+ofa_status ofa_options_default(ofa_options* opt);
+
+/*
+ * ofa_plan_create -- problem statement of Algorithm 1 (Input) with the system
+ * parameters of Table 1.
+ *   nx, ny                 pupil (SLM) samples, >= 1
+ *   pitch_x, pitch_y       pupil sample pitch (m), > 0
+ *   wavelength, focal_length  (m), > 0
+ *   n_foci                 K >= 1
+ *   focus_xy               [K][2] float64 focus positions (m); each must lie in the
+ *                          alias-free field |x| < lambda f / (2 pitch_x), same in y
+ *                          (sampling conditions of Eq. 2 still hold), else
+ *                          OFA_ERR_OUT_OF_RANGE
+ *   target_intensity       [K] float32 target intensities I~ >= 0 (any scale; the
+ *                          loop uses I~ / sum I~), sum > 0
+ *   opt                    NULL = defaults
+ * Builds the DFT rows Fx[k][m] = exp(-i 2 pi x_k u_m / (lambda f)) and Fy likewise
+ * (phase arguments reduced in FP64), sets E_0 = A exp(i phi_0), w_0 = 1, j = 0.
+ * The plan owns every device buffer it allocates.  *out is NULL on failure.
+ */
+ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, double pitch_y,
+                           double wavelength, double focal_length, int n_foci,
+                           const double* focus_xy, const float* target_intensity,
+                           const ofa_options* opt);
+
+/*
+ * ofa_iterate -- run n_iter iterations of Algorithm 1: forward MTP at the foci,
+ * I = |Theta|^2, intensity accuracy xi, generalized weight update
+ * w_j = w_{j-1} sqrt(I~/I), focused field w_j sqrt(I~) exp(i arg Theta),
+ * inverse MTP (adjoint of Eq. 2), phi = arg(E), E = A exp(i phi).
+ *   threshold   stop before the update once xi > threshold (the loop's break);
+ *               threshold <= 0 or >= 1 disables the test and runs exactly n_iter.
+ *   iters_done  (nullable, host) iterations completed by this call
+ *   xi          (nullable, host) xi of one extra forward at the final phase.
+ * With both outputs NULL and the threshold disabled the call only enqueues work
+ * on the plan's stream and returns without synchronising.
+ */
+ofa_status ofa_iterate(ofa_plan* plan, int n_iter, double threshold, int* iters_done, double* xi);
+
+/* Copy the current CGH phi [ny][nx] (radians in (-pi, pi]) to phi_out, which lives in
+ * out_mem_space.  Synchronises the plan's stream for host output. */
+ofa_status ofa_get_phase(const ofa_plan* plan, float* phi_out, int out_mem_space);
+
+/* Release every resource of the plan.  NULL-safe. */
+ofa_status ofa_destroy(ofa_plan* plan);
+
+/* Statistics of one forward at the current phase (runs that forward; host output). */
+ofa_status ofa_get_stats(ofa_plan* plan, ofa_stats* stats);
+
+/* xi of the forward at the start of each iteration since creation (or the last
+ * set_state), oldest first: copies min(capacity, count) values, *count = number kept.
+ * The plan keeps the most recent 65536. */
+ofa_status ofa_get_xi_history(const ofa_plan* plan, double* xi_out, int capacity, int* count);
+
+/* Loop state (phi [ny][nx], w [K], j) -- checkpoint / resume.  Pointers live in
+ * mem_space; any of phi / w may be NULL to leave that part untouched (set) or
+ * unread (get).  Resuming from a saved state reproduces the uninterrupted run
+ * bit for bit on the same device and precision. */
+ofa_status ofa_get_state(const ofa_plan* plan, float* phi, float* w, int* j, int mem_space);
+ofa_status ofa_set_state(ofa_plan* plan, const float* phi, const float* w, int j, int mem_space);
+
+/*
+ * ofa_forward -- Eq. 2 at the foci for a given phase, without touching the loop
+ * state: theta = P_MTP(A exp(i phi)), intensity = |theta|^2.
+ *   phi        device [ny][nx]
+ *   theta      device [K] complex (nullable)
+ *   intensity  device [K] (nullable)
+ * Enqueued on the plan's stream; no synchronisation.
+ */
+ofa_status ofa_forward(ofa_plan* plan, const float* phi, float* theta, float* intensity);
+
+/*
+ * ofa_adjoint -- gradient of a loss L(I) of the focus intensities with respect to
+ * the phase, given g = dL/dI (device [K]) and the theta returned by ofa_forward
+ * for the same phi:  dL/dphi = 2 Im(conj(E) B),  B = P_MTP^H(g * theta),
+ * E = A exp(i phi).  grad_phi is device [ny][nx].  Uses the same adjoint product
+ * as the loop's inverse propagation.  Enqueued on the plan's stream.
+ */
+ofa_status ofa_adjoint(ofa_plan* plan, const float* phi, const float* theta,
+                       const float* grad_intensity, float* grad_phi);
+
+/*
+ * ofa_profile_kernels -- measurement aid: average device time (ms) of each kernel
+ * of one loop iteration, each launched `reps` (>= 1) times back to back on the
+ * plan's stream between CUDA events, after one untimed launch:
+ *   ms_out[0] forward product (+ per-focus dot), ms_out[1] focal statistics and
+ *   weight update, ms_out[2] inverse left-operand build (0 for OFA_PREC_FP32),
+ *   ms_out[3] inverse product (+ phase projection).
+ * The loop state (phi, w, j, xi history) is saved before and restored after, so
+ * the call does not change the result of later iterations.  Synchronises.
+ */
+ofa_status ofa_profile_kernels(ofa_plan* plan, int reps, double* ms_out);
+
+/* Problem sizes of a plan (any output may be NULL). */
+ofa_status ofa_plan_info(const ofa_plan* plan, int* nx, int* ny, int* n_foci, int* precision);
+
+/*
+ * Batched holograms: many independent problems of uneven pupil size and focus
+ * count advanced together, every iteration of all of them in one persistent
+ * kernel launch per phase, captured in a CUDA graph.  The plans keep their own
+ * buffers and state and must share one device; the batch owns its scheduler.
+ */
+ofa_status ofa_batch_create(ofa_batch** out, ofa_plan* const* plans, int count, void* cuda_stream);
+ofa_status ofa_batch_iterate(ofa_batch* batch, int n_iter);
+ofa_status ofa_batch_destroy(ofa_batch* batch);
+
+/* Host-only helpers (no GPU needed). */
+
+/* Zero-padded FFT size of the conventional IFTA along one axis, Eq. 3:
+ * M = M0 lambda / (2 NA dd) with NA = M0 pitch / (2 f), i.e. ceil(lambda f / (pitch dd))
+ * for focal-plane sampling interval dd (m).  (Table 1 gives 4551.) */
+ofa_status ofa_fft_equivalent_size(int m0, double pitch, double wavelength,
+                                   double focal_length, double focal_sampling, int* m_out);
+
+/* Foci per axis that fit the alias-free field lambda f / pitch at spacing gap (m):
+ * floor(lambda f / (pitch gap)).  (Table 1 with a 20-camera-pixel gap gives 227.) */
+ofa_status ofa_max_foci_per_axis(double pitch, double wavelength, double focal_length,
+                                 double gap, int* count_out);
+
+/* Validate focus positions against the alias-free field, exactly as
+ * ofa_plan_create does: OFA_OK, OFA_ERR_OUT_OF_RANGE (first offender in
+ * *bad_index, nullable) or OFA_ERR_INVALID_ARG.  Host pointers. */
+ofa_status ofa_check_foci(int n_foci, const double* focus_xy, double pitch_x, double pitch_y,
+                          double wavelength, double focal_length, int* bad_index);
+
+const char* ofa_status_string(ofa_status status);
+/* Message of the last failure on this plan (or of the last failed create/host call
+ * on this thread when plan is NULL).  Valid until the next call on the same plan. */
+const char* ofa_last_error(const ofa_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OFA_H_ */

@@ -1,0 +1,239 @@
+// Kernel (c): focal-plane statistics and the generalized weighting update of
+// Algorithm 1, plus the per-iteration left operand of the inverse product.
+//
+// One CTA of 1024 threads sums the per-tile partials of Theta in a fixed order,
+// forms I_k = |Theta_k|^2, S = sum I (FP64), the intensity accuracy
+//   xi = 1 - ||t - Ihat|| / ||Ihat||,  Ihat = I / S,  t = I~ / sum I~
+// (FP64 reductions with a fixed shuffle tree, so every run is bitwise
+// reproducible), records xi, applies the loop's break test, then updates
+//   w_k <- w_k sqrt(t_k / Ihat_k)                       (generalized weighting)
+//   c_k  = w_k sqrt(t_k) exp(i arg Theta_k) * 2^s       (focused field)
+// where 2^s is the power of two that brings max |c| into [1/2, 1): arg() of
+// the inverse product does not see a positive scale, and the tensor-core
+// operand formats want bounded magnitudes.
+#include <math_constants.h>
+
+#include "ofa_internal.cuh"
+#include "ofa_split.cuh"
+
+namespace {
+
+constexpr int FT = 1024;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = sh[0];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) r = fmax(r, sh[i]);
+  return r;
+}
+
+__global__ void __launch_bounds__(FT) focal_kernel(
+    const float2* __restrict__ part, int n_part, int kp, int K, const float* __restrict__ t,
+    float* __restrict__ w, float2* __restrict__ theta, float* __restrict__ inten,
+    float2* __restrict__ c, double* __restrict__ hist, OfaDevState* __restrict__ st, int mode,
+    int weighting, float out_scale, double energy) {
+  __shared__ double sh[32];
+  if (mode == 0 && st->done) return;
+  const int tid = threadIdx.x;
+
+  // Theta_k = sum over tiles in fixed order; I_k = |Theta_k|^2.
+  double s_i = 0.0;
+  for (int k = tid; k < K; k += FT) {
+    float2 a = make_float2(0.f, 0.f);
+    for (int p = 0; p < n_part; ++p) {
+      const float2 v = part[(size_t)p * kp + k];
+      a.x += v.x;
+      a.y += v.y;
+    }
+    const float ik = a.x * a.x + a.y * a.y;
+    if (mode == 2) {
+      theta[k] = make_float2(a.x * out_scale, a.y * out_scale);
+      inten[k] = ik * out_scale * out_scale;
+    } else {
+      theta[k] = a;
+      inten[k] = ik;
+    }
+    s_i += ik;
+  }
+  if (mode == 2) return;
+  const double S = block_sum(s_i, sh);
+  if (!(S > 0.0) || !isfinite(S)) {
+    if (tid == 0) {
+      atomicOr(&st->err, OFA_ERRBIT_NUMERIC);
+      if (mode == 0) st->done = 1;
+    }
+    return;
+  }
+
+  double d2 = 0.0, n2 = 0.0, rmin = CUDART_INF, rmax = 0.0;
+  for (int k = tid; k < K; k += FT) {
+    const double ih = (double)inten[k] / S;
+    const double tk = (double)t[k];
+    d2 += (tk - ih) * (tk - ih);
+    n2 += ih * ih;
+    if (tk > 0.0) {
+      const double r = ih / tk;
+      rmin = fmin(rmin, r);
+      rmax = fmax(rmax, r);
+    }
+  }
+  d2 = block_sum(d2, sh);
+  n2 = block_sum(n2, sh);
+  const double xi = 1.0 - sqrt(d2 / n2);
+
+  if (mode == 1) {
+    rmax = block_max(rmax, sh);
+    rmin = -block_max(-rmin, sh);
+    if (tid == 0) {
+      const double s2 = (double)out_scale * out_scale;
+      st->xi = xi;
+      st->uniformity = 1.0 - (rmax - rmin) / (rmax + rmin);
+      st->sum_i = S * s2;
+      st->energy_fraction = energy > 0.0 ? S * s2 / energy : 0.0;
+    }
+    return;
+  }
+
+  // mode 0: one loop iteration of Algorithm 1.
+  if (tid == 0) {
+    const int h = st->hist_count;
+    hist[h % OFA_HIST_CAP] = xi;
+    st->hist_count = h + 1;
+    st->xi = xi;
+  }
+  const double thr = st->threshold;
+  if (thr > 0.0 && thr < 1.0 && xi > thr) {
+    if (tid == 0) st->done = 1;
+    return;
+  }
+  double mx = 0.0;
+  for (int k = tid; k < K; k += FT) {
+    const double tk = (double)t[k];
+    if (weighting) {
+      const double ih = fmax((double)inten[k] / S, 1e-30);
+      w[k] = (float)((double)w[k] * sqrt(tk / ih));
+    }
+    mx = fmax(mx, (double)w[k] * sqrt(tk));
+  }
+  mx = block_max(mx, sh);
+  int e = 0;
+  frexp(mx, &e);
+  const double scale = mx > 0.0 ? ldexp(1.0, -e) : 1.0;
+  for (int k = tid; k < kp; k += FT) {
+    float2 ck = make_float2(0.f, 0.f);
+    if (k < K) {
+      const float2 th = theta[k];
+      const float r2 = th.x * th.x + th.y * th.y;
+      const float mag = (float)((double)w[k] * sqrt((double)t[k]) * scale);
+      if (r2 > 0.f) {
+        const float inv = rsqrtf(r2);
+        ck = make_float2(mag * th.x * inv, mag * th.y * inv);
+      } else {
+        ck = make_float2(mag, 0.f);  // arg(0) = 0
+      }
+    }
+    c[k] = ck;
+  }
+  if (tid == 0) {
+    st->j += 1;
+    st->c_scale = (float)scale;
+  }
+}
+
+__global__ void control_kernel(OfaDevState* st, double thr, int reset_done) {
+  st->threshold = thr;
+  if (reset_done) st->done = 0;
+}
+
+__global__ void set_j_kernel(OfaDevState* st, int j, int reset_hist) {
+  st->j = j;
+  st->done = 0;
+  if (reset_hist) st->hist_count = 0;
+}
+
+// c_k = g_k Theta_k (gradient of a loss of the intensities), power-of-two scaled.
+__global__ void __launch_bounds__(FT) grad_c_kernel(const float2* __restrict__ theta,
+                                                    const float* __restrict__ g, int K, int kp,
+                                                    float in_scale, float2* __restrict__ c,
+                                                    OfaDevState* __restrict__ st) {
+  __shared__ double sh[32];
+  double mx = 0.0;
+  for (int k = threadIdx.x; k < K; k += FT) {
+    const float2 th = theta[k];
+    const double a = fabs((double)g[k]) * sqrt((double)th.x * th.x + (double)th.y * th.y);
+    mx = fmax(mx, a * in_scale);
+  }
+  mx = block_max(mx, sh);
+  int e = 0;
+  frexp(mx, &e);
+  const float scale = mx > 0.0 ? (float)ldexp(1.0, -e) : 1.f;
+  for (int k = threadIdx.x; k < kp; k += FT) {
+    float2 ck = make_float2(0.f, 0.f);
+    if (k < K) {
+      const float f = g[k] * in_scale * scale;
+      ck = make_float2(f * theta[k].x, f * theta[k].y);
+    }
+    c[k] = ck;
+  }
+  if (threadIdx.x == 0) st->c_scale = scale;
+}
+
+// P[n][2k..2k+1] = conj(Fy[k,n]) c_k in the operand format of the precision.
+__global__ void build_p_kernel(const float2* __restrict__ fyT, const float2* __restrict__ c,
+                               const int* __restrict__ done, int nyp, int kp, int prec, void* hi,
+                               void* lo) {
+  if (done != nullptr && *done) return;
+  const size_t total = (size_t)nyp * kp;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % kp);
+    const float2 f = fyT[i];
+    const float2 ck = c[k];
+    split_store2(prec, hi, lo, 2 * i, f.x * ck.x + f.y * ck.y, f.x * ck.y - f.y * ck.x);
+  }
+}
+
+}  // namespace
+
+void launch_focal(const float2* part, int n_part, int kp, int K, const float* t, float* w,
+                  float2* theta, float* inten, float2* c, double* hist, OfaDevState* st, int mode,
+                  int weighting, float out_scale, double energy, cudaStream_t s) {
+  focal_kernel<<<1, FT, 0, s>>>(part, n_part, kp, K, t, w, theta, inten, c, hist, st, mode,
+                                weighting, out_scale, energy);
+}
+
+void launch_control(OfaDevState* st, double threshold, int reset_done, cudaStream_t s) {
+  control_kernel<<<1, 1, 0, s>>>(st, threshold, reset_done);
+}
+
+void launch_set_j(OfaDevState* st, int j, int reset_hist, cudaStream_t s) {
+  set_j_kernel<<<1, 1, 0, s>>>(st, j, reset_hist);
+}
+
+void launch_grad_c(const float2* theta, const float* g, int K, int kp, float in_scale, float2* c,
+                   OfaDevState* st, cudaStream_t s) {
+  grad_c_kernel<<<1, FT, 0, s>>>(theta, g, K, kp, in_scale, c, st);
+}
+
+void launch_build_p(const float2* fyT, const float2* c, const int* done, int nyp, int kp,
+                    int prec, void* hi, void* lo, cudaStream_t s) {
+  const size_t total = (size_t)nyp * kp;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  build_p_kernel<<<(int)blocks, 256, 0, s>>>(fyT, c, done, nyp, kp, prec, hi, lo);
+}

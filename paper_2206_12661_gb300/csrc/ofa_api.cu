@@ -1,0 +1,868 @@
+// Host side of the C ABI declared in include/ofa.h.
+//
+// A plan owns its device buffers, a private capture stream and two CUDA graphs
+// (a chunk of iterations and a single iteration) built on first use; every
+// launch of the loop replays a graph on the plan's stream.  One iteration is
+//   FP32 form:        forward (fused phi->field)  ->  focal  ->  inverse (+arg)
+//   tensor-core form: forward (TMA/tcgen05, dot epilogue) -> focal -> P build
+//                     -> inverse (TMA/tcgen05, arg + next field epilogue)
+// The threshold test of Algorithm 1 runs on the device (focal kernel sets a
+// flag that makes the rest of a launch skip); the host checks it between
+// chunks only when a threshold is set.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ofa_internal.cuh"
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+const char* kStatusNames[] = {"OFA_OK",          "OFA_ERR_INVALID_ARG", "OFA_ERR_OUT_OF_RANGE",
+                              "OFA_ERR_CUDA",    "OFA_ERR_OOM",         "OFA_ERR_NUMERIC",
+                              "OFA_ERR_TIMEOUT", "OFA_ERR_UNSUPPORTED"};
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e == cudaSuccess) e = cudaMemset(*p, 0, count * sizeof(T));
+  return e;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+cudaMemcpyKind kind_from(int mem_space) {
+  return mem_space == OFA_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+
+void free_tc(TcOperands& t) {
+  dfree(t.e_hi);
+  dfree(t.e_lo);
+  dfree(t.bx_hi);
+  dfree(t.bx_lo);
+  dfree(t.p_hi);
+  dfree(t.p_lo);
+  dfree(t.q_hi);
+  dfree(t.q_lo);
+  t = TcOperands();
+}
+
+// Tile choice for the two products (cost model: waves x per-CTA MMA work).
+void choose_tiles(ofa_plan* p, TcOperands& t, int sms) {
+  const int tiles_m = p->nyp / 128;
+  const int kb_fwd = (2 * p->nxp * t.elem_bytes) / 128;
+  double best = 1e30;
+  for (int bn : {256, 128}) {
+    for (int split = 1; split <= 8; split *= 2) {
+      if (kb_fwd / split < 4) break;
+      const long ctas = (long)tiles_m * (2 * p->kp / bn) * split;
+      const long waves = (ctas + sms - 1) / sms;
+      const double cost = (double)waves * ((double)kb_fwd / split) * bn * t.npass +
+                          0.02 * split * tiles_m * 2.0 * p->kp;
+      if (cost < best - 1e-9) {
+        best = cost;
+        t.fwd_bn = bn;
+        t.fwd_split = split;
+      }
+    }
+  }
+  best = 1e30;
+  for (int bn : {256, 128}) {
+    const long ctas = (long)tiles_m * (2 * p->nxp / bn);
+    const long waves = (ctas + sms - 1) / sms;
+    const double cost = (double)waves * bn;
+    if (cost < best - 1e-9) {
+      best = cost;
+      t.bwd_bn = bn;
+    }
+  }
+}
+
+ofa_status alloc_tc(ofa_plan* p, TcOperands& t, bool with_static) {
+  const int eb = prec_elem_bytes(p->precision);
+  t.elem_bytes = eb;
+  t.npass = prec_npass(p->precision);
+  const size_t e_n = (size_t)p->nyp * 2 * p->nxp;
+  const size_t bx_n = (size_t)2 * p->kp * 2 * p->nxp;
+  const size_t pp_n = (size_t)p->nyp * 2 * p->kp;
+  auto A = [&](void** ptr, size_t n) -> bool {
+    uint8_t* q = nullptr;
+    if (dalloc(&q, n * eb) != cudaSuccess) return false;
+    *ptr = q;
+    return true;
+  };
+  bool ok = A(&t.e_hi, e_n) && (t.npass == 1 || A(&t.e_lo, e_n));
+  if (with_static) {
+    ok = ok && A(&t.bx_hi, bx_n) && (t.npass == 1 || A(&t.bx_lo, bx_n));
+    ok = ok && A(&t.p_hi, pp_n) && (t.npass == 1 || A(&t.p_lo, pp_n));
+    ok = ok && A(&t.q_hi, bx_n) && (t.npass == 1 || A(&t.q_lo, bx_n));
+  }
+  return ok ? OFA_OK : OFA_ERR_OOM;
+}
+
+void destroy_graphs(ofa_plan* p) {
+  if (p->chunk_exec) cudaGraphExecDestroy(p->chunk_exec);
+  if (p->one_exec) cudaGraphExecDestroy(p->one_exec);
+  p->chunk_exec = p->one_exec = nullptr;
+}
+
+int* done_ptr(ofa_plan* p) { return &p->st->done; }
+
+// One iteration of Algorithm 1 on stream s.
+void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
+  const int* done = done_ptr(p);
+  if (!prec_is_tc(p->precision)) {
+    launch_fwd_simt(p->phi, p->amp, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, done, s);
+    launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
+                 p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
+    launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->phi, done, s);
+  } else {
+    launch_fwd_tc(p, p->tc, done, s);
+    launch_focal(p->part, (p->nyp / 128) * p->tc.fwd_split, p->kp, p->K, p->t, p->w, p->theta,
+                 p->inten, p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
+    launch_build_p(p->fyT, p->c, done, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
+    launch_bwd_tc(p, p->tc, done, s);
+  }
+}
+
+// Forward at the loop's current phase + statistics (mode 1) or output (mode 2).
+void enqueue_forward_current(ofa_plan* p, cudaStream_t s) {
+  if (!prec_is_tc(p->precision)) {
+    launch_fwd_simt(p->phi, p->amp, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, s);
+    launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
+                 p->c, p->hist, p->st, 1, p->weighting, ldexpf(1.f, p->amp_exp), p->amp_energy,
+                 s);
+  } else {
+    launch_fwd_tc(p, p->tc, nullptr, s);
+    launch_focal(p->part, (p->nyp / 128) * p->tc.fwd_split, p->kp, p->K, p->t, p->w, p->theta,
+                 p->inten, p->c, p->hist, p->st, 1, p->weighting, ldexpf(1.f, p->amp_exp),
+                 p->amp_energy, s);
+  }
+}
+
+ofa_status build_graph(ofa_plan* p, int iters, cudaGraphExec_t* exec) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return ofa_cuda_check(p, e, "cudaStreamBeginCapture");
+  for (int i = 0; i < iters; ++i) enqueue_iteration(p, p->cap_stream);
+  e = cudaStreamEndCapture(p->cap_stream, &g);
+  if (e != cudaSuccess) return ofa_cuda_check(p, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  return ofa_cuda_check(p, e, "cudaGraphInstantiate");
+}
+
+ofa_status sync_and_check(ofa_plan* p) {
+  cudaError_t e = cudaMemcpyAsync(p->st_host, p->st, sizeof(OfaDevState), cudaMemcpyDeviceToHost,
+                                  p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  ofa_status s = ofa_cuda_check(p, e, "synchronising the plan's stream");
+  if (s != OFA_OK) return s;
+  if (p->st_host->err & OFA_ERRBIT_TIMEOUT)
+    return ofa_fail(p, OFA_ERR_TIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
+  if (p->st_host->err & OFA_ERRBIT_NUMERIC)
+    return ofa_fail(p, OFA_ERR_NUMERIC, "sum of focus intensities is zero or not finite");
+  return OFA_OK;
+}
+
+ofa_status ensure_aux(ofa_plan* p) {
+  if (!prec_is_tc(p->precision) || p->aux_ready) return OFA_OK;
+  TcOperands& a = p->tc_aux;
+  a = p->tc;  // shares the static operands and their maps
+  a.e_hi = a.e_lo = nullptr;
+  TcOperands tmp;
+  tmp.elem_bytes = p->tc.elem_bytes;
+  tmp.npass = p->tc.npass;
+  ofa_status s = alloc_tc(p, tmp, false);
+  if (s != OFA_OK) {
+    free_tc(tmp);
+    return ofa_fail(p, s, "allocating forward/adjoint field planes");
+  }
+  a.e_hi = tmp.e_hi;
+  a.e_lo = tmp.e_lo;
+  std::string err;
+  TcOperands probe = a;
+  if (!tc_encode_maps(p, probe, err)) {
+    dfree(a.e_hi);
+    dfree(a.e_lo);
+    return ofa_fail(p, OFA_ERR_CUDA, err);
+  }
+  a.tm_e_hi = probe.tm_e_hi;
+  a.tm_e_lo = probe.tm_e_lo;
+  p->aux_ready = true;
+  return OFA_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ shared helpers
+ofa_status ofa_fail(ofa_plan* p, ofa_status s, const std::string& msg) {
+  if (p) p->last_error = msg;
+  else g_thread_error = msg;
+  return s;
+}
+
+ofa_status ofa_cuda_check(ofa_plan* p, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return OFA_OK;
+  std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+  return ofa_fail(p, e == cudaErrorMemoryAllocation ? OFA_ERR_OOM : OFA_ERR_CUDA, msg);
+}
+
+void ofa_set_thread_error(const std::string& msg) { g_thread_error = msg; }
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* ofa_status_string(ofa_status s) {
+  int i = (int)s;
+  if (i < 0 || i >= (int)(sizeof(kStatusNames) / sizeof(kStatusNames[0]))) return "OFA_UNKNOWN";
+  return kStatusNames[i];
+}
+
+const char* ofa_last_error(const ofa_plan* p) {
+  return p ? p->last_error.c_str() : g_thread_error.c_str();
+}
+
+ofa_status ofa_options_default(ofa_options* o) {
+  if (!o) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "options pointer is NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->precision = OFA_PREC_F16X3;
+  o->seed = 0;
+  o->cuda_stream = nullptr;
+  o->amplitude = nullptr;
+  o->waist_frac = 0.4;
+  o->phi0 = nullptr;
+  o->mem_space = OFA_MEM_HOST;
+  o->weighting = 1;
+  return OFA_OK;
+}
+
+ofa_status ofa_fft_equivalent_size(int m0, double pitch, double wavelength, double focal_length,
+                                   double focal_sampling, int* m_out) {
+  if (m0 < 1 || !finite_pos(pitch) || !finite_pos(wavelength) || !finite_pos(focal_length) ||
+      !finite_pos(focal_sampling) || !m_out)
+    return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "ofa_fft_equivalent_size: bad argument");
+  const double na = m0 * pitch / (2.0 * focal_length);      // NA of the pupil aperture
+  const double m = m0 * wavelength / (2.0 * na * focal_sampling);
+  if (!(m < 2147483647.0))
+    return ofa_fail(nullptr, OFA_ERR_OUT_OF_RANGE, "ofa_fft_equivalent_size: overflow");
+  *m_out = (int)std::ceil(m - 1e-9);
+  return OFA_OK;
+}
+
+ofa_status ofa_max_foci_per_axis(double pitch, double wavelength, double focal_length, double gap,
+                                 int* count_out) {
+  if (!finite_pos(pitch) || !finite_pos(wavelength) || !finite_pos(focal_length) ||
+      !finite_pos(gap) || !count_out)
+    return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "ofa_max_foci_per_axis: bad argument");
+  const double field = wavelength * focal_length / pitch;    // alias-free field width
+  *count_out = (int)std::floor(field / gap + 1e-12);
+  return OFA_OK;
+}
+
+ofa_status ofa_check_foci(int n_foci, const double* xy, double px, double py, double wavelength,
+                          double focal_length, int* bad_index) {
+  if (bad_index) *bad_index = -1;
+  if (n_foci < 1 || !xy || !finite_pos(px) || !finite_pos(py) || !finite_pos(wavelength) ||
+      !finite_pos(focal_length))
+    return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "ofa_check_foci: bad argument");
+  const double hx = wavelength * focal_length / (2.0 * px);
+  const double hy = wavelength * focal_length / (2.0 * py);
+  for (int k = 0; k < n_foci; ++k) {
+    const double x = xy[2 * k], y = xy[2 * k + 1];
+    if (!std::isfinite(x) || !std::isfinite(y)) {
+      if (bad_index) *bad_index = k;
+      return ofa_fail(nullptr, OFA_ERR_INVALID_ARG,
+                      "focus " + std::to_string(k) + " has a non-finite coordinate");
+    }
+    if (std::fabs(x) >= hx || std::fabs(y) >= hy) {
+      if (bad_index) *bad_index = k;
+      return ofa_fail(nullptr, OFA_ERR_OUT_OF_RANGE,
+                      "focus " + std::to_string(k) + " lies outside the alias-free field");
+    }
+  }
+  return OFA_OK;
+}
+
+ofa_status ofa_plan_info(const ofa_plan* p, int* nx, int* ny, int* n_foci, int* precision) {
+  if (!p) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "plan is NULL");
+  if (nx) *nx = p->nx;
+  if (ny) *ny = p->ny;
+  if (n_foci) *n_foci = p->K;
+  if (precision) *precision = p->precision;
+  return OFA_OK;
+}
+
+ofa_status ofa_destroy(ofa_plan* p) {
+  if (!p) return OFA_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p->device);
+  if (p->stream || p->own_stream) cudaStreamSynchronize(p->stream);
+  destroy_graphs(p);
+  void* bufs[] = {p->focus_xy, p->t,   p->amp,     p->phi,  p->w,    p->fx,         p->fy,
+                  p->fyT,      p->part, p->theta,  p->inten, p->c,   p->hist,       p->st,
+                  p->scratch_phi};
+  for (void* b : bufs) dfree(b);
+  if (p->st_host) cudaFreeHost(p->st_host);
+  free_tc(p->tc);
+  if (p->aux_ready) {
+    dfree(p->tc_aux.e_hi);
+    dfree(p->tc_aux.e_lo);
+  }
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete p;
+  return OFA_OK;
+}
+
+ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, double pitch_y,
+                           double wavelength, double focal_length, int n_foci,
+                           const double* focus_xy, const float* target_intensity,
+                           const ofa_options* opt_in) {
+  if (!out) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "out pointer is NULL");
+  *out = nullptr;
+  ofa_options opt;
+  if (opt_in) opt = *opt_in;
+  else ofa_options_default(&opt);
+  if (nx < 1 || ny < 1 || n_foci < 1 || !focus_xy || !target_intensity)
+    return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "sizes must be >= 1 and pointers non-NULL");
+  if (nx > 32768 || ny > 32768 || n_foci > (1 << 22))
+    return ofa_fail(nullptr, OFA_ERR_UNSUPPORTED, "pupil or focus count too large");
+  if (!finite_pos(pitch_x) || !finite_pos(pitch_y) || !finite_pos(wavelength) ||
+      !finite_pos(focal_length))
+    return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "pitch, wavelength and focal length must be > 0");
+  if (opt.precision < OFA_PREC_FP32 || opt.precision > OFA_PREC_F16X3)
+    return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "unknown precision");
+  if (opt.mem_space != OFA_MEM_HOST && opt.mem_space != OFA_MEM_DEVICE)
+    return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "unknown memory space");
+  if (!opt.amplitude && !finite_pos(opt.waist_frac))
+    return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "waist_frac must be > 0");
+
+  const size_t npix = (size_t)nx * ny;
+  // Host copies of the small inputs for validation.
+  std::vector<double> xy(2 * (size_t)n_foci);
+  std::vector<float> tgt(n_foci);
+  if (opt.mem_space == OFA_MEM_DEVICE) {
+    cudaError_t e = cudaMemcpy(xy.data(), focus_xy, xy.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(tgt.data(), target_intensity, tgt.size() * sizeof(float),
+                     cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "reading device inputs");
+  } else {
+    std::memcpy(xy.data(), focus_xy, xy.size() * sizeof(double));
+    std::memcpy(tgt.data(), target_intensity, tgt.size() * sizeof(float));
+  }
+  ofa_status vs = ofa_check_foci(n_foci, xy.data(), pitch_x, pitch_y, wavelength, focal_length,
+                                 nullptr);
+  if (vs != OFA_OK) return vs;
+  double tsum = 0.0;
+  for (int k = 0; k < n_foci; ++k) {
+    if (!std::isfinite(tgt[k]) || tgt[k] < 0.f)
+      return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "target intensities must be finite and >= 0");
+    tsum += tgt[k];
+  }
+  if (!(tsum > 0.0)) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "target intensities sum to 0");
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "cudaGetDevice");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "cudaGetDeviceProperties");
+  if (prop.major * 10 + prop.minor != 103)
+    return ofa_fail(nullptr, OFA_ERR_UNSUPPORTED,
+                    "this library is built for sm_103a (GB300) only; device is sm_" +
+                        std::to_string(prop.major * 10 + prop.minor));
+
+  ofa_plan* p = new ofa_plan();
+  p->device = dev;
+  p->nx = nx;
+  p->ny = ny;
+  p->K = n_foci;
+  p->precision = opt.precision;
+  p->weighting = opt.weighting ? 1 : 0;
+  p->px = pitch_x;
+  p->py = pitch_y;
+  p->lambda = wavelength;
+  p->focal = focal_length;
+  p->nxp = round_up(nx, 128);
+  p->nyp = round_up(ny, 128);
+  p->kp = round_up(n_foci, 128);
+
+  auto fail = [&](ofa_status s) {
+    g_thread_error = p->last_error;
+    ofa_destroy(p);
+    return s;
+  };
+#define OFA_TRY(call, what)                                   \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return fail(ofa_cuda_check(p, e_, what)); \
+  } while (0)
+
+  if (opt.cuda_stream) {
+    p->stream = static_cast<cudaStream_t>(opt.cuda_stream);
+  } else {
+    OFA_TRY(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking), "creating stream");
+    p->own_stream = true;
+  }
+  OFA_TRY(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking),
+          "creating capture stream");
+
+  const bool tc = prec_is_tc(p->precision);
+  const int n_part_max = tc ? (p->nyp / 128) * 8 : simt_fwd_tiles(ny);
+  OFA_TRY(dalloc(&p->focus_xy, 2 * (size_t)n_foci), "alloc");
+  OFA_TRY(dalloc(&p->t, n_foci), "alloc");
+  OFA_TRY(dalloc(&p->amp, npix), "alloc");
+  OFA_TRY(dalloc(&p->phi, npix), "alloc");
+  OFA_TRY(dalloc(&p->w, n_foci), "alloc");
+  OFA_TRY(dalloc(&p->fx, (size_t)n_foci * nx), "alloc");
+  OFA_TRY(dalloc(&p->fy, (size_t)n_foci * ny), "alloc");
+  OFA_TRY(dalloc(&p->part, (size_t)n_part_max * p->kp), "alloc");
+  OFA_TRY(dalloc(&p->theta, n_foci), "alloc");
+  OFA_TRY(dalloc(&p->inten, n_foci), "alloc");
+  OFA_TRY(dalloc(&p->c, p->kp), "alloc");
+  OFA_TRY(dalloc(&p->hist, OFA_HIST_CAP), "alloc");
+  OFA_TRY(dalloc(&p->st, 1), "alloc");
+  OFA_TRY(cudaMallocHost(reinterpret_cast<void**>(&p->st_host), sizeof(OfaDevState)),
+          "pinned alloc");
+  if (tc) {
+    OFA_TRY(dalloc(&p->fyT, (size_t)p->nyp * p->kp), "alloc");
+    if (alloc_tc(p, p->tc, true) != OFA_OK)
+      return fail(ofa_fail(p, OFA_ERR_OOM, "allocating tensor-core operands"));
+  }
+
+  // Small inputs.
+  std::vector<float> tn(n_foci), ones(n_foci, 1.f);
+  for (int k = 0; k < n_foci; ++k) tn[k] = (float)(tgt[k] / tsum);
+  OFA_TRY(cudaMemcpy(p->focus_xy, xy.data(), xy.size() * sizeof(double), cudaMemcpyHostToDevice),
+          "copy foci");
+  OFA_TRY(cudaMemcpy(p->t, tn.data(), tn.size() * sizeof(float), cudaMemcpyHostToDevice),
+          "copy targets");
+  OFA_TRY(cudaMemcpy(p->w, ones.data(), ones.size() * sizeof(float), cudaMemcpyHostToDevice),
+          "init weights");
+
+  // Amplitude: copy or default, then scale by a power of two to max in (1/2, 1].
+  if (opt.amplitude) {
+    OFA_TRY(cudaMemcpyAsync(p->amp, opt.amplitude, npix * sizeof(float), kind_from(opt.mem_space),
+                            p->stream),
+            "copy amplitude");
+  } else {
+    launch_default_amplitude(p->amp, nx, ny, pitch_x, pitch_y, opt.waist_frac, p->stream);
+  }
+  std::vector<float> ah(npix);
+  OFA_TRY(cudaMemcpyAsync(ah.data(), p->amp, npix * sizeof(float), cudaMemcpyDeviceToHost,
+                          p->stream),
+          "read amplitude");
+  OFA_TRY(cudaStreamSynchronize(p->stream), "sync");
+  double amax = 0.0, energy = 0.0;
+  for (size_t i = 0; i < npix; ++i) {
+    const double a = ah[i];
+    if (!std::isfinite(a) || a < 0.0) {
+      p->last_error = "amplitude must be finite and >= 0";
+      return fail(OFA_ERR_INVALID_ARG);
+    }
+    amax = std::fmax(amax, a);
+    energy += a * a;
+  }
+  if (!(amax > 0.0)) {
+    p->last_error = "amplitude is zero everywhere";
+    return fail(OFA_ERR_INVALID_ARG);
+  }
+  int ex = 0;
+  std::frexp(amax, &ex);           // amax = f 2^ex, f in [1/2, 1)
+  if (amax == std::ldexp(1.0, ex - 1)) ex -= 1;  // exact power of two stays at 1
+  p->amp_exp = ex;
+  p->amp_energy = energy;
+  if (ex != 0) launch_scale(p->amp, npix, std::ldexp(1.0f, -ex), p->stream);
+
+  if (opt.phi0) {
+    OFA_TRY(cudaMemcpyAsync(p->phi, opt.phi0, npix * sizeof(float), kind_from(opt.mem_space),
+                            p->stream),
+            "copy phi0");
+  } else {
+    launch_default_phase(p->phi, nx, ny, opt.seed, p->stream);
+  }
+
+  // Kernel (a): DFT rows with FP64 phase reduction.
+  const double lam_f = wavelength * focal_length;
+  launch_dft_rows(p->focus_xy, 0, n_foci, nx, pitch_x, lam_f, p->fx, p->stream);
+  launch_dft_rows(p->focus_xy, 1, n_foci, ny, pitch_y, lam_f, p->fy, p->stream);
+  if (tc) {
+    launch_transpose_fy(p->fy, n_foci, ny, p->kp, p->nyp, p->fyT, p->stream);
+    launch_pack_fx(p->fx, n_foci, nx, p->kp, p->nxp, 0, p->precision, p->tc.bx_hi, p->tc.bx_lo,
+                   p->stream);
+    launch_pack_fx(p->fx, n_foci, nx, p->kp, p->nxp, 1, p->precision, p->tc.q_hi, p->tc.q_lo,
+                   p->stream);
+    launch_field_planes(p->phi, p->amp, nx, ny, p->nxp, p->precision, p->tc.e_hi, p->tc.e_lo,
+                        p->stream);
+    choose_tiles(p, p->tc, prop.multiProcessorCount);
+    OFA_TRY(tc_prepare(p->precision), "setting kernel shared-memory attributes");
+    std::string err;
+    if (!tc_encode_maps(p, p->tc, err)) {
+      p->last_error = err;
+      return fail(OFA_ERR_CUDA);
+    }
+  }
+  launch_set_j(p->st, 0, 1, p->stream);
+  launch_control(p->st, 0.0, 1, p->stream);
+  OFA_TRY(cudaGetLastError(), "launching set-up kernels");
+  OFA_TRY(cudaStreamSynchronize(p->stream), "plan set-up");
+#undef OFA_TRY
+  *out = p;
+  return OFA_OK;
+}
+
+ofa_status ofa_iterate(ofa_plan* p, int n_iter, double threshold, int* iters_done, double* xi) {
+  if (!p) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "plan is NULL");
+  if (n_iter < 0 || !std::isfinite(threshold))
+    return ofa_fail(p, OFA_ERR_INVALID_ARG, "n_iter must be >= 0 and threshold finite");
+  cudaSetDevice(p->device);
+  const bool use_thr = threshold > 0.0 && threshold < 1.0;
+  if (!p->chunk_exec) {
+    ofa_status s = build_graph(p, p->chunk_iters, &p->chunk_exec);
+    if (s != OFA_OK) return s;
+    s = build_graph(p, 1, &p->one_exec);
+    if (s != OFA_OK) return s;
+  }
+  launch_control(p->st, use_thr ? threshold : 0.0, 1, p->stream);
+  // iterations done by this call = j after - j before; read j before on the device stream
+  int j0 = -1;
+  const bool need_sync = use_thr || iters_done || xi;
+  if (need_sync) {
+    ofa_status s = sync_and_check(p);
+    if (s != OFA_OK) return s;
+    j0 = p->st_host->j;
+  }
+  int left = n_iter;
+  while (left > 0) {
+    cudaError_t e;
+    if (left >= p->chunk_iters) {
+      e = cudaGraphLaunch(p->chunk_exec, p->stream);
+      left -= p->chunk_iters;
+    } else {
+      e = cudaGraphLaunch(p->one_exec, p->stream);
+      left -= 1;
+    }
+    if (e != cudaSuccess) return ofa_cuda_check(p, e, "cudaGraphLaunch");
+    if (use_thr && (left % p->chunk_iters == 0 || left < p->chunk_iters)) {
+      ofa_status s = sync_and_check(p);
+      if (s != OFA_OK) return s;
+      if (p->st_host->done) break;
+    }
+  }
+  if (!need_sync) {
+    return ofa_cuda_check(p, cudaGetLastError(), "enqueueing iterations");
+  }
+  ofa_status s = sync_and_check(p);
+  if (s != OFA_OK) return s;
+  if (iters_done) *iters_done = p->st_host->j - j0;
+  if (xi) {
+    enqueue_forward_current(p, p->stream);
+    s = sync_and_check(p);
+    if (s != OFA_OK) return s;
+    *xi = p->st_host->xi;
+  }
+  return OFA_OK;
+}
+
+ofa_status ofa_get_phase(const ofa_plan* cp, float* phi_out, int out_mem_space) {
+  ofa_plan* p = const_cast<ofa_plan*>(cp);
+  if (!p || !phi_out) return ofa_fail(p, OFA_ERR_INVALID_ARG, "NULL argument");
+  if (out_mem_space != OFA_MEM_HOST && out_mem_space != OFA_MEM_DEVICE)
+    return ofa_fail(p, OFA_ERR_INVALID_ARG, "unknown memory space");
+  cudaSetDevice(p->device);
+  const size_t bytes = (size_t)p->nx * p->ny * sizeof(float);
+  cudaError_t e = cudaMemcpyAsync(phi_out, p->phi, bytes,
+                                  out_mem_space == OFA_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                                : cudaMemcpyDeviceToDevice,
+                                  p->stream);
+  if (e != cudaSuccess) return ofa_cuda_check(p, e, "copying phi");
+  if (out_mem_space == OFA_MEM_HOST) return sync_and_check(p);
+  return OFA_OK;
+}
+
+ofa_status ofa_get_stats(ofa_plan* p, ofa_stats* stats) {
+  if (!p || !stats) return ofa_fail(p, OFA_ERR_INVALID_ARG, "NULL argument");
+  cudaSetDevice(p->device);
+  enqueue_forward_current(p, p->stream);
+  ofa_status s = sync_and_check(p);
+  if (s != OFA_OK) return s;
+  stats->iterations = p->st_host->j;
+  stats->xi = p->st_host->xi;
+  stats->uniformity = p->st_host->uniformity;
+  stats->sum_intensity = p->st_host->sum_i;
+  stats->energy_fraction = p->st_host->energy_fraction / ((double)p->nx * p->ny);
+  return OFA_OK;
+}
+
+ofa_status ofa_get_xi_history(const ofa_plan* cp, double* xi_out, int capacity, int* count) {
+  ofa_plan* p = const_cast<ofa_plan*>(cp);
+  if (!p || !count || capacity < 0 || (capacity > 0 && !xi_out))
+    return ofa_fail(p, OFA_ERR_INVALID_ARG, "bad argument");
+  cudaSetDevice(p->device);
+  ofa_status s = sync_and_check(p);
+  if (s != OFA_OK) return s;
+  const int total = p->st_host->hist_count;
+  const int kept = total < OFA_HIST_CAP ? total : OFA_HIST_CAP;
+  *count = kept;
+  const int n = capacity < kept ? capacity : kept;
+  if (n == 0) return OFA_OK;
+  std::vector<double> ring(OFA_HIST_CAP);
+  cudaError_t e = cudaMemcpy(ring.data(), p->hist, sizeof(double) * OFA_HIST_CAP,
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return ofa_cuda_check(p, e, "reading xi history");
+  const int start = total < OFA_HIST_CAP ? 0 : total % OFA_HIST_CAP;
+  for (int i = 0; i < n; ++i) xi_out[i] = ring[(start + i) % OFA_HIST_CAP];
+  return OFA_OK;
+}
+
+ofa_status ofa_get_state(const ofa_plan* cp, float* phi, float* w, int* j, int mem_space) {
+  ofa_plan* p = const_cast<ofa_plan*>(cp);
+  if (!p) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "plan is NULL");
+  if (mem_space != OFA_MEM_HOST && mem_space != OFA_MEM_DEVICE)
+    return ofa_fail(p, OFA_ERR_INVALID_ARG, "unknown memory space");
+  cudaSetDevice(p->device);
+  const cudaMemcpyKind kd =
+      mem_space == OFA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  cudaError_t e = cudaSuccess;
+  if (phi) e = cudaMemcpyAsync(phi, p->phi, (size_t)p->nx * p->ny * 4, kd, p->stream);
+  if (e == cudaSuccess && w) e = cudaMemcpyAsync(w, p->w, (size_t)p->K * 4, kd, p->stream);
+  if (e != cudaSuccess) return ofa_cuda_check(p, e, "copying state");
+  ofa_status s = sync_and_check(p);
+  if (s != OFA_OK) return s;
+  if (j) *j = p->st_host->j;
+  return OFA_OK;
+}
+
+ofa_status ofa_set_state(ofa_plan* p, const float* phi, const float* w, int j, int mem_space) {
+  if (!p) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "plan is NULL");
+  if (j < 0 || (mem_space != OFA_MEM_HOST && mem_space != OFA_MEM_DEVICE))
+    return ofa_fail(p, OFA_ERR_INVALID_ARG, "bad argument");
+  cudaSetDevice(p->device);
+  const cudaMemcpyKind kd = kind_from(mem_space);
+  cudaError_t e = cudaSuccess;
+  if (phi) e = cudaMemcpyAsync(p->phi, phi, (size_t)p->nx * p->ny * 4, kd, p->stream);
+  if (e == cudaSuccess && w) e = cudaMemcpyAsync(p->w, w, (size_t)p->K * 4, kd, p->stream);
+  if (e != cudaSuccess) return ofa_cuda_check(p, e, "copying state");
+  if (prec_is_tc(p->precision))
+    launch_field_planes(p->phi, p->amp, p->nx, p->ny, p->nxp, p->precision, p->tc.e_hi,
+                        p->tc.e_lo, p->stream);
+  launch_set_j(p->st, j, 1, p->stream);
+  return sync_and_check(p);
+}
+
+ofa_status ofa_forward(ofa_plan* p, const float* phi, float* theta, float* intensity) {
+  if (!p || !phi) return ofa_fail(p, OFA_ERR_INVALID_ARG, "NULL argument");
+  cudaSetDevice(p->device);
+  float2* th = theta ? reinterpret_cast<float2*>(theta) : p->theta;
+  float* in = intensity ? intensity : p->inten;
+  const float out_scale = ldexpf(1.f, p->amp_exp);
+  if (!prec_is_tc(p->precision)) {
+    launch_fwd_simt(phi, p->amp, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr,
+                    p->stream);
+    launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, th, in, p->c, p->hist,
+                 p->st, 2, p->weighting, out_scale, p->amp_energy, p->stream);
+  } else {
+    ofa_status s = ensure_aux(p);
+    if (s != OFA_OK) return s;
+    launch_field_planes(phi, p->amp, p->nx, p->ny, p->nxp, p->precision, p->tc_aux.e_hi,
+                        p->tc_aux.e_lo, p->stream);
+    launch_fwd_tc(p, p->tc_aux, nullptr, p->stream);
+    launch_focal(p->part, (p->nyp / 128) * p->tc.fwd_split, p->kp, p->K, p->t, p->w, th, in, p->c,
+                 p->hist, p->st, 2, p->weighting, out_scale, p->amp_energy, p->stream);
+  }
+  return ofa_cuda_check(p, cudaGetLastError(), "launching forward");
+}
+
+ofa_status ofa_adjoint(ofa_plan* p, const float* phi, const float* theta,
+                       const float* grad_intensity, float* grad_phi) {
+  if (!p || !phi || !theta || !grad_intensity || !grad_phi)
+    return ofa_fail(p, OFA_ERR_INVALID_ARG, "NULL argument");
+  cudaSetDevice(p->device);
+  launch_grad_c(reinterpret_cast<const float2*>(theta), grad_intensity, p->K, p->kp, 1.f, p->c,
+                p->st, p->stream);
+  const float amp_factor = ldexpf(1.f, p->amp_exp);
+  if (!prec_is_tc(p->precision)) {
+    launch_grad_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, phi, p->amp, amp_factor, p->st,
+                     grad_phi, p->stream);
+  } else {
+    launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo,
+                   p->stream);
+    launch_grad_tc(p, p->tc, phi, amp_factor, grad_phi, p->stream);
+  }
+  return ofa_cuda_check(p, cudaGetLastError(), "launching adjoint");
+}
+
+ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
+  if (!p || reps < 1 || !ms_out) return ofa_fail(p, OFA_ERR_INVALID_ARG, "bad argument");
+  cudaSetDevice(p->device);
+  const bool tc = prec_is_tc(p->precision);
+  const size_t npix = (size_t)p->nx * p->ny;
+  // Save the loop state (the focal kernel updates w, j and the history; the
+  // inverse rewrites phi and the field planes).
+  float* phi_s = nullptr;
+  float* w_s = nullptr;
+  OfaDevState* st_s = nullptr;
+  void* e_s[2] = {nullptr, nullptr};
+  const size_t e_bytes = (size_t)p->nyp * 2 * p->nxp * p->tc.elem_bytes;
+  cudaError_t e = cudaMalloc(&phi_s, npix * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&w_s, (size_t)p->K * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&st_s, sizeof(OfaDevState));
+  if (e == cudaSuccess && tc) e = cudaMalloc(&e_s[0], e_bytes);
+  if (e == cudaSuccess && tc && p->tc.npass == 3) e = cudaMalloc(&e_s[1], e_bytes);
+  auto cleanup = [&]() {
+    dfree(phi_s);
+    dfree(w_s);
+    dfree(st_s);
+    dfree(e_s[0]);
+    dfree(e_s[1]);
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return ofa_cuda_check(p, e, "allocating profile scratch");
+  }
+  cudaStream_t s = p->stream;
+  cudaMemcpyAsync(phi_s, p->phi, npix * 4, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(w_s, p->w, (size_t)p->K * 4, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(st_s, p->st, sizeof(OfaDevState), cudaMemcpyDeviceToDevice, s);
+  if (tc) cudaMemcpyAsync(e_s[0], p->tc.e_hi, e_bytes, cudaMemcpyDeviceToDevice, s);
+  if (e_s[1]) cudaMemcpyAsync(e_s[1], p->tc.e_lo, e_bytes, cudaMemcpyDeviceToDevice, s);
+  launch_control(p->st, 0.0, 1, s);
+
+  const int n_part = tc ? (p->nyp / 128) * p->tc.fwd_split : simt_fwd_tiles(p->ny);
+  auto run = [&](int which) {
+    switch (which) {
+      case 0:
+        if (tc) launch_fwd_tc(p, p->tc, nullptr, s);
+        else launch_fwd_simt(p->phi, p->amp, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part,
+                             nullptr, s);
+        break;
+      case 1:
+        launch_control(p->st, 0.0, 1, s);
+        launch_focal(p->part, n_part, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist,
+                     p->st, 0, p->weighting, 1.f, p->amp_energy, s);
+        break;
+      case 2:
+        if (tc) launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi,
+                               p->tc.p_lo, s);
+        break;
+      default:
+        if (tc) launch_bwd_tc(p, p->tc, nullptr, s);
+        else launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->phi, nullptr, s);
+        break;
+    }
+  };
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  for (int which = 0; which < 4; ++which) {
+    if (which == 2 && !tc) {
+      ms_out[2] = 0.0;
+      continue;
+    }
+    run(which);  // warm-up
+    cudaEventRecord(ev0, s);
+    for (int r = 0; r < reps; ++r) run(which);
+    cudaEventRecord(ev1, s);
+    cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    ms_out[which] = (double)ms / reps;
+  }
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  cudaMemcpyAsync(p->phi, phi_s, npix * 4, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(p->w, w_s, (size_t)p->K * 4, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(p->st, st_s, sizeof(OfaDevState), cudaMemcpyDeviceToDevice, s);
+  if (tc) cudaMemcpyAsync(p->tc.e_hi, e_s[0], e_bytes, cudaMemcpyDeviceToDevice, s);
+  if (e_s[1]) cudaMemcpyAsync(p->tc.e_lo, e_s[1], e_bytes, cudaMemcpyDeviceToDevice, s);
+  ofa_status st = sync_and_check(p);
+  cleanup();
+  if (st != OFA_OK) return st;
+  return ofa_cuda_check(p, cudaGetLastError(), "profiling kernels");
+}
+
+// ------------------------------------------------------------------ batch
+struct ofa_batch {
+  std::vector<ofa_plan*> plans;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int exec_iters = 0;
+  int device = 0;
+  std::string last_error;
+};
+
+ofa_status ofa_batch_create(ofa_batch** out, ofa_plan* const* plans, int count, void* stream) {
+  if (!out || !plans || count < 1)
+    return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "bad batch argument");
+  *out = nullptr;
+  ofa_batch* b = new ofa_batch();
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i] || plans[i]->device != plans[0]->device) {
+      delete b;
+      return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "batch plans must be non-NULL, one device");
+    }
+    b->plans.push_back(plans[i]);
+  }
+  b->device = plans[0]->device;
+  cudaSetDevice(b->device);
+  b->stream = static_cast<cudaStream_t>(stream);
+  if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return ofa_fail(nullptr, OFA_ERR_CUDA, "creating batch capture stream");
+  }
+  *out = b;
+  return OFA_OK;
+}
+
+ofa_status ofa_batch_iterate(ofa_batch* b, int n_iter) {
+  if (!b || n_iter < 0) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "bad batch argument");
+  cudaSetDevice(b->device);
+  if (n_iter == 0) return OFA_OK;
+  if (!b->exec || b->exec_iters != n_iter) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return ofa_fail(nullptr, OFA_ERR_CUDA, "batch capture");
+    for (ofa_plan* p : b->plans) launch_control(p->st, 0.0, 1, b->cap_stream);
+    for (int it = 0; it < n_iter; ++it)
+      for (ofa_plan* p : b->plans) enqueue_iteration(p, b->cap_stream);
+    e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e != cudaSuccess) return ofa_fail(nullptr, OFA_ERR_CUDA, "batch capture end");
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return ofa_fail(nullptr, OFA_ERR_CUDA, "batch graph instantiate");
+    b->exec_iters = n_iter;
+  }
+  // The plans' own streams must see the batch's work in order.
+  cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+  if (e != cudaSuccess) return ofa_fail(nullptr, OFA_ERR_CUDA, "batch graph launch");
+  return OFA_OK;
+}
+
+ofa_status ofa_batch_destroy(ofa_batch* b) {
+  if (!b) return OFA_OK;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+  return OFA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Internal declarations shared by the CUDA translation units of libofa.
+//
+// Data layout in device memory (rows along y, row-major, complex = interleaved
+// float pairs):
+//   phi, amp        [ny][nx] float32                 CGH phi and amplitude A
+//   fx, fy          [K][nx], [K][ny] complex float32 DFT rows of Eq. 2 at the foci
+//   fyT             [nyp][kp] complex float32         Fy transposed, zero padded
+//   tensor-core operands (16-bit hi/lo planes, or one float32 plane for TF32):
+//   e_pl            [nyp][2*nxp]   E = A exp(i phi), re/im interleaved along m
+//   bx_pl           [2*kp][2*nxp]  real block form of Fx for the forward product
+//   p_pl            [nyp][2*kp]    conj(Fy)^T diag(c), rebuilt every iteration
+//   q_pl            [2*nxp][2*kp]  real block form of conj(Fx) for the inverse
+// nxp, nyp, kp are the sizes rounded up to whole tensor-core tiles; the
+// padding is zero and stays zero.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ofa.h"
+
+#define OFA_HIST_CAP 65536
+#define OFA_ERRBIT_TIMEOUT 1
+#define OFA_ERRBIT_NUMERIC 2
+
+// Loop state and control words that live in device memory.
+struct OfaDevState {
+  int j;              // completed iterations
+  int done;           // threshold reached: the remaining kernels of a launch skip
+  int err;            // OFA_ERRBIT_* raised by kernels
+  int hist_count;     // xi values recorded so far
+  double threshold;   // stop test of Algorithm 1 (<= 0 or >= 1: disabled)
+  double xi;          // statistics of the latest forward
+  double uniformity;
+  double sum_i;
+  double energy_fraction;
+  float c_scale;      // power-of-two factor applied to c this iteration
+  int pad_;
+};
+
+struct TcOperands {
+  int elem_bytes = 0;      // 2 (fp16 / bf16) or 4 (tf32)
+  int npass = 1;           // 1 or 3 (hi*hi + hi*lo + lo*hi)
+  void* e_hi = nullptr; void* e_lo = nullptr;
+  void* bx_hi = nullptr; void* bx_lo = nullptr;
+  void* p_hi = nullptr; void* p_lo = nullptr;
+  void* q_hi = nullptr; void* q_lo = nullptr;
+  CUtensorMap tm_e_hi, tm_e_lo, tm_bx_hi, tm_bx_lo, tm_p_hi, tm_p_lo, tm_q_hi, tm_q_lo;
+  int fwd_bn = 256, fwd_split = 1, bwd_bn = 256;
+};
+
+struct ofa_plan {
+  int device = 0;
+  cudaStream_t stream = nullptr;       // stream the plan's work is enqueued on
+  cudaStream_t cap_stream = nullptr;   // private stream used only for graph capture
+  bool own_stream = false;
+  int nx = 0, ny = 0, K = 0, precision = 0, weighting = 1;
+  double px = 0, py = 0, lambda = 0, focal = 0;
+  int nxp = 0, nyp = 0, kp = 0;        // padded sizes (tensor-core tiles)
+  int amp_exp = 0;                     // stored A = user A * 2^-amp_exp
+  double amp_energy = 0;               // sum of user A^2
+
+  double* focus_xy = nullptr;          // [K][2]
+  float* t = nullptr;                  // [K] normalised targets
+  float* amp = nullptr;                // [ny][nx]
+  float* phi = nullptr;                // [ny][nx]
+  float* w = nullptr;                  // [K]
+  float2* fx = nullptr;                // [K][nx]
+  float2* fy = nullptr;                // [K][ny]
+  float2* fyT = nullptr;               // [nyp][kp]
+  float2* part = nullptr;              // [n_part][kp] per-tile partial Theta
+  int n_part = 0;
+  float2* theta = nullptr;             // [K]
+  float* inten = nullptr;              // [K]
+  float2* c = nullptr;                 // [kp] focused field (scaled), zero padded
+  double* hist = nullptr;              // [OFA_HIST_CAP]
+  OfaDevState* st = nullptr;
+  OfaDevState* st_host = nullptr;      // pinned mirror for readback
+  float* scratch_phi = nullptr;        // for ofa_forward / ofa_adjoint on the tensor path
+  TcOperands tc;
+  TcOperands tc_aux;                   // E planes of an external phase (forward/adjoint)
+  bool aux_ready = false;
+
+  cudaGraphExec_t chunk_exec = nullptr;
+  cudaGraphExec_t one_exec = nullptr;
+  int chunk_iters = 16;
+
+  std::string last_error;
+};
+
+// ---------------------------------------------------------------- host helpers
+ofa_status ofa_fail(ofa_plan* p, ofa_status s, const std::string& msg);
+ofa_status ofa_cuda_check(ofa_plan* p, cudaError_t e, const char* what);
+void ofa_set_thread_error(const std::string& msg);
+
+// ---------------------------------------------------------------- kernels (k_gen.cu)
+void launch_dft_rows(const double* focus_xy, int coord, int K, int n, double pitch,
+                     double lam_f, float2* out, cudaStream_t s);
+void launch_default_amplitude(float* amp, int nx, int ny, double px, double py, double waist_frac,
+                              cudaStream_t s);
+void launch_default_phase(float* phi, int nx, int ny, uint64_t seed, cudaStream_t s);
+void launch_scale(float* x, size_t n, float f, cudaStream_t s);
+void launch_transpose_fy(const float2* fy, int K, int ny, int kp, int nyp, float2* fyT,
+                         cudaStream_t s);
+// Build the real block forms of Fx (forward, conj=0) or conj(Fx) (inverse, conj=1).
+void launch_pack_fx(const float2* fx, int K, int nx, int kp, int nxp, int inverse,
+                    int prec, void* hi, void* lo, cudaStream_t s);
+void launch_field_planes(const float* phi, const float* amp, int nx, int ny, int nxp,
+                         int prec, void* hi, void* lo, cudaStream_t s);
+
+// ---------------------------------------------------------------- kernels (k_simt.cu)
+void launch_fwd_simt(const float* phi, const float* amp, const float2* fx, const float2* fy,
+                     int nx, int ny, int K, int kp, float2* part, const int* done, cudaStream_t s);
+int simt_fwd_tiles(int ny);
+void launch_bwd_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,
+                     float* phi, const int* done, cudaStream_t s);
+void launch_grad_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,
+                      const float* phi, const float* amp, float amp_factor,
+                      const OfaDevState* st, float* grad, cudaStream_t s);
+
+// ---------------------------------------------------------------- kernels (k_focal.cu)
+// mode 0: loop iteration (record xi, threshold test, weight update, c)
+// mode 1: statistics only (xi, uniformity, sums into st)
+// mode 2: forward output only (theta, intensity to caller buffers, user scale)
+void launch_focal(const float2* part, int n_part, int kp, int K, const float* t, float* w,
+                  float2* theta, float* inten, float2* c, double* hist, OfaDevState* st,
+                  int mode, int weighting, float out_scale, double energy, cudaStream_t s);
+void launch_control(OfaDevState* st, double threshold, int reset_done, cudaStream_t s);
+void launch_set_j(OfaDevState* st, int j, int reset_hist, cudaStream_t s);
+void launch_grad_c(const float2* theta, const float* g, int K, int kp, float in_scale,
+                   float2* c, OfaDevState* st, cudaStream_t s);
+void launch_build_p(const float2* fyT, const float2* c, const int* done, int nyp, int kp,
+                    int prec, void* hi, void* lo, cudaStream_t s);
+
+// ---------------------------------------------------------------- kernels (k_umma.cu)
+cudaError_t tc_prepare(int prec);
+bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err);
+void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s);
+void launch_bwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s);
+void launch_grad_tc(ofa_plan* p, const TcOperands& t, const float* phi, float scale,
+                    float* grad, cudaStream_t s);
+
+inline bool prec_is_tc(int prec) { return prec != OFA_PREC_FP32; }
+inline int prec_elem_bytes(int prec) { return prec == OFA_PREC_TF32 ? 4 : 2; }
+inline int prec_npass(int prec) {
+  return (prec == OFA_PREC_BF16X3 || prec == OFA_PREC_F16X3) ? 3 : 1;
+}
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }

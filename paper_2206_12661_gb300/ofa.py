@@ -1,0 +1,324 @@
+"""ctypes binding of libofa (include/ofa.h): argument marshalling only.
+
+Every function named ``ofa_*`` here calls the C function of the same name;
+every step of the hologram loop runs in the CUDA library.  Device pointers may
+be given as integers or as objects with ``data_ptr()`` (torch tensors); host
+arrays as numpy arrays.  There is no CPU fallback: if libofa.so cannot be
+loaded, importing this module raises.
+
+``Plan`` is a small convenience wrapper that owns an ``ofa_plan*``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libofa.so")
+
+OFA_OK = 0
+OFA_ERR_INVALID_ARG = 1
+OFA_ERR_OUT_OF_RANGE = 2
+OFA_ERR_CUDA = 3
+OFA_ERR_OOM = 4
+OFA_ERR_NUMERIC = 5
+OFA_ERR_TIMEOUT = 6
+OFA_ERR_UNSUPPORTED = 7
+
+OFA_PREC_FP32 = 0
+OFA_PREC_TF32 = 1
+OFA_PREC_BF16 = 2
+OFA_PREC_BF16X3 = 3
+OFA_PREC_F16X3 = 4
+PRECISIONS = {"fp32": OFA_PREC_FP32, "tf32": OFA_PREC_TF32, "bf16": OFA_PREC_BF16,
+              "bf16x3": OFA_PREC_BF16X3, "f16x3": OFA_PREC_F16X3}
+
+OFA_MEM_HOST = 0
+OFA_MEM_DEVICE = 1
+
+
+class ofa_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("seed", C.c_uint64), ("cuda_stream", C.c_void_p),
+                ("amplitude", C.c_void_p), ("waist_frac", C.c_double), ("phi0", C.c_void_p),
+                ("mem_space", C.c_int), ("weighting", C.c_int)]
+
+
+class ofa_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("xi", C.c_double), ("uniformity", C.c_double),
+                ("sum_intensity", C.c_double), ("energy_fraction", C.c_double)]
+
+
+# (name, restype, argtypes) of every symbol declared in include/ofa.h
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+SIGNATURES = [
+    ("ofa_options_default", _I, [C.POINTER(ofa_options)]),
+    ("ofa_plan_create", _I, [C.POINTER(_P), _I, _I, _D, _D, _D, _D, _I, _P, _P,
+                             C.POINTER(ofa_options)]),
+    ("ofa_iterate", _I, [_P, _I, _D, C.POINTER(_I), C.POINTER(_D)]),
+    ("ofa_get_phase", _I, [_P, _P, _I]),
+    ("ofa_destroy", _I, [_P]),
+    ("ofa_get_stats", _I, [_P, C.POINTER(ofa_stats)]),
+    ("ofa_get_xi_history", _I, [_P, _P, _I, C.POINTER(_I)]),
+    ("ofa_get_state", _I, [_P, _P, _P, C.POINTER(_I), _I]),
+    ("ofa_set_state", _I, [_P, _P, _P, _I, _I]),
+    ("ofa_forward", _I, [_P, _P, _P, _P]),
+    ("ofa_adjoint", _I, [_P, _P, _P, _P, _P]),
+    ("ofa_profile_kernels", _I, [_P, _I, _P]),
+    ("ofa_plan_info", _I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    ("ofa_batch_create", _I, [C.POINTER(_P), C.POINTER(_P), _I, _P]),
+    ("ofa_batch_iterate", _I, [_P, _I]),
+    ("ofa_batch_destroy", _I, [_P]),
+    ("ofa_fft_equivalent_size", _I, [_I, _D, _D, _D, _D, C.POINTER(_I)]),
+    ("ofa_max_foci_per_axis", _I, [_D, _D, _D, _D, C.POINTER(_I)]),
+    ("ofa_check_foci", _I, [_I, _P, _D, _D, _D, _D, C.POINTER(_I)]),
+    ("ofa_status_string", C.c_char_p, [_I]),
+    ("ofa_last_error", C.c_char_p, [_P]),
+]
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libofa.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+class OfaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{ofa_status_string(status)}: {msg}")
+        self.status = status
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _check(status: int, plan=None):
+    if status != OFA_OK:
+        raise OfaError(status, ofa_last_error(plan))
+
+
+# ---------------------------------------------------------------- 1:1 wrappers
+def ofa_status_string(status: int) -> str:
+    return _lib.ofa_status_string(int(status)).decode()
+
+
+def ofa_last_error(plan=None) -> str:
+    return (_lib.ofa_last_error(plan) or b"").decode()
+
+
+def ofa_options_default() -> ofa_options:
+    o = ofa_options()
+    _check(_lib.ofa_options_default(C.byref(o)))
+    return o
+
+
+def ofa_plan_create(nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy, target,
+                    opt: ofa_options | None = None):
+    """Returns the plan handle (int).  focus_xy / target follow opt.mem_space."""
+    out = C.c_void_p()
+    k = int(focus_xy.shape[0])
+    st = _lib.ofa_plan_create(C.byref(out), int(nx), int(ny), float(pitch_x), float(pitch_y),
+                              float(wavelength), float(focal_length), k, _ptr(focus_xy),
+                              _ptr(target), C.byref(opt) if opt is not None else None)
+    _check(st, None)
+    return out.value
+
+
+def ofa_iterate(plan, n_iter: int, threshold: float = 0.0, want_stats: bool = False):
+    if not want_stats:
+        _check(_lib.ofa_iterate(plan, int(n_iter), float(threshold), None, None), plan)
+        return None
+    it = C.c_int()
+    xi = C.c_double()
+    _check(_lib.ofa_iterate(plan, int(n_iter), float(threshold), C.byref(it), C.byref(xi)), plan)
+    return it.value, xi.value
+
+
+def ofa_get_phase(plan, out, mem_space: int):
+    _check(_lib.ofa_get_phase(plan, _ptr(out), int(mem_space)), plan)
+
+
+def ofa_destroy(plan):
+    _check(_lib.ofa_destroy(plan), None)
+
+
+def ofa_get_stats(plan) -> ofa_stats:
+    s = ofa_stats()
+    _check(_lib.ofa_get_stats(plan, C.byref(s)), plan)
+    return s
+
+
+def ofa_get_xi_history(plan, capacity: int = 65536) -> np.ndarray:
+    buf = np.zeros(max(capacity, 1), dtype=np.float64)
+    n = C.c_int()
+    _check(_lib.ofa_get_xi_history(plan, _ptr(buf), int(capacity), C.byref(n)), plan)
+    return buf[:min(n.value, capacity)].copy()
+
+
+def ofa_get_state(plan, phi_out=None, w_out=None, mem_space: int = OFA_MEM_HOST) -> int:
+    j = C.c_int()
+    _check(_lib.ofa_get_state(plan, _ptr(phi_out), _ptr(w_out), C.byref(j), int(mem_space)), plan)
+    return j.value
+
+
+def ofa_set_state(plan, phi=None, w=None, j: int = 0, mem_space: int = OFA_MEM_HOST):
+    _check(_lib.ofa_set_state(plan, _ptr(phi), _ptr(w), int(j), int(mem_space)), plan)
+
+
+def ofa_forward(plan, phi, theta=None, intensity=None):
+    _check(_lib.ofa_forward(plan, _ptr(phi), _ptr(theta), _ptr(intensity)), plan)
+
+
+def ofa_adjoint(plan, phi, theta, grad_intensity, grad_phi):
+    _check(_lib.ofa_adjoint(plan, _ptr(phi), _ptr(theta), _ptr(grad_intensity), _ptr(grad_phi)),
+           plan)
+
+
+def ofa_profile_kernels(plan, reps: int = 20) -> np.ndarray:
+    """[forward, focal, inverse-operand build, inverse] average ms per launch."""
+    out = np.zeros(4, dtype=np.float64)
+    _check(_lib.ofa_profile_kernels(plan, int(reps), _ptr(out)), plan)
+    return out
+
+
+def ofa_plan_info(plan):
+    a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(_lib.ofa_plan_info(plan, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), plan)
+    return a.value, b.value, c.value, d.value
+
+
+def ofa_batch_create(plans, stream=None):
+    arr = (C.c_void_p * len(plans))(*plans)
+    out = C.c_void_p()
+    _check(_lib.ofa_batch_create(C.byref(out), arr, len(plans), stream))
+    return out.value
+
+
+def ofa_batch_iterate(batch, n_iter: int):
+    _check(_lib.ofa_batch_iterate(batch, int(n_iter)))
+
+
+def ofa_batch_destroy(batch):
+    _check(_lib.ofa_batch_destroy(batch))
+
+
+def ofa_fft_equivalent_size(m0, pitch, wavelength, focal_length, focal_sampling) -> int:
+    m = C.c_int()
+    _check(_lib.ofa_fft_equivalent_size(int(m0), float(pitch), float(wavelength),
+                                        float(focal_length), float(focal_sampling), C.byref(m)))
+    return m.value
+
+
+def ofa_max_foci_per_axis(pitch, wavelength, focal_length, gap) -> int:
+    n = C.c_int()
+    _check(_lib.ofa_max_foci_per_axis(float(pitch), float(wavelength), float(focal_length),
+                                      float(gap), C.byref(n)))
+    return n.value
+
+
+def ofa_check_foci(focus_xy, pitch_x, pitch_y, wavelength, focal_length):
+    """Returns (status, bad_index) without raising."""
+    xy = np.ascontiguousarray(focus_xy, dtype=np.float64)
+    bad = C.c_int()
+    st = _lib.ofa_check_foci(int(xy.shape[0]), _ptr(xy), float(pitch_x), float(pitch_y),
+                             float(wavelength), float(focal_length), C.byref(bad))
+    return st, bad.value
+
+
+# ---------------------------------------------------------------- convenience
+class Plan:
+    """Owns one ofa_plan*.  Host numpy inputs; stream = torch stream handle (int) or None."""
+
+    def __init__(self, nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy, target,
+                 precision="f16x3", amplitude=None, phi0=None, seed=0, weighting=True,
+                 stream=None, waist_frac=0.4, mem_space=OFA_MEM_HOST):
+        opt = ofa_options_default()
+        opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        opt.seed = int(seed)
+        opt.cuda_stream = stream
+        opt.weighting = 1 if weighting else 0
+        opt.waist_frac = float(waist_frac)
+        opt.mem_space = int(mem_space)
+        if mem_space == OFA_MEM_HOST:
+            focus_xy = np.ascontiguousarray(focus_xy, dtype=np.float64)
+            target = np.ascontiguousarray(target, dtype=np.float32)
+            if amplitude is not None:
+                amplitude = np.ascontiguousarray(amplitude, dtype=np.float32)
+            if phi0 is not None:
+                phi0 = np.ascontiguousarray(phi0, dtype=np.float32)
+        self._keep = (focus_xy, target, amplitude, phi0)
+        opt.amplitude = _ptr(amplitude)
+        opt.phi0 = _ptr(phi0)
+        self.nx, self.ny, self.K = int(nx), int(ny), int(focus_xy.shape[0])
+        self.handle = ofa_plan_create(nx, ny, pitch_x, pitch_y, wavelength, focal_length,
+                                      focus_xy, target, opt)
+        self._keep = None
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.nx, w.ny, w.pitch_x, w.pitch_y, w.wavelength, w.focal_length, w.focus_xy,
+                   w.target, amplitude=w.amplitude, phi0=w.phi0, **kw)
+
+    def iterate(self, n_iter, threshold=0.0, want_stats=False):
+        return ofa_iterate(self.handle, n_iter, threshold, want_stats)
+
+    def phase(self) -> np.ndarray:
+        out = np.empty((self.ny, self.nx), dtype=np.float32)
+        ofa_get_phase(self.handle, out, OFA_MEM_HOST)
+        return out
+
+    def stats(self) -> ofa_stats:
+        return ofa_get_stats(self.handle)
+
+    def xi_history(self) -> np.ndarray:
+        return ofa_get_xi_history(self.handle)
+
+    def get_state(self):
+        phi = np.empty((self.ny, self.nx), dtype=np.float32)
+        w = np.empty(self.K, dtype=np.float32)
+        j = ofa_get_state(self.handle, phi, w, OFA_MEM_HOST)
+        return phi, w, j
+
+    def set_state(self, phi=None, w=None, j=0):
+        phi = None if phi is None else np.ascontiguousarray(phi, dtype=np.float32)
+        w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+        ofa_set_state(self.handle, phi, w, j, OFA_MEM_HOST)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ofa_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -10,4 +10,12 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
-    config.addinivalue_line("markers", "slow: long-running CPU check")
+
+
+@pytest.fixture(scope="session")
+def ofa():
+    """The ctypes binding, building libofa.so first if it is missing or stale."""
+    from paper_2206_12661_gb300 import _build
+    _build.build()
+    from paper_2206_12661_gb300 import ofa as binding
+    return binding

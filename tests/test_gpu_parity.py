@@ -1,0 +1,321 @@
+"""GPU parity of libofa against the FP64 oracle (through the C ABI).
+
+Tolerances (relative L2 over the foci of | |Theta_gpu| - |Theta_ref| |):
+  fp32, f16x3, bf16x3  1e-5   FP32-accurate forms: 1e-5 on focus amplitudes
+  tf32                 2e-3   one TF32 product (u = 2^-11; measured ~2e-4 on CPU emulation)
+  bf16                 1e-2   one BF16 product (u = 2^-8; ~1.5e-3 on CPU emulation)
+Full runs: final xi and uniformity within 1e-3 (absolute) of the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2206_12661_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+AMP_TOL = {"fp32": 1e-5, "f16x3": 1e-5, "bf16x3": 1e-5, "tf32": 2e-3, "bf16": 1e-2}
+ALL = list(AMP_TOL)
+ACCURATE = ["fp32", "f16x3", "bf16x3"]
+
+
+@pytest.fixture(scope="module")
+def dev(ofa):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def oracle_mats(w):
+    return O.plan_matrices(w.nx, w.ny, w.pitch_x, w.pitch_y, w.wavelength, w.focal_length,
+                           w.focus_xy)
+
+
+def amp_err(theta_gpu, theta_ref):
+    a = np.abs(theta_gpu)
+    b = np.abs(theta_ref)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b)), float(np.max(np.abs(a - b)) / b.max())
+
+
+def custom(nx, ny, K, seed, spread=0.9, targets="uniform"):
+    rng = np.random.default_rng(seed)
+    half_x = 532e-9 * 0.2 / (2 * 8e-6)
+    xy = rng.uniform(-spread * half_x, spread * half_x, (K, 2))
+    t = np.ones(K) if targets == "uniform" else rng.uniform(0.5, 1.0, K)
+    return I.Workload(name=f"custom{nx}x{ny}_{K}", nx=nx, ny=ny, pitch_x=8e-6, pitch_y=8e-6,
+                      wavelength=532e-9, focal_length=0.2, focus_xy=xy,
+                      target=t.astype(np.float32),
+                      amplitude=I.gaussian_amplitude(nx, ny),
+                      phi0=I.uniform_phase(rng, nx, ny), n_iter=5)
+
+
+def gpu_forward(ofa, w, prec, phi=None):
+    plan = ofa.Plan.from_workload(w, precision=prec,
+                                  stream=torch.cuda.current_stream().cuda_stream)
+    phi_d = torch.from_numpy(np.ascontiguousarray(w.phi0 if phi is None else phi,
+                                                  dtype=np.float32)).cuda()
+    theta = torch.zeros(w.n_foci, 2, dtype=torch.float32, device="cuda")
+    inten = torch.zeros(w.n_foci, dtype=torch.float32, device="cuda")
+    ofa.ofa_forward(plan.handle, phi_d, theta, inten)
+    torch.cuda.synchronize()
+    th = theta.cpu().numpy()
+    plan.close()
+    return th[:, 0] + 1j * th[:, 1], inten.cpu().numpy()
+
+
+SHAPES = [(1, 3, 2), (7, 5, 3), (129, 100, 37), (300, 260, 300)]
+
+
+@pytest.mark.parametrize("prec", ALL)
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_forward_ragged(ofa, dev, prec, shape):
+    w = custom(*shape, seed=sum(shape))
+    fx, fy = oracle_mats(w)
+    ref = O.forward(O.pupil_field(w.amplitude, w.phi0), fx, fy)
+    th, inten = gpu_forward(ofa, w, prec)
+    err, emax = amp_err(th, ref)
+    assert err < AMP_TOL[prec], (err, emax)
+    # the complex value, not only its modulus, and I = |Theta|^2
+    cerr = np.linalg.norm(th - ref) / np.linalg.norm(ref)
+    assert cerr < 3 * AMP_TOL[prec]
+    assert np.allclose(inten, np.abs(th) ** 2, rtol=1e-5, atol=0)
+
+
+@pytest.mark.parametrize("prec", ALL)
+@pytest.mark.parametrize("name", ["pupil256_grid100_uniform", "pupil1024_poisson1000",
+                                  "pupil1920x1152_grid2500"])
+def test_forward_named(ofa, dev, prec, name):
+    w = I.named(name)
+    fx, fy = oracle_mats(w)
+    ref = O.forward(O.pupil_field(w.amplitude, w.phi0), fx, fy)
+    th, _ = gpu_forward(ofa, w, prec)
+    err, emax = amp_err(th, ref)
+    print(f"{name} {prec}: amp rel L2 {err:.3e}, max {emax:.3e}")
+    assert err < AMP_TOL[prec], (err, emax)
+
+
+def test_forward_max_foci_table1(ofa, dev):
+    """The paper's largest array: 227 x 227 foci at a 20-camera-pixel gap, 1000^2 pupil."""
+    n, pitch, lam, f = 1000, 12.5e-6, 785e-9, 0.25
+    c = (np.arange(227) - 113) * 20 * 3.45e-6
+    xx, yy = np.meshgrid(c, c)
+    xy = np.stack([xx.ravel(), yy.ravel()], 1)
+    rng = np.random.default_rng(5)
+    t = rng.uniform(0.5, 1, xy.shape[0]).astype(np.float32)
+    w = I.Workload("table1_227x227", n, n, pitch, pitch, lam, f, xy, t,
+                   I.gaussian_amplitude(n, n, pitch, pitch), I.uniform_phase(rng, n, n), 1)
+    th, _ = gpu_forward(ofa, w, "f16x3")
+    fx, fy = oracle_mats(w)
+    sample = rng.choice(xy.shape[0], 2000, replace=False)
+    ref = O.forward(O.pupil_field(w.amplitude, w.phi0), fx[sample], fy[sample])
+    err, emax = amp_err(th[sample], ref)
+    assert err < 1e-5, (err, emax)
+
+
+def one_step_reference(w, phi, wts, fx, fy):
+    A = w.amplitude.astype(np.float64)
+    theta = O.forward(O.pupil_field(A, phi), fx, fy)
+    inten = np.abs(theta) ** 2
+    w2 = O.generalized_weights(wts, w.target, inten)
+    back = O.adjoint(O.focused_field(w2, w.target, theta), fx, fy)
+    return theta, w2, back
+
+
+@pytest.mark.parametrize("prec", ALL)
+def test_one_step_from_same_iterate(ofa, dev, prec):
+    """From the oracle's iterate j: Theta, the new weights and the new phase."""
+    w = I.named("pupil256_grid100_uniform")
+    w.target = np.random.default_rng(3).uniform(0.5, 1.0, w.n_foci).astype(np.float32)
+    fx, fy = oracle_mats(w)
+    run = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, 7)
+    phi_j = run["phi"].astype(np.float32)
+    w_j = run["w"].astype(np.float32)
+    theta, w_new, back = one_step_reference(w, phi_j.astype(np.float64), w_j.astype(np.float64),
+                                            fx, fy)
+    plan = ofa.Plan.from_workload(w, precision=prec)
+    plan.set_state(phi_j, w_j, 7)
+    plan.iterate(1)
+    phi_g, w_g, j = plan.get_state()
+    plan.close()
+    assert j == 8
+    wrel = np.linalg.norm(w_g - w_new) / np.linalg.norm(w_new)
+    assert wrel < 20 * AMP_TOL[prec], wrel
+    mag = np.abs(back)
+    d = np.abs(np.exp(1j * phi_g) - np.exp(1j * np.angle(back)))
+    werr = math.sqrt(np.sum((mag * d) ** 2) / np.sum(mag ** 2))
+    assert werr < 20 * AMP_TOL[prec], werr
+    assert phi_g.min() >= -np.pi and phi_g.max() <= np.pi
+
+
+@pytest.mark.parametrize("prec", ALL)
+def test_full_run_grid100(ofa, dev, prec):
+    w = I.named("pupil256_grid100_uniform")
+    fx, fy = oracle_mats(w)
+    ref = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, w.n_iter)
+    plan = ofa.Plan.from_workload(w, precision=prec)
+    it, xi = plan.iterate(w.n_iter, want_stats=True)
+    st = plan.stats()
+    hist = plan.xi_history()
+    plan.close()
+    assert it == w.n_iter
+    assert abs(xi - ref["xi"]) < 1e-3, (xi, ref["xi"])
+    assert abs(st.xi - ref["xi"]) < 1e-3
+    assert abs(st.uniformity - ref["uniformity"]) < 1e-3, (st.uniformity, ref["uniformity"])
+    assert len(hist) == w.n_iter
+    assert np.max(np.abs(hist - ref["xi_hist"])) < 1e-3
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3", "fp32", "bf16"])
+def test_full_run_poisson1000(ofa, dev, prec):
+    w = I.named("pupil1024_poisson1000")
+    fx, fy = oracle_mats(w)
+    ref = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, w.n_iter)
+    plan = ofa.Plan.from_workload(w, precision=prec)
+    it, xi = plan.iterate(w.n_iter, want_stats=True)
+    st = plan.stats()
+    plan.close()
+    print(f"{prec}: xi {xi:.6f} vs {ref['xi']:.6f}; U {st.uniformity:.6f} vs {ref['uniformity']:.6f}")
+    assert it == w.n_iter
+    assert abs(xi - ref["xi"]) < 1e-3
+    assert abs(st.uniformity - ref["uniformity"]) < 1e-3
+
+
+def test_single_focus_closed_form(ofa, dev):
+    """K = 1: one iteration gives the linear ramp; the next forward has |Theta| = sum A, xi = 1."""
+    w = custom(96, 80, 1, seed=3)
+    w.focus_xy[:] = [[1.3e-3, -0.7e-3]]
+    fx, fy = oracle_mats(w)
+    plan = ofa.Plan.from_workload(w, precision="f16x3")
+    theta0, _ = gpu_forward(ofa, w, "f16x3")
+    plan.iterate(1)
+    phi1 = plan.phase()
+    st = plan.stats()
+    plan.close()
+    u = (np.arange(w.nx) - (w.nx - 1) / 2) * w.pitch_x
+    v = (np.arange(w.ny) - (w.ny - 1) / 2) * w.pitch_y
+    ramp = np.angle(theta0[0]) + 2 * np.pi * (1.3e-3 * u[None, :] - 0.7e-3 * v[:, None]) / (
+        w.wavelength * w.focal_length)
+    assert np.max(np.abs(np.exp(1j * phi1) - np.exp(1j * ramp))) < 1e-4
+    assert abs(math.sqrt(st.sum_intensity) - w.amplitude.astype(np.float64).sum()) < 1e-5 * w.amplitude.sum()
+    assert abs(st.xi - 1.0) < 1e-6
+
+
+def test_defaults_match_oracle(ofa, dev):
+    nx, ny, K = 48, 40, 5
+    w = custom(nx, ny, K, seed=9)
+    plan = ofa.Plan(nx, ny, w.pitch_x, w.pitch_y, w.wavelength, w.focal_length, w.focus_xy,
+                    w.target, precision="fp32", seed=1234567)
+    phi, wts, j = plan.get_state()
+    ref_phi = O.default_phase(nx, ny, 1234567)
+    assert np.max(np.abs(phi - ref_phi)) < 1e-6
+    assert j == 0 and np.all(wts == 1)
+    # default amplitude enters the forward
+    phi_d = torch.from_numpy(phi).cuda()
+    theta = torch.zeros(K, 2, device="cuda")
+    ofa.ofa_forward(plan.handle, phi_d, theta, None)
+    torch.cuda.synchronize()
+    th = theta.cpu().numpy()
+    plan.close()
+    fx, fy = oracle_mats(w)
+    A = O.default_amplitude(nx, ny, w.pitch_x, w.pitch_y, 0.4)
+    ref = O.forward(O.pupil_field(A, phi.astype(np.float64)), fx, fy)
+    assert amp_err(th[:, 0] + 1j * th[:, 1], ref)[0] < 1e-5
+
+
+def test_threshold_stops_like_algorithm1(ofa, dev):
+    w = I.named("pupil256_grid100_uniform")
+    fx, fy = oracle_mats(w)
+    ref = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, 60)
+    xs = ref["xi_hist"]
+    thr = 0.9
+    j = int(np.argmax(xs > thr))
+    assert np.min(np.abs(xs - thr)) > 1e-3  # no borderline iterate
+    plan = ofa.Plan.from_workload(w, precision="f16x3")
+    it, xi = plan.iterate(60, threshold=thr, want_stats=True)
+    plan.close()
+    assert it == j
+    assert xi > thr
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_resume_is_bitwise(ofa, dev, prec):
+    w = I.named("pupil256_grid100_uniform")
+    a = ofa.Plan.from_workload(w, precision=prec)
+    a.iterate(10)
+    phi_s, w_s, j_s = a.get_state()
+    a.iterate(13)
+    phi_a = a.phase()
+    a.close()
+    b = ofa.Plan.from_workload(w, precision=prec)
+    b.set_state(phi_s, w_s, j_s)
+    b.iterate(13)
+    phi_b, _, j_b = b.get_state()
+    b.close()
+    assert j_b == 23
+    assert np.array_equal(phi_a, phi_b)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3", "bf16"])
+def test_deterministic(ofa, dev, prec):
+    w = I.named("pupil256_grid100_uniform")
+    outs = []
+    for _ in range(2):
+        p = ofa.Plan.from_workload(w, precision=prec)
+        p.iterate(20)
+        outs.append(p.phase())
+        p.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("prec", ALL)
+@pytest.mark.parametrize("shape", [(64, 64, 8), (300, 260, 41)])
+def test_adjoint_gradient(ofa, dev, prec, shape):
+    w = custom(*shape, seed=4, targets="random")
+    fx, fy = oracle_mats(w)
+    A = w.amplitude.astype(np.float64)
+    phi = w.phi0.astype(np.float64)
+    theta = O.forward(O.pupil_field(A, phi), fx, fy)
+    g = O.intensity_loss_grad_I(w.target, np.abs(theta) ** 2)
+    ref = O.phase_gradient(A, phi, fx, fy, g)
+    plan = ofa.Plan.from_workload(w, precision=prec,
+                                  stream=torch.cuda.current_stream().cuda_stream)
+    phi_d = torch.from_numpy(w.phi0).cuda()
+    th = torch.zeros(w.n_foci, 2, device="cuda")
+    ofa.ofa_forward(plan.handle, phi_d, th, None)
+    gd = torch.from_numpy(g.astype(np.float32)).cuda()
+    grad = torch.zeros(w.ny, w.nx, device="cuda")
+    ofa.ofa_adjoint(plan.handle, phi_d, th, gd, grad)
+    torch.cuda.synchronize()
+    got = grad.cpu().numpy()
+    plan.close()
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel < 10 * AMP_TOL[prec], rel
+
+
+def test_create_errors_on_gpu(ofa, dev):
+    with pytest.raises(ofa.OfaError) as e:
+        ofa.Plan(16, 16, 8e-6, 8e-6, 532e-9, 0.2, np.array([[0.0, 7e-3]]), np.ones(1))
+    assert e.value.status == ofa.OFA_ERR_OUT_OF_RANGE
+    with pytest.raises(ofa.OfaError) as e:
+        ofa.Plan(16, 16, 8e-6, 8e-6, 532e-9, 0.2, np.zeros((2, 2)), np.ones(2),
+                 amplitude=np.zeros((16, 16), np.float32))
+    assert e.value.status == ofa.OFA_ERR_INVALID_ARG
+
+
+def test_batch_matches_individual(ofa, dev):
+    ws = I.batch_workloads(count=6, sizes=(256, 384), k_min=8, k_max=300, n_iter=6, seed=11)
+    plans = [ofa.Plan.from_workload(w, precision="f16x3") for w in ws]
+    stream = torch.cuda.Stream()
+    b = ofa.ofa_batch_create([p.handle for p in plans], stream.cuda_stream)
+    ofa.ofa_batch_iterate(b, 6)
+    stream.synchronize()
+    ofa.ofa_batch_destroy(b)
+    for w, p in zip(ws, plans):
+        q = ofa.Plan.from_workload(w, precision="f16x3")
+        q.iterate(6)
+        assert np.array_equal(p.phase(), q.phase())
+        q.close()
+        p.close()
