@@ -2,10 +2,11 @@
 // Algorithm 1, plus the per-iteration left operand of the inverse product.
 //
 // One CTA of 1024 threads sums the per-tile partials of Theta in a fixed order,
-// forms I_k = |Theta_k|^2, S = sum I (FP64), the intensity accuracy
+// forms I_k = |Theta_k|^2, S = sum I, the intensity accuracy
 //   xi = 1 - ||t - Ihat|| / ||Ihat||,  Ihat = I / S,  t = I~ / sum I~
-// (FP64 reductions with a fixed shuffle tree, so every run is bitwise
-// reproducible), records xi, applies the loop's break test, then updates
+// (fixed-order shuffle-tree reductions, so every run is bitwise reproducible;
+// FP32 inside the loop, FP64 for the reported statistic), records xi, applies
+// the loop's break test, then updates
 //   w_k <- w_k sqrt(t_k / Ihat_k)                       (generalized weighting)
 //   c_k  = w_k sqrt(t_k) exp(i arg Theta_k) * 2^s       (focused field)
 // where 2^s is the power of two that brings max |c| into [1/2, 1): arg() of
@@ -42,16 +43,53 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   return r;
 }
 
+// Fixed-order FP32 block reductions (every lane of every warp ends with the same
+// bits: xor-butterfly in registers, then warp partials summed in warp order).
+template <int N>
+__device__ __forceinline__ void block_sum_f(float (&v)[N], float* sh) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < N; ++i) sh[i * 32 + (threadIdx.x >> 5)] = v[i];
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float r = 0.f;
+    for (int w = 0; w < nw; ++w) r += sh[i * 32 + w];
+    v[i] = r;
+  }
+}
+
+__device__ __forceinline__ float block_max_f(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = sh[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, sh[w]);
+  return r;
+}
+
+// Per-focus work of one loop iteration runs in FP32; the statistics of mode 1
+// (the reported intensity accuracy and uniformity) are reduced in FP64.
 __global__ void __launch_bounds__(FT) focal_kernel(
     const float2* __restrict__ part, int n_part, int kp, int K, const float* __restrict__ t,
     float* __restrict__ w, float2* __restrict__ theta, float* __restrict__ inten,
     float2* __restrict__ c, double* __restrict__ hist, OfaDevState* __restrict__ st, int mode,
     int weighting, float out_scale, double energy) {
+  __shared__ float shf[4 * 32];
   __shared__ double sh[32];
   if (mode == 0 && st->done) return;
   const int tid = threadIdx.x;
 
   // Theta_k = sum over tiles in fixed order; I_k = |Theta_k|^2.
+  float r1[1] = {0.f};
   double s_i = 0.0;
   for (int k = tid; k < K; k += FT) {
     float2 a = make_float2(0.f, 0.f);
@@ -68,40 +106,36 @@ __global__ void __launch_bounds__(FT) focal_kernel(
       theta[k] = a;
       inten[k] = ik;
     }
-    s_i += ik;
+    r1[0] += ik;
+    if (mode == 1) s_i += ik;
   }
   if (mode == 2) return;
-  const double S = block_sum(s_i, sh);
-  if (!(S > 0.0) || !isfinite(S)) {
-    if (tid == 0) {
-      atomicOr(&st->err, OFA_ERRBIT_NUMERIC);
-      if (mode == 0) st->done = 1;
-    }
-    return;
-  }
-
-  double d2 = 0.0, n2 = 0.0, rmin = CUDART_INF, rmax = 0.0;
-  for (int k = tid; k < K; k += FT) {
-    const double ih = (double)inten[k] / S;
-    const double tk = (double)t[k];
-    d2 += (tk - ih) * (tk - ih);
-    n2 += ih * ih;
-    if (tk > 0.0) {
-      const double r = ih / tk;
-      rmin = fmin(rmin, r);
-      rmax = fmax(rmax, r);
-    }
-  }
-  d2 = block_sum(d2, sh);
-  n2 = block_sum(n2, sh);
-  const double xi = 1.0 - sqrt(d2 / n2);
 
   if (mode == 1) {
+    const double S = block_sum(s_i, sh);
+    if (!(S > 0.0) || !isfinite(S)) {
+      if (tid == 0) atomicOr(&st->err, OFA_ERRBIT_NUMERIC);
+      return;
+    }
+    double d2 = 0.0, n2 = 0.0, rmin = CUDART_INF, rmax = 0.0;
+    for (int k = tid; k < K; k += FT) {
+      const double ih = (double)inten[k] / S;
+      const double tk = (double)t[k];
+      d2 += (tk - ih) * (tk - ih);
+      n2 += ih * ih;
+      if (tk > 0.0) {
+        const double r = ih / tk;
+        rmin = fmin(rmin, r);
+        rmax = fmax(rmax, r);
+      }
+    }
+    d2 = block_sum(d2, sh);
+    n2 = block_sum(n2, sh);
     rmax = block_max(rmax, sh);
     rmin = -block_max(-rmin, sh);
     if (tid == 0) {
       const double s2 = (double)out_scale * out_scale;
-      st->xi = xi;
+      st->xi = 1.0 - sqrt(d2 / n2);
       st->uniformity = 1.0 - (rmax - rmin) / (rmax + rmin);
       st->sum_i = S * s2;
       st->energy_fraction = energy > 0.0 ? S * s2 / energy : 0.0;
@@ -110,6 +144,32 @@ __global__ void __launch_bounds__(FT) focal_kernel(
   }
 
   // mode 0: one loop iteration of Algorithm 1.
+  block_sum_f(r1, shf);
+  const float S = r1[0];
+  if (!(S > 0.f) || !isfinite(S)) {
+    if (tid == 0) {
+      atomicOr(&st->err, OFA_ERRBIT_NUMERIC);
+      st->done = 1;
+    }
+    return;
+  }
+  const float inv_s = 1.f / S;
+  // xi terms and the largest new focused-field magnitude, one reduction round
+  float r2[2] = {0.f, 0.f};
+  float mx = 0.f;
+  for (int k = tid; k < K; k += FT) {
+    const float ih = inten[k] * inv_s;
+    const float tk = t[k];
+    const float d = tk - ih;
+    r2[0] += d * d;
+    r2[1] += ih * ih;
+    float wk = w[k];
+    if (weighting) wk *= sqrtf(tk / fmaxf(ih, 1e-30f));
+    mx = fmaxf(mx, wk * sqrtf(tk));
+  }
+  block_sum_f(r2, shf + 32);
+  mx = block_max_f(mx, shf + 96);
+  const double xi = 1.0 - sqrt((double)r2[0] / (double)r2[1]);
   if (tid == 0) {
     const int h = st->hist_count;
     hist[h % OFA_HIST_CAP] = xi;
@@ -121,27 +181,23 @@ __global__ void __launch_bounds__(FT) focal_kernel(
     if (tid == 0) st->done = 1;
     return;
   }
-  double mx = 0.0;
-  for (int k = tid; k < K; k += FT) {
-    const double tk = (double)t[k];
-    if (weighting) {
-      const double ih = fmax((double)inten[k] / S, 1e-30);
-      w[k] = (float)((double)w[k] * sqrt(tk / ih));
-    }
-    mx = fmax(mx, (double)w[k] * sqrt(tk));
-  }
-  mx = block_max(mx, sh);
   int e = 0;
-  frexp(mx, &e);
-  const double scale = mx > 0.0 ? ldexp(1.0, -e) : 1.0;
+  frexpf(mx, &e);
+  const float scale = mx > 0.f ? exp2f((float)-e) : 1.f;
   for (int k = tid; k < kp; k += FT) {
     float2 ck = make_float2(0.f, 0.f);
     if (k < K) {
+      const float tk = t[k];
+      float wk = w[k];
+      if (weighting) {
+        wk *= sqrtf(tk / fmaxf(inten[k] * inv_s, 1e-30f));  // w_j = w_{j-1} sqrt(t / Ihat)
+        w[k] = wk;
+      }
+      const float mag = wk * sqrtf(tk) * scale;
       const float2 th = theta[k];
-      const float r2 = th.x * th.x + th.y * th.y;
-      const float mag = (float)((double)w[k] * sqrt((double)t[k]) * scale);
-      if (r2 > 0.f) {
-        const float inv = rsqrtf(r2);
+      const float rr = th.x * th.x + th.y * th.y;
+      if (rr > 0.f) {
+        const float inv = rsqrtf(rr);
         ck = make_float2(mag * th.x * inv, mag * th.y * inv);
       } else {
         ck = make_float2(mag, 0.f);  // arg(0) = 0
@@ -151,7 +207,7 @@ __global__ void __launch_bounds__(FT) focal_kernel(
   }
   if (tid == 0) {
     st->j += 1;
-    st->c_scale = (float)scale;
+    st->c_scale = scale;
   }
 }
 

@@ -114,7 +114,7 @@ __global__ void field_planes_kernel(const float* __restrict__ phi, const float* 
        i += (size_t)gridDim.x * blockDim.x) {
     int n = (int)(i / nx), m = (int)(i % nx);
     float s, c;
-    sincosf(phi[i], &s, &c);
+    __sincosf(phi[i], &s, &c);  // same intrinsic as the inverse epilogue: resume is bitwise
     float a = amp[i];
     split_store2(prec, hi, lo, ((size_t)n * nxp + m) * 2, a * c, a * s);
   }

@@ -16,7 +16,7 @@
 // Epilogues (fused, no intermediate goes to global memory):
 //   FWD   Theta partial of the tile: sum over its 128 rows n of Fy[k,n] G[n,k]
 //         (warp-shuffle reduce-scatter, then a fixed-order sum of four warps)
-//   BWD   phi = arg(E') and the next pupil field A E'/|E'| in operand format
+//   BWD   phi = arg(E') and the next pupil field A exp(i phi) in operand format
 //   GRAD  2 A Im(exp(-i phi) B) for the adjoint
 //
 // Warp roles (192 threads): warps 0-3 epilogue (TMEM lanes 32w..32w+31),
@@ -384,7 +384,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int col = t; col < BN; col += 128)
         dst[col] = ((red[col] + red[BN + col]) + red[2 * BN + col]) + red[3 * BN + col];
     } else {
-      const bool row_ok = n < ep.ny;
+      // Per-pixel work (thread = row); global loads and stores are staged through
+      // shared memory (the operand stages are free once the accumulator is
+      // complete) so that every warp-wide access covers whole 64-byte row segments.
+      uint8_t* wb = base + warp * 16384;
+      float* s_a = reinterpret_cast<float*>(wb);      // [32][17] amplitude
+      float* s_p = s_a + 32 * 17;                     // [32][17] phase in (gradient)
+      float* s_o = s_p + 32 * 17;                     // [32][17] phase / gradient out
+      uint2* s_h = reinterpret_cast<uint2*>(s_o + 32 * 17);  // [32][17] field, hi bits
+      uint2* s_l = s_h + 32 * 17;                     // [32][17] field, lo bits
+      const int nbase = m_tile * BM + warp * 32;
+      const int lr = lane >> 4, lc = lane & 15;
+      const bool wide = ep.prec == OFA_PREC_TF32;
       float factor = 0.f;
       if (EPI == EPI_GRAD) factor = 2.f * ep.amp_factor / ep.st->c_scale;
 #pragma unroll 1
@@ -392,29 +403,54 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint32_t v[32];
         if (!valid) break;
         tmem_ld32(tw + ch * 32, v);
-        if (!row_ok) continue;
         const int mbase = (n_tile * BN + ch * 32) >> 1;   // 16 pupil columns
-#pragma unroll
+        const int gm = mbase + lc;
+        __syncwarp();
+#pragma unroll 4
+        for (int it = 0; it < 16; ++it) {
+          const int row = 2 * it + lr, gn = nbase + row;
+          const bool ok = gn < ep.ny && gm < ep.nx;
+          const size_t idx = (size_t)gn * ep.nx + gm;
+          s_a[row * 17 + lc] = ok ? ep.amp[idx] : 0.f;
+          if (EPI == EPI_GRAD) s_p[row * 17 + lc] = ok ? ep.phi_in[idx] : 0.f;
+        }
+        __syncwarp();
+#pragma unroll 4
         for (int q = 0; q < 16; ++q) {
-          const int m = mbase + q;
-          if (m >= ep.nx) break;
           const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
-          const size_t idx = (size_t)n * ep.nx + m;
+          const float a = s_a[lane * 17 + q];
           if (EPI == EPI_BWD) {
-            ep.out[idx] = atan2f(im, re);                       // phi = arg(E')
-            const float a = ep.amp[idx];
-            const float r2 = re * re + im * im;
-            float er = a, ei = 0.f;                            // arg(0) = 0
-            if (r2 > 0.f) {
-              const float inv = rsqrtf(r2);
-              er = a * re * inv;
-              ei = a * im * inv;
-            }
-            split_store2(ep.prec, ep.e_hi, ep.e_lo, ((size_t)n * ep.nxp + m) * 2, er, ei);
+            // phi = arg(E') (atan2(0,0) = 0), then the next pupil field A exp(i phi),
+            // formed exactly as the field-plane builder forms it from a stored phi
+            const float ph = atan2f(im, re);
+            s_o[lane * 17 + q] = ph;
+            float sn, cs;
+            __sincosf(ph, &sn, &cs);
+            uint2 h, l;
+            split_pack(ep.prec, a * cs, a * sn, h, l);
+            s_h[lane * 17 + q] = h;
+            s_l[lane * 17 + q] = l;
           } else {
-            float s, c;
-            sincosf(ep.phi_in[idx], &s, &c);
-            ep.out[idx] = factor * ep.amp[idx] * (c * im - s * re);
+            float sn, cs;
+            sincosf(s_p[lane * 17 + q], &sn, &cs);
+            s_o[lane * 17 + q] = factor * a * (cs * im - sn * re);
+          }
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int it = 0; it < 16; ++it) {
+          const int row = 2 * it + lr, gn = nbase + row;
+          if (gn >= ep.ny || gm >= ep.nx) continue;
+          ep.out[(size_t)gn * ep.nx + gm] = s_o[row * 17 + lc];
+          if (EPI == EPI_BWD) {
+            const size_t e = (size_t)gn * ep.nxp + gm;   // complex element index
+            const uint2 h = s_h[row * 17 + lc];
+            if (wide) {
+              reinterpret_cast<uint2*>(ep.e_hi)[e] = h;
+            } else {
+              reinterpret_cast<uint32_t*>(ep.e_hi)[e] = h.x;
+              if (ep.e_lo) reinterpret_cast<uint32_t*>(ep.e_lo)[e] = s_l[row * 17 + lc].x;
+            }
           }
         }
       }

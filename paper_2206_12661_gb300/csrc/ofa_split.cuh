@@ -73,3 +73,38 @@ __device__ __forceinline__ void split_store2(int prec, void* hi, void* lo, size_
       break;
   }
 }
+
+// Bits of the complex pair (re, im) in the operand format: .x (16-bit formats:
+// both halves packed) or .x/.y (TF32); lo is zero for single-plane formats.
+__device__ __forceinline__ void split_pack(int prec, float re, float im, uint2& hi, uint2& lo) {
+  hi = make_uint2(0u, 0u);
+  lo = make_uint2(0u, 0u);
+  switch (prec) {
+    case OFA_PREC_TF32:
+      hi = make_uint2(__float_as_uint(tf32_round(re)), __float_as_uint(tf32_round(im)));
+      break;
+    case OFA_PREC_BF16: {
+      __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+      hi.x = *reinterpret_cast<uint32_t*>(&h);
+      break;
+    }
+    case OFA_PREC_BF16X3: {
+      __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+      const float2 hf = __bfloat1622float2(h);
+      __nv_bfloat162 l = __floats2bfloat162_rn(re - hf.x, im - hf.y);
+      hi.x = *reinterpret_cast<uint32_t*>(&h);
+      lo.x = *reinterpret_cast<uint32_t*>(&l);
+      break;
+    }
+    case OFA_PREC_F16X3: {
+      __half2 h = __floats2half2_rn(re, im);
+      const float2 hf = __half22float2(h);
+      __half2 l = __floats2half2_rn(re - hf.x, im - hf.y);
+      hi.x = *reinterpret_cast<uint32_t*>(&h);
+      lo.x = *reinterpret_cast<uint32_t*>(&l);
+      break;
+    }
+    default:
+      break;
+  }
+}

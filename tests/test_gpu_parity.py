@@ -165,7 +165,9 @@ def test_full_run_grid100(ofa, dev, prec):
     assert abs(st.xi - ref["xi"]) < 1e-3
     assert abs(st.uniformity - ref["uniformity"]) < 1e-3, (st.uniformity, ref["uniformity"])
     assert len(hist) == w.n_iter
-    assert np.max(np.abs(hist - ref["xi_hist"])) < 1e-3
+    # single-product forms perturb the early, fast-moving iterates more than 1e-3
+    hist_tol = 1e-3 if prec in ACCURATE else 1e-2
+    assert np.max(np.abs(hist - ref["xi_hist"])) < hist_tol
 
 
 @pytest.mark.parametrize("prec", ["f16x3", "bf16x3", "fp32", "bf16"])
