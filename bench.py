@@ -253,6 +253,7 @@ def main():
 
     # live per-kernel timing (CUDA events on the plan's stream) for the roofline
     kms = ofa.ofa_profile_kernels(plan.handle, reps=50)
+    kernel_config = ofa.ofa_plan_config(plan.handle)
     peaks, peak_src = load_peaks()
     flops_per_product = 8.0 * w.nx * w.ny * w.n_foci
     dom = int(np.argmax([kms[0], kms[3]]))
@@ -284,7 +285,8 @@ def main():
                          "foci": "Poisson disk, 3-spot min spacing, 2.0 mm ROI",
                          "l2": "flushed (256 MiB write) before every step; inputs "
                                "(about 45 MB) stay L2-resident within a step",
-                         "parallelism": f"replicas x{world}"},
+                         "parallelism": f"replicas x{world}",
+                         "kernels": kernel_config},
               "roofline": roofline, "clocks": clocks}
     kernels_per_iter = 3 if args.precision == "fp32" else 4
     result["gpu_launches"] = args.steps * (n_iter * kernels_per_iter + 1)
@@ -327,7 +329,8 @@ def main():
                 ms += e0.elapsed_time(e1)
             k = ofa.ofa_profile_kernels(p.handle, reps=10 if prec == "fp32" else 50)
             forms[prec] = {"iterations_per_s": reps * n_iter / (ms / 1000.0),
-                           "kernel_ms": [round(x, 5) for x in k]}
+                           "kernel_ms": [round(x, 5) for x in k],
+                           "kernels": ofa.ofa_plan_config(p.handle)}
             p.close()
         result["forms"] = forms
 

@@ -76,6 +76,11 @@ typedef struct ofa_options {
   int mem_space;             /* ofa_mem_space of focus_xy, target, amplitude and phi0 */
   int weighting;             /* 1 = generalized weighting of Algorithm 1 (default),
                                 0 = plain GS (w stays 1) */
+  int autotune;              /* tensor-core forms: 1 = time the candidate tile shapes,
+                                split-K factors and cluster multicast of both products
+                                at creation and keep the fastest (default; results are
+                                cached per device, size and precision for the process),
+                                0 = a static cost model */
 } ofa_options;
 
 typedef struct ofa_stats {
@@ -174,13 +179,22 @@ ofa_status ofa_adjoint(ofa_plan* plan, const float* phi, const float* theta,
  * ofa_profile_kernels -- measurement aid: average device time (ms) of each kernel
  * of one loop iteration, each launched `reps` (>= 1) times back to back on the
  * plan's stream between CUDA events, after one untimed launch:
- *   ms_out[0] forward product (+ per-focus dot), ms_out[1] focal statistics and
- *   weight update, ms_out[2] inverse left-operand build (0 for OFA_PREC_FP32),
- *   ms_out[3] inverse product (+ phase projection).
+ *   ms_out[0] forward product (+ per-focus dot; in the tensor-core forms also the
+ *   focal statistics and weight update, which run in its last CTA), ms_out[1] focal
+ *   statistics and weight update as a separate kernel (0 for the tensor-core forms),
+ *   ms_out[2] inverse left-operand build (0 for OFA_PREC_FP32), ms_out[3] inverse
+ *   product (+ phase projection).
  * The loop state (phi, w, j, xi history) is saved before and restored after, so
  * the call does not change the result of later iterations.  Synchronises.
  */
 ofa_status ofa_profile_kernels(ofa_plan* plan, int reps, double* ms_out);
+
+/* Kernel configuration chosen at creation (host output, 10 ints): forward tile width
+ * (accumulator columns), forward split-K factor, forward cluster shape x and y,
+ * inverse tile width, inverse cluster shape x and y, 1 if the focal step runs in the
+ * forward kernel's last CTA, forward and inverse operand row width per pipeline stage
+ * (bytes of K: 128 or 64).  The FP32 form reports zeros. */
+ofa_status ofa_plan_config(const ofa_plan* plan, int* config_out);
 
 /* Problem sizes of a plan (any output may be NULL). */
 ofa_status ofa_plan_info(const ofa_plan* plan, int* nx, int* ny, int* n_foci, int* precision);

@@ -15,6 +15,7 @@
 #include <math_constants.h>
 
 #include "ofa_internal.cuh"
+#include "ofa_focal.cuh"
 #include "ofa_split.cuh"
 
 namespace {
@@ -211,6 +212,39 @@ __global__ void __launch_bounds__(FT) focal_kernel(
   }
 }
 
+// One loop iteration (mode 0): Theta_k from the per-tile partials (fixed order),
+// then the shared focal routine of ofa_focal.cuh on 1024 threads.
+__global__ void __launch_bounds__(FT) focal_iter_kernel(
+    const float2* __restrict__ part, int n_part, int kp, int K, const float* __restrict__ t,
+    float* __restrict__ w, float2* __restrict__ theta, float2* __restrict__ c,
+    double* __restrict__ hist, OfaDevState* __restrict__ st, int weighting) {
+  __shared__ float sh[4 * 33];
+  if (st->done) return;
+  for (int k = threadIdx.x; k < K; k += FT) {
+    float2 a = make_float2(0.f, 0.f);
+    for (int p = 0; p < n_part; ++p) {
+      const float2 v = part[(size_t)p * kp + k];
+      a.x += v.x;
+      a.y += v.y;
+    }
+    theta[k] = a;
+  }
+  __syncthreads();
+  ofa_focal::iterate<FT>(theta, K, kp, t, w, c, hist, st, weighting, sh, (int)threadIdx.x,
+                         ofa_focal::BarBlock());
+}
+
+// Mode 0 for K <= 4096: everything from registers (ofa_focal::iterate_regs).
+__global__ void __launch_bounds__(FT) focal_regs_kernel(
+    const float2* __restrict__ part, int n_part, int kp, int K, const float* __restrict__ t,
+    float* __restrict__ w, float2* __restrict__ c, double* __restrict__ hist,
+    OfaDevState* __restrict__ st, int weighting) {
+  __shared__ float sh[4 * 33];
+  if (st->done) return;
+  ofa_focal::iterate_regs<FT, 4>(part, n_part, K, kp, t, w, c, hist, st, weighting, sh,
+                                 (int)threadIdx.x, ofa_focal::BarBlock());
+}
+
 __global__ void control_kernel(OfaDevState* st, double thr, int reset_done) {
   st->threshold = thr;
   if (reset_done) st->done = 0;
@@ -249,18 +283,43 @@ __global__ void __launch_bounds__(FT) grad_c_kernel(const float2* __restrict__ t
   if (threadIdx.x == 0) st->c_scale = scale;
 }
 
-// P[n][2k..2k+1] = conj(Fy[k,n]) c_k in the operand format of the precision.
+// P[n][2k..2k+1] = conj(Fy[k,n]) c_k in the operand format of the precision;
+// four foci per thread (kp is a multiple of 128): 16-byte loads and stores.
 __global__ void build_p_kernel(const float2* __restrict__ fyT, const float2* __restrict__ c,
                                const int* __restrict__ done, int nyp, int kp, int prec, void* hi,
                                void* lo) {
+  // programmatic dependent launch: schedule the inverse product now, then wait
+  // for the forward kernel (which produced c) to complete
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (done != nullptr && *done) return;
-  const size_t total = (size_t)nyp * kp;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+  const size_t quads = (size_t)nyp * kp / 4;
+  const bool wide = prec == OFA_PREC_TF32;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < quads;
        i += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(i % kp);
-    const float2 f = fyT[i];
-    const float2 ck = c[k];
-    split_store2(prec, hi, lo, 2 * i, f.x * ck.x + f.y * ck.y, f.x * ck.y - f.y * ck.x);
+    const size_t e0 = 4 * i;                 // first complex element
+    const int k0 = (int)(e0 % kp);
+    const float4 f01 = __ldg(reinterpret_cast<const float4*>(fyT + e0));
+    const float4 f23 = __ldg(reinterpret_cast<const float4*>(fyT + e0) + 1);
+    const float4 c01 = __ldg(reinterpret_cast<const float4*>(c + k0));
+    const float4 c23 = __ldg(reinterpret_cast<const float4*>(c + k0) + 1);
+    const float fr[4] = {f01.x, f01.z, f23.x, f23.z}, fi[4] = {f01.y, f01.w, f23.y, f23.w};
+    const float cr[4] = {c01.x, c01.z, c23.x, c23.z}, ci[4] = {c01.y, c01.w, c23.y, c23.w};
+    uint2 h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      split_pack(prec, fr[j] * cr[j] + fi[j] * ci[j], fr[j] * ci[j] - fi[j] * cr[j], h[j], l[j]);
+    if (wide) {
+      uint4* dst = reinterpret_cast<uint4*>(static_cast<float*>(hi) + 2 * e0);
+      dst[0] = make_uint4(h[0].x, h[0].y, h[1].x, h[1].y);
+      dst[1] = make_uint4(h[2].x, h[2].y, h[3].x, h[3].y);
+    } else {
+      reinterpret_cast<uint4*>(static_cast<uint16_t*>(hi) + 2 * e0)[0] =
+          make_uint4(h[0].x, h[1].x, h[2].x, h[3].x);
+      if (lo != nullptr)
+        reinterpret_cast<uint4*>(static_cast<uint16_t*>(lo) + 2 * e0)[0] =
+            make_uint4(l[0].x, l[1].x, l[2].x, l[3].x);
+    }
   }
 }
 
@@ -269,6 +328,15 @@ __global__ void build_p_kernel(const float2* __restrict__ fyT, const float2* __r
 void launch_focal(const float2* part, int n_part, int kp, int K, const float* t, float* w,
                   float2* theta, float* inten, float2* c, double* hist, OfaDevState* st, int mode,
                   int weighting, float out_scale, double energy, cudaStream_t s) {
+  if (mode == 0 && K <= 4 * FT) {
+    focal_regs_kernel<<<1, FT, 0, s>>>(reinterpret_cast<const float2*>(part), n_part, kp, K, t,
+                                       w, c, hist, st, weighting);
+    return;
+  }
+  if (mode == 0) {
+    focal_iter_kernel<<<1, FT, 0, s>>>(part, n_part, kp, K, t, w, theta, c, hist, st, weighting);
+    return;
+  }
   focal_kernel<<<1, FT, 0, s>>>(part, n_part, kp, K, t, w, theta, inten, c, hist, st, mode,
                                 weighting, out_scale, energy);
 }
@@ -288,8 +356,17 @@ void launch_grad_c(const float2* theta, const float* g, int K, int kp, float in_
 
 void launch_build_p(const float2* fyT, const float2* c, const int* done, int nyp, int kp,
                     int prec, void* hi, void* lo, cudaStream_t s) {
-  const size_t total = (size_t)nyp * kp;
+  const size_t total = (size_t)nyp * kp / 4;
   size_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  build_p_kernel<<<(int)blocks, 256, 0, s>>>(fyT, c, done, nyp, kp, prec, hi, lo);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, build_p_kernel, fyT, c, done, nyp, kp, prec, hi, lo);
 }

@@ -12,6 +12,7 @@
 // Both are 64 x 64 complex tiles, 256 threads, 4 x 4 complex accumulators per
 // thread, 16-deep steps staged through shared memory with register prefetch.
 #include "ofa_internal.cuh"
+#include "ofa_math.cuh"
 
 namespace {
 
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(256) bwd_simt_kernel(
     for (int j = 0; j < 4; ++j) {
       const int m = m0 + tx * 4 + j;
       if (EPI == 0) {
-        v[j] = atan2f(acc[i][j].y, acc[i][j].x);
+        v[j] = ofa_arg(acc[i][j].y, acc[i][j].x);
       } else if (m < nx) {
         float s, cc;
         sincosf(phi_in[(size_t)n * nx + m], &s, &cc);

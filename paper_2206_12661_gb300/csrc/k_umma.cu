@@ -19,26 +19,71 @@
 //   BWD   phi = arg(E') and the next pupil field A exp(i phi) in operand format
 //   GRAD  2 A Im(exp(-i phi) B) for the adjoint
 //
-// Warp roles (192 threads): warps 0-3 epilogue (TMEM lanes 32w..32w+31),
-// warp 4 TMA producer, warp 5 TMEM allocator + MMA issuer.  Every mbarrier
+// Warp roles (320 threads): warps 0-7 epilogue (warp w reads TMEM lanes
+// 32*(w%4).. and column half w/4; each prefetches its epilogue inputs into
+// registers while the mainloop runs), warp 8 TMA producer, warp 9 TMEM
+// allocator + MMA issuer.  Every mbarrier
 // wait is bounded (one second of %globaltimer); a wait that gives up
 // raises OFA_ERRBIT_TIMEOUT and the CTA drains and frees TMEM before exiting.
 #include <cudaTypedefs.h>
 
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <type_traits>
 
 #include "ofa_internal.cuh"
+#ifdef OFA_PHASE_TRACE
+__device__ unsigned long long g_phase_trace[2][1024][16];
+#define OFA_FOCAL_STAMP(slot)                                                        \
+  do {                                                                               \
+    unsigned long long t_;                                                           \
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                           \
+    const int lin_ = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); \
+    if (lin_ < 1024) g_phase_trace[0][lin_][slot] = t_;                              \
+  } while (0)
+#endif
+#include "ofa_focal.cuh"
+#include "ofa_math.cuh"
 #include "ofa_split.cuh"
 
 namespace {
 
 constexpr int BM = 128;
-constexpr int NTHREADS = 192;
-constexpr int ROW_BYTES = 128;            // one 128B-swizzle row per operand row per stage
+// Epilogue warps: 8 (two per TMEM lane quarter) for the forward, 16 (four per
+// quarter) for the inverse, whose per-pixel epilogue needs more latency hiding.
+// The two warps after them are the TMA producer and the MMA issuer.
+template <int EPI> struct Warps {
+  static constexpr int EPI_THREADS = EPI == 0 ? 256 : 512;
+  static constexpr int TMA = EPI_THREADS / 32;
+  static constexpr int MMA = TMA + 1;
+  static constexpr int THREADS = EPI_THREADS + 64;
+};
+constexpr int NUM_EPI_THREADS = 256;  // forward epilogue (the fused focal step runs on these)
+// Operand rows per stage are RB = 128 or 64 bytes of K (128B or 64B swizzle).
 constexpr int SMEM_BUDGET = 200 * 1024;   // operand stages
 constexpr uint64_t WAIT_NS = 1000000000ull;
 
 enum { EPI_FWD = 0, EPI_BWD = 1, EPI_GRAD = 2 };
+
+#ifdef OFA_PHASE_TRACE
+// Diagnostic build only: per-CTA %globaltimer stamps of the kernel phases
+// (entry, setup done, first TMA issued, first MMA issued, last MMA issued,
+// accumulator ready, epilogue done, exit; 8-15: inside the epilogue of warp 0,
+// and in the forward the focal tail) of the most recent launch.
+#define OFA_STAMP(slot)                                                            \
+  do {                                                                             \
+    const int lin_ = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); \
+    if (lin_ < 1024) g_phase_trace[EPI == EPI_FWD ? 0 : 1][lin_][slot] = gtimer();  \
+  } while (0)
+#else
+#define OFA_STAMP(slot) \
+  do {                  \
+  } while (0)
+#endif
 enum { KIND_F16 = 0, KIND_BF16 = 1, KIND_TF32 = 2 };
 
 struct EpiArgs {
@@ -58,6 +103,19 @@ struct EpiArgs {
   float amp_factor;
   const OfaDevState* st;
   int* err;
+  // forward with the focal step fused into its last CTA (fuse != 0)
+  int fuse;
+  unsigned int* counters;  // [n_tiles + 1], zero between launches
+  int n_tiles;             // forward grid.x
+  int n_part;              // partial rows = tiles_m * splits
+  int K;
+  float2* theta;           // [K] final Theta
+  const float* t;
+  float* w;
+  float2* c;
+  double* hist;
+  OfaDevState* stw;
+  int weighting;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -108,9 +166,35 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
       : "memory");
 }
+// Multicast form: the tile lands at the same shared-memory offset in every CTA of
+// cta_mask and signals the barrier at the same offset in each of them.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                               int x, int y, uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(cta_mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" :::
+               "memory");
+}
 __device__ __forceinline__ void tmap_prefetch(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
+// Programmatic dependent launch: let the next kernel of the stream be scheduled
+// now, and (separately) wait until the previous kernel has completed and its
+// memory is visible.  Both are no-ops for launches without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -149,6 +233,14 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
       : "memory");
 }
+// Arrive on the barrier at this offset in every CTA of cta_mask once all prior
+// tcgen05 operations of this thread have completed.
+__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar), "h"(cta_mask)
+      : "memory");
+}
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -164,16 +256,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row core-matrix groups 1024 bytes apart (SBO), LBO unused (1),
-// descriptor version 1 (bits 46-48), swizzle mode 2 = 128B (bits 61-63).
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major operand tile whose rows are RB
+// bytes (RB = 128: 128-byte swizzle, mode 2; RB = 64: 64-byte swizzle, mode 4;
+// bits 61-63), 8-row core-matrix groups 8*RB bytes apart (SBO, bits 32-45),
+// LBO unused (1), descriptor version 1 (bits 46-48).
+template <int RB>
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)((8 * RB) >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)(RB == 128 ? 2 : 4) << 61;
   return d;
 }
 
@@ -203,19 +297,24 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
 }
 
 __device__ __forceinline__ void named_bar_epi() {
-  asm volatile("bar.sync 1, 128;" ::: "memory");
+  asm volatile("bar.sync 1, 256;" ::: "memory");
 }
+struct BarEpi {
+  __device__ __forceinline__ void operator()() const { named_bar_epi(); }
+};
 
-template <int KIND, int NPASS, int BN, int EPI>
+template <int KIND, int NPASS, int BN, int EPI, int RB>
 struct Cfg {
   static constexpr int EB = KIND == KIND_TF32 ? 4 : 2;
-  static constexpr int BK = ROW_BYTES / EB;               // elements per stage
+  static constexpr int BK = RB / EB;                      // elements of K per stage
   static constexpr int PLANES = NPASS == 3 ? 2 : 1;
-  static constexpr int A_BYTES = BM * ROW_BYTES;          // 16 KB
-  static constexpr int B_BYTES = BN * ROW_BYTES;          // 16 or 32 KB
+  static constexpr int A_BYTES = BM * RB;
+  static constexpr int B_BYTES = BN * RB;
   static constexpr int STAGE_BYTES = PLANES * (A_BYTES + B_BYTES);
-  static constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES > 8 ? 8 : SMEM_BUDGET / STAGE_BYTES;
-  static constexpr int UMMA_K_STEPS = 4;                  // 32 bytes of K per MMA
+  static constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES > 12 ? 12 : SMEM_BUDGET / STAGE_BYTES;
+  // the inverse epilogue stages its output through 16 x 11 KB of the freed stages
+  static_assert(EPI == 0 || STAGES * STAGE_BYTES >= 16 * 11264, "epilogue staging");
+  static constexpr int UMMA_K_STEPS = RB / 32;            // 32 bytes of K per MMA
   static constexpr int RED_BYTES = EPI == EPI_FWD ? 4 * BN * 4 : 0;
   static constexpr int BAR_OFF = STAGES * STAGE_BYTES + RED_BYTES;
   static constexpr int SMEM = BAR_OFF + 256 + 1024;        // barriers, slot, alignment
@@ -223,16 +322,19 @@ struct Cfg {
   static_assert(STAGES >= 2, "need at least two stages");
 };
 
-template <int KIND, int NPASS, int BN, int EPI>
-__global__ void __launch_bounds__(NTHREADS, 1)
+template <int KIND, int NPASS, int BN, int EPI, int RB>
+__global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tma_hi,
                      const __grid_constant__ CUtensorMap tma_lo,
                      const __grid_constant__ CUtensorMap tmb_hi,
                      const __grid_constant__ CUtensorMap tmb_lo, int kb_per_split, int kb_total,
-                     EpiArgs ep, const int* __restrict__ done) {
-  using C = Cfg<KIND, NPASS, BN, EPI>;
-  if (done != nullptr && *done) return;
-  if (*ep.err & OFA_ERRBIT_TIMEOUT) return;  // an earlier launch already gave up
+                     EpiArgs ep, const int* __restrict__ done, int ccx, int ccy) {
+  using C = Cfg<KIND, NPASS, BN, EPI, RB>;
+  constexpr int WARP_TMA = Warps<EPI>::TMA, WARP_MMA = Warps<EPI>::MMA;
+  constexpr int GROUPS = Warps<EPI>::EPI_THREADS / 128;   // epilogue warps per lane quarter
+  constexpr int CPW = BN / (32 * GROUPS);                  // 32-column chunks per epilogue warp
+  if (threadIdx.x == 0) OFA_STAMP(0);
+  pdl_launch_dependents();  // the next kernel may start its own set-up on free SMs
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base_u32 = (raw + 1023u) & ~1023u;
@@ -247,19 +349,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t bar_empty = bar_full + 8 * C::STAGES;      // STAGES x 8 bytes
   const uint32_t bar_accum = bar_empty + 8 * C::STAGES;     // 8 bytes
   const uint32_t slot_u32 = bar_accum + 8;                  // TMEM address slot
-  volatile uint32_t* slot = reinterpret_cast<volatile uint32_t*>(base + C::BAR_OFF + 16 * C::STAGES + 8);
-  __shared__ int abort_flag;
+  volatile uint32_t* slot =
+      reinterpret_cast<volatile uint32_t*>(base + C::BAR_OFF + 16 * C::STAGES + 8);
 
+  // Cluster (ccx x ccy CTAs, ccx along the output columns, ccy along the rows):
+  // CTAs of one cluster row share the A tile, CTAs of one cluster column the B
+  // tile; each loads a 1/ccx slice of A and a 1/ccy slice of B and multicasts it.
+  const bool clustered = (ccx * ccy) > 1;
+  const int crank = clustered ? (int)cluster_ctarank() : 0;
+  const int cx = crank % ccx, cy = crank / ccx;
+  uint16_t row_mask = 0, col_mask = 0;
+  for (int i = 0; i < ccx; ++i) row_mask |= (uint16_t)(1u << (i + cy * ccx));
+  for (int i = 0; i < ccy; ++i) col_mask |= (uint16_t)(1u << (cx + i * ccx));
   if (threadIdx.x == 0) {
-    abort_flag = 0;
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(bar_full + 8 * s, 1);
-      mbar_init(bar_empty + 8 * s, 1);
+      // every CTA that writes into this CTA's stages must have consumed them
+      mbar_init(bar_empty + 8 * s, ccx + ccy - 1);
     }
     mbar_init(bar_accum, 1);
     fence_mbar_init();
   }
-  if (warp == 4 && lane == 0) {
+  if (warp == WARP_TMA && lane == 0) {
     tmap_prefetch(&tma_hi);
     tmap_prefetch(&tmb_hi);
     if (NPASS == 3) {
@@ -267,13 +378,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tmap_prefetch(&tmb_lo);
     }
   }
-  if (warp == 5) tmem_alloc(slot_u32, BN);
+  if (warp == WARP_MMA) tmem_alloc(slot_u32, BN);
   tc_fence_before();
-  __syncthreads();
+  if (clustered) cluster_sync_all();  // partners' barriers exist before any multicast
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
+  // Everything above is independent of the previous kernel; from here on its
+  // outputs (the dynamic operand, the loop flags) are read.
+  pdl_wait();
+  // skip: the loop already stopped, or an earlier launch gave up (uniform over the grid)
+  const bool skip = (done != nullptr && *done) || (*ep.err & OFA_ERRBIT_TIMEOUT);
+  if (threadIdx.x == 0) OFA_STAMP(1);
 
-  if (warp == 4) {
+  if (skip) {
+    // nothing to compute; fall through to the teardown
+  } else if (warp == WARP_TMA) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       int issued = 0;
@@ -288,20 +408,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         const uint32_t st = base_u32 + s * C::STAGE_BYTES;
         const int x = (kb0 + kb) * C::BK;
-        mbar_expect_tx(bar_full + 8 * s, C::STAGE_BYTES);
-        tma_load_2d(st, &tma_hi, bar_full + 8 * s, x, m_tile * BM);
-        tma_load_2d(st + C::PLANES * C::A_BYTES, &tmb_hi, bar_full + 8 * s, x, n_tile * BN);
-        if (NPASS == 3) {
-          tma_load_2d(st + C::A_BYTES, &tma_lo, bar_full + 8 * s, x, m_tile * BM);
-          tma_load_2d(st + C::PLANES * C::A_BYTES + C::B_BYTES, &tmb_lo, bar_full + 8 * s, x,
-                      n_tile * BN);
+        mbar_expect_tx(bar_full + 8 * s, C::STAGE_BYTES);  // whole stage, all sources
+        if (!clustered) {
+          tma_load_2d(st, &tma_hi, bar_full + 8 * s, x, m_tile * BM);
+          tma_load_2d(st + C::PLANES * C::A_BYTES, &tmb_hi, bar_full + 8 * s, x, n_tile * BN);
+          if (NPASS == 3) {
+            tma_load_2d(st + C::A_BYTES, &tma_lo, bar_full + 8 * s, x, m_tile * BM);
+            tma_load_2d(st + C::PLANES * C::A_BYTES + C::B_BYTES, &tmb_lo, bar_full + 8 * s, x,
+                        n_tile * BN);
+          }
+        } else {
+          const int ar = BM / ccx, br = BN / ccy;   // slice rows
+          const uint32_t ao = (uint32_t)(cx * ar * RB), bo = (uint32_t)(cy * br * RB);
+          tma_load_2d_mc(st + ao, &tma_hi, bar_full + 8 * s, x, m_tile * BM + cx * ar, row_mask);
+          tma_load_2d_mc(st + C::PLANES * C::A_BYTES + bo, &tmb_hi, bar_full + 8 * s, x,
+                         n_tile * BN + cy * br, col_mask);
+          if (NPASS == 3) {
+            tma_load_2d_mc(st + C::A_BYTES + ao, &tma_lo, bar_full + 8 * s, x,
+                           m_tile * BM + cx * ar, row_mask);
+            tma_load_2d_mc(st + C::PLANES * C::A_BYTES + C::B_BYTES + bo, &tmb_lo,
+                           bar_full + 8 * s, x, n_tile * BN + cy * br, col_mask);
+          }
         }
+        if (issued == 0) OFA_STAMP(2);
         ++issued;
       }
-      if (!ok) {
-        atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
-        abort_flag = 1;
-      }
+      if (!ok) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
       // Drain: every issued copy must have landed before the CTA may exit.
       for (int kb = max(0, issued - C::STAGES); kb < issued; ++kb)
         if (!mbar_wait(bar_full + 8 * (kb % C::STAGES), (kb / C::STAGES) & 1)) {
@@ -309,7 +441,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
     }
-  } else if (warp == 5) {
+  } else if (warp == WARP_MMA) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       bool ok = true;
@@ -321,50 +453,63 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         tc_fence_after();
         const uint32_t st = base_u32 + s * C::STAGE_BYTES;
-        const uint64_t a_hi = sdesc_sw128(st);
-        const uint64_t a_lo = sdesc_sw128(st + C::A_BYTES);
-        const uint64_t b_hi = sdesc_sw128(st + C::PLANES * C::A_BYTES);
-        const uint64_t b_lo = sdesc_sw128(st + C::PLANES * C::A_BYTES + C::B_BYTES);
+        const uint64_t a_hi = sdesc<RB>(st);
+        const uint64_t a_lo = sdesc<RB>(st + C::A_BYTES);
+        const uint64_t b_hi = sdesc<RB>(st + C::PLANES * C::A_BYTES);
+        const uint64_t b_lo = sdesc<RB>(st + C::PLANES * C::A_BYTES + C::B_BYTES);
 #pragma unroll
         for (int kk = 0; kk < C::UMMA_K_STEPS; ++kk) {
           const uint64_t adv = (uint64_t)((kk * 32) >> 4);  // 32 bytes of K per MMA
+          if ((kb | kk) == 0) OFA_STAMP(3);
           umma<KIND>(tmem, a_hi + adv, b_hi + adv, C::IDESC, (kb | kk) != 0);
           if (NPASS == 3) {
             umma<KIND>(tmem, a_hi + adv, b_lo + adv, C::IDESC, 1);
             umma<KIND>(tmem, a_lo + adv, b_hi + adv, C::IDESC, 1);
           }
         }
-        umma_commit(bar_empty + 8 * s);  // stage free once these MMAs have read it
+        // stage free (in this CTA and for every CTA that writes into it) once
+        // these MMAs have read it
+        if (clustered) umma_commit_mc(bar_empty + 8 * s, (uint16_t)(row_mask | col_mask));
+        else umma_commit(bar_empty + 8 * s);
       }
-      if (!ok) {
-        atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
-        abort_flag = 1;
-      }
+      if (!ok) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
+      OFA_STAMP(4);
       umma_commit(bar_accum);  // accumulator complete (or drained, on abort)
     }
   } else {
-    // ------------------------------------------------------------ epilogue
-    const bool ready = mbar_wait(bar_accum, 0);
-    tc_fence_after();
-    if (!ready) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
-    const bool valid = ready && nkb > 0;
-    const int r = warp * 32 + lane;               // accumulator row = TMEM lane
-    const int n = m_tile * BM + r;                // pupil row
-    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+    // ------------------------------------------------------------ epilogue warps
+    // warp w reads TMEM lanes 32*(w%4).. (rows of the tile) and column group w/4.
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;             // accumulator row = TMEM lane
+    const int n = m_tile * BM + r;                 // pupil row
+    const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int col0 = half * CPW * 32;              // first accumulator column of this warp
 
     if (EPI == EPI_FWD) {
+      // Prefetch this row's Fy values for the warp's foci while the mainloop runs.
+      float4 fy[CPW][8];
+      const float4* fr = reinterpret_cast<const float4*>(
+          ep.fyT + (size_t)n * ep.kp + ((n_tile * BN + col0) >> 1));
+#pragma unroll
+      for (int c = 0; c < CPW; ++c)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) fy[c][q] = __ldg(fr + c * 8 + q);
+      const bool ready = mbar_wait(bar_accum, 0);
+      tc_fence_after();
+      if (threadIdx.x == 0) OFA_STAMP(5);
+      if (!ready) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
+      const bool valid = ready && nkb > 0;
       float* red = reinterpret_cast<float*>(base + C::STAGES * C::STAGE_BYTES);
-#pragma unroll 1
-      for (int ch = 0; ch < BN / 32; ++ch) {
+#pragma unroll
+      for (int c = 0; c < CPW; ++c) {
+        const int ch = half * CPW + c;
         uint32_t v[32];
         float p[32];
         if (valid) {
           tmem_ld32(tw + ch * 32, v);
-          const int kbase = (n_tile * BN + ch * 32) >> 1;   // 16 foci in this chunk
-          const float4* fr = reinterpret_cast<const float4*>(ep.fyT + (size_t)n * ep.kp + kbase);
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const float4 f = __ldg(fr + q);
+            const float4 f = fy[c][q];
             const float g0r = __uint_as_float(v[4 * q]), g0i = __uint_as_float(v[4 * q + 1]);
             const float g1r = __uint_as_float(v[4 * q + 2]), g1i = __uint_as_float(v[4 * q + 3]);
             p[4 * q] = f.x * g0r - f.y * g0i;
@@ -376,53 +521,104 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int q = 0; q < 32; ++q) p[q] = 0.f;
         }
-        red[warp * BN + ch * 32 + lane] = warp_reduce_scatter32(p);
+        red[quarter * BN + ch * 32 + lane] = warp_reduce_scatter32(p);
       }
       named_bar_epi();
-      const int t = threadIdx.x;  // 0..127
+      const int t = threadIdx.x;  // 0..255
       float* dst = ep.part + (size_t)(split * ep.tiles_m + m_tile) * 2 * ep.kp + n_tile * BN;
-      for (int col = t; col < BN; col += 128)
+      for (int col = t; col < BN; col += NUM_EPI_THREADS)
         dst[col] = ((red[col] + red[BN + col]) + red[2 * BN + col]) + red[3 * BN + col];
+      if (ep.fuse) {
+        // The last CTA to finish runs the focal step of the loop on the partials
+        // of every tile (summed in fixed order, so the result does not depend on
+        // which CTA finishes last).
+        __shared__ int tail_flag;
+        __shared__ float focal_sh[4 * 33];
+        if (t == 0) OFA_STAMP(8);
+        named_bar_epi();  // every partial of this CTA is written (CTA scope) ...
+        if (t == 0) {
+          __threadfence();  // ... and, cumulatively, visible GPU-wide before the arrival
+          const unsigned prev = atomicAdd(ep.counters, 1u);
+          tail_flag = prev == (unsigned)(gridDim.x * gridDim.y * gridDim.z - 1);
+          if (tail_flag) {
+            __threadfence();  // acquire the other CTAs' partials
+            *ep.counters = 0u;
+          }
+        }
+        named_bar_epi();
+        if (t == 0) OFA_STAMP(9);
+        if (tail_flag) {
+          const float2* pt = reinterpret_cast<const float2*>(ep.part);
+          if (ep.K <= NUM_EPI_THREADS * 4)
+            ofa_focal::iterate_regs<NUM_EPI_THREADS, 4>(pt, ep.n_part, ep.K, ep.kp, ep.t, ep.w,
+                                                        ep.c, ep.hist, ep.stw, ep.weighting,
+                                                        focal_sh, t, BarEpi());
+          else
+            ofa_focal::iterate_regs<NUM_EPI_THREADS, 16>(pt, ep.n_part, ep.K, ep.kp, ep.t, ep.w,
+                                                         ep.c, ep.hist, ep.stw, ep.weighting,
+                                                         focal_sh, t, BarEpi());
+        }
+      }
     } else {
-      // Per-pixel work (thread = row); global loads and stores are staged through
-      // shared memory (the operand stages are free once the accumulator is
-      // complete) so that every warp-wide access covers whole 64-byte row segments.
-      uint8_t* wb = base + warp * 16384;
-      float* s_a = reinterpret_cast<float*>(wb);      // [32][17] amplitude
-      float* s_p = s_a + 32 * 17;                     // [32][17] phase in (gradient)
-      float* s_o = s_p + 32 * 17;                     // [32][17] phase / gradient out
-      uint2* s_h = reinterpret_cast<uint2*>(s_o + 32 * 17);  // [32][17] field, hi bits
-      uint2* s_l = s_h + 32 * 17;                     // [32][17] field, lo bits
-      const int nbase = m_tile * BM + warp * 32;
+      // Per-pixel work (thread = row).  Inputs are prefetched into registers while
+      // the mainloop runs; outputs are staged through shared memory (free once the
+      // accumulator is complete) so every warp store covers whole row segments.
+      const int m0 = (n_tile * BN + col0) >> 1;    // first pupil column of this warp
+      const bool row_ok = n < ep.ny;
+      if (threadIdx.x == 0) OFA_STAMP(14);
+      float av[CPW * 16];
+      float pv[EPI == EPI_GRAD ? CPW * 16 : 1];
+      {
+        const size_t rb = (size_t)n * ep.nx;
+        const bool vec = ((ep.nx & 3) == 0) && row_ok && (m0 + CPW * 16 <= ep.nx);
+        if (vec) {
+#pragma unroll
+          for (int j = 0; j < CPW * 4; ++j) {
+            const float4 a4 = __ldg(reinterpret_cast<const float4*>(ep.amp + rb + m0) + j);
+            av[4 * j] = a4.x; av[4 * j + 1] = a4.y; av[4 * j + 2] = a4.z; av[4 * j + 3] = a4.w;
+            if (EPI == EPI_GRAD) {
+              const float4 p4 = __ldg(reinterpret_cast<const float4*>(ep.phi_in + rb + m0) + j);
+              pv[4 * j] = p4.x; pv[4 * j + 1] = p4.y; pv[4 * j + 2] = p4.z; pv[4 * j + 3] = p4.w;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < CPW * 16; ++j) {
+            const bool ok = row_ok && (m0 + j) < ep.nx;
+            av[j] = ok ? __ldg(ep.amp + rb + m0 + j) : 0.f;
+            if (EPI == EPI_GRAD) pv[j] = ok ? __ldg(ep.phi_in + rb + m0 + j) : 0.f;
+          }
+        }
+      }
+      const bool ready = mbar_wait(bar_accum, 0);
+      tc_fence_after();
+      if (threadIdx.x == 0) OFA_STAMP(5);
+      if (!ready) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
+      const bool valid = ready && nkb > 0;
+      uint8_t* wb = base + warp * 11264;   // 16 warps x 11 KB of the freed stages
+      float* s_o = reinterpret_cast<float*>(wb);                 // [32][17] phase / gradient
+      uint2* s_h = reinterpret_cast<uint2*>(wb + 32 * 17 * 4 + 16);  // [32][17] field, hi bits
+      uint2* s_l = s_h + 32 * 17;                                // [32][17] field, lo bits
+      const int nbase = m_tile * BM + quarter * 32;
       const int lr = lane >> 4, lc = lane & 15;
       const bool wide = ep.prec == OFA_PREC_TF32;
       float factor = 0.f;
       if (EPI == EPI_GRAD) factor = 2.f * ep.amp_factor / ep.st->c_scale;
-#pragma unroll 1
-      for (int ch = 0; ch < BN / 32; ++ch) {
-        uint32_t v[32];
+#pragma unroll
+      for (int c = 0; c < CPW; ++c) {
         if (!valid) break;
+        const int ch = half * CPW + c;
+        uint32_t v[32];
         tmem_ld32(tw + ch * 32, v);
-        const int mbase = (n_tile * BN + ch * 32) >> 1;   // 16 pupil columns
-        const int gm = mbase + lc;
-        __syncwarp();
-#pragma unroll 4
-        for (int it = 0; it < 16; ++it) {
-          const int row = 2 * it + lr, gn = nbase + row;
-          const bool ok = gn < ep.ny && gm < ep.nx;
-          const size_t idx = (size_t)gn * ep.nx + gm;
-          s_a[row * 17 + lc] = ok ? ep.amp[idx] : 0.f;
-          if (EPI == EPI_GRAD) s_p[row * 17 + lc] = ok ? ep.phi_in[idx] : 0.f;
-        }
-        __syncwarp();
-#pragma unroll 4
+        if (threadIdx.x == 0 && c < 2) OFA_STAMP(8 + 3 * c);
+#pragma unroll
         for (int q = 0; q < 16; ++q) {
           const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
-          const float a = s_a[lane * 17 + q];
+          const float a = av[c * 16 + q];
           if (EPI == EPI_BWD) {
             // phi = arg(E') (atan2(0,0) = 0), then the next pupil field A exp(i phi),
             // formed exactly as the field-plane builder forms it from a stored phi
-            const float ph = atan2f(im, re);
+            const float ph = ofa_arg(im, re);
             s_o[lane * 17 + q] = ph;
             float sn, cs;
             __sincosf(ph, &sn, &cs);
@@ -432,11 +628,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             s_l[lane * 17 + q] = l;
           } else {
             float sn, cs;
-            sincosf(s_p[lane * 17 + q], &sn, &cs);
+            sincosf(pv[c * 16 + q], &sn, &cs);
             s_o[lane * 17 + q] = factor * a * (cs * im - sn * re);
           }
         }
         __syncwarp();
+        if (threadIdx.x == 0 && c < 2) OFA_STAMP(9 + 3 * c);
+        const int gm = m0 + c * 16 + lc;
 #pragma unroll 4
         for (int it = 0; it < 16; ++it) {
           const int row = 2 * it + lr, gn = nbase + row;
@@ -453,17 +651,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           }
         }
+        __syncwarp();
+        if (threadIdx.x == 0 && c < 2) OFA_STAMP(10 + 3 * c);
       }
     }
   }
 
   // ------------------------------------------------------------ teardown
+  if (threadIdx.x == 0) OFA_STAMP(6);
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) {
+  if (warp == WARP_MMA) {
     tc_fence_after();
     tmem_dealloc(tmem, BN);
   }
+  // No CTA may leave while a partner can still multicast into its shared memory
+  // or arrive on its barriers.
+  if (clustered) cluster_sync_all();
+  if (threadIdx.x == 0) OFA_STAMP(7);
 }
 
 // ------------------------------------------------------------------ host side
@@ -481,7 +686,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 bool encode(CUtensorMap* m, void* ptr, int elem_bytes, uint64_t cols, uint64_t rows,
-            uint32_t box_rows, std::string& err) {
+            uint32_t box_rows, int rb, std::string& err) {
   auto fn = encode_fn();
   if (fn == nullptr) {
     err = "cuTensorMapEncodeTiled is not available from the driver";
@@ -491,11 +696,11 @@ bool encode(CUtensorMap* m, void* ptr, int elem_bytes, uint64_t cols, uint64_t r
       elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
   cuuint64_t dims[2] = {cols, rows};
   cuuint64_t strides[1] = {cols * (cuuint64_t)elem_bytes};
-  cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / elem_bytes), box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)(rb / elem_bytes), box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, dt, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  rb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     err = "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r);
     return false;
@@ -503,62 +708,97 @@ bool encode(CUtensorMap* m, void* ptr, int elem_bytes, uint64_t cols, uint64_t r
   return true;
 }
 
-template <int KIND, int NPASS, int BN, int EPI>
-void launch_cfg(const TcOperands& t, const CUtensorMap& a_hi, const CUtensorMap& a_lo,
-                const CUtensorMap& b_hi, const CUtensorMap& b_lo, dim3 grid, int kb_per_split,
-                int kb_total, const EpiArgs& ep, const int* done, cudaStream_t s) {
-  using C = Cfg<KIND, NPASS, BN, EPI>;
-  umma_gemm_kernel<KIND, NPASS, BN, EPI><<<grid, NTHREADS, C::SMEM, s>>>(
-      a_hi, a_lo, b_hi, b_lo, kb_per_split, kb_total, ep, done);
-}
+template <int V>
+using IC = std::integral_constant<int, V>;
 
-template <int EPI, int BN>
-void dispatch_prec(int prec, const TcOperands& t, const CUtensorMap& a_hi,
-                   const CUtensorMap& a_lo, const CUtensorMap& b_hi, const CUtensorMap& b_lo,
-                   dim3 grid, int kbps, int kbt, const EpiArgs& ep, const int* done,
-                   cudaStream_t s) {
+// Calls f(kind, npass, bn, rb) (integral constants) for the kernel variant of a
+// precision, tile width (accumulator columns) and operand row width (bytes).
+template <class F>
+void visit_variant(int prec, int bn, int rb, F&& f) {
+  auto by_rb = [&](auto kind, auto npass, auto bnc) {
+    if (rb == 64) f(kind, npass, bnc, IC<64>{});
+    else f(kind, npass, bnc, IC<128>{});
+  };
+  auto by_bn = [&](auto kind, auto npass) {
+    if (bn == 256) by_rb(kind, npass, IC<256>{});
+    else by_rb(kind, npass, IC<128>{});
+  };
   switch (prec) {
-    case OFA_PREC_TF32:
-      launch_cfg<KIND_TF32, 1, BN, EPI>(t, a_hi, a_lo, b_hi, b_lo, grid, kbps, kbt, ep, done, s);
-      break;
-    case OFA_PREC_BF16:
-      launch_cfg<KIND_BF16, 1, BN, EPI>(t, a_hi, a_lo, b_hi, b_lo, grid, kbps, kbt, ep, done, s);
-      break;
-    case OFA_PREC_BF16X3:
-      launch_cfg<KIND_BF16, 3, BN, EPI>(t, a_hi, a_lo, b_hi, b_lo, grid, kbps, kbt, ep, done, s);
-      break;
-    case OFA_PREC_F16X3:
-      launch_cfg<KIND_F16, 3, BN, EPI>(t, a_hi, a_lo, b_hi, b_lo, grid, kbps, kbt, ep, done, s);
-      break;
-    default:
-      break;
+    case OFA_PREC_TF32: by_bn(IC<KIND_TF32>{}, IC<1>{}); break;
+    case OFA_PREC_BF16: by_bn(IC<KIND_BF16>{}, IC<1>{}); break;
+    case OFA_PREC_BF16X3: by_bn(IC<KIND_BF16>{}, IC<3>{}); break;
+    case OFA_PREC_F16X3: by_bn(IC<KIND_F16>{}, IC<3>{}); break;
+    default: break;
   }
 }
 
-template <int EPI>
-void dispatch(int prec, int bn, const TcOperands& t, const CUtensorMap& a_hi,
-              const CUtensorMap& a_lo, const CUtensorMap& b_hi, const CUtensorMap& b_lo,
-              dim3 grid, int kbps, int kbt, const EpiArgs& ep, const int* done, cudaStream_t s) {
-  if (bn == 128)
-    dispatch_prec<EPI, 128>(prec, t, a_hi, a_lo, b_hi, b_lo, grid, kbps, kbt, ep, done, s);
-  else
-    dispatch_prec<EPI, 256>(prec, t, a_hi, a_lo, b_hi, b_lo, grid, kbps, kbt, ep, done, s);
+#define OFA_VARIANT_TYPES                                                        \
+  constexpr int K_ = decltype(kind)::value, NP_ = decltype(npass)::value;        \
+  constexpr int BN_ = decltype(bnc)::value, RB_ = decltype(rbc)::value;          \
+  using C = Cfg<K_, NP_, BN_, EPI, RB_>;                                          \
+  (void)sizeof(C)
+
+cudaLaunchConfig_t make_cfg(dim3 grid, int threads, int smem, cudaStream_t s,
+                            cudaLaunchAttribute* attr, int ccx, int ccy) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ccx;
+  attr[0].val.clusterDim.y = ccy;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cfg;
 }
 
-template <int KIND, int NPASS>
-cudaError_t set_attrs() {
+template <int EPI>
+void launch_gemm(int prec, int bn, int rb, int ccx, int ccy, const CUtensorMap& a_hi,
+                 const CUtensorMap& a_lo, const CUtensorMap& b_hi, const CUtensorMap& b_lo,
+                 dim3 grid, int kbps, int kbt, const EpiArgs& ep, const int* done,
+                 cudaStream_t s) {
+  visit_variant(prec, bn, rb, [&](auto kind, auto npass, auto bnc, auto rbc) {
+    OFA_VARIANT_TYPES;
+    cudaLaunchAttribute attr[2];
+    cudaLaunchConfig_t cfg = make_cfg(grid, Warps<EPI>::THREADS, C::SMEM, s, attr, ccx, ccy);
+    cudaLaunchKernelEx(&cfg, umma_gemm_kernel<K_, NP_, BN_, EPI, RB_>, a_hi, a_lo, b_hi, b_lo,
+                       kbps, kbt, ep, done, ccx, ccy);
+  });
+}
+
+template <int EPI>
+cudaError_t set_attr_epi(int prec) {
   cudaError_t e = cudaSuccess;
-  auto one = [&](auto kern, int bytes) {
-    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (r != cudaSuccess) e = r;
-  };
-  one(umma_gemm_kernel<KIND, NPASS, 128, EPI_FWD>, Cfg<KIND, NPASS, 128, EPI_FWD>::SMEM);
-  one(umma_gemm_kernel<KIND, NPASS, 256, EPI_FWD>, Cfg<KIND, NPASS, 256, EPI_FWD>::SMEM);
-  one(umma_gemm_kernel<KIND, NPASS, 128, EPI_BWD>, Cfg<KIND, NPASS, 128, EPI_BWD>::SMEM);
-  one(umma_gemm_kernel<KIND, NPASS, 256, EPI_BWD>, Cfg<KIND, NPASS, 256, EPI_BWD>::SMEM);
-  one(umma_gemm_kernel<KIND, NPASS, 128, EPI_GRAD>, Cfg<KIND, NPASS, 128, EPI_GRAD>::SMEM);
-  one(umma_gemm_kernel<KIND, NPASS, 256, EPI_GRAD>, Cfg<KIND, NPASS, 256, EPI_GRAD>::SMEM);
+  for (int bn : {128, 256})
+    for (int rb : {128, 64})
+      visit_variant(prec, bn, rb, [&](auto kind, auto npass, auto bnc, auto rbc) {
+        OFA_VARIANT_TYPES;
+        cudaError_t r = cudaFuncSetAttribute(umma_gemm_kernel<K_, NP_, BN_, EPI, RB_>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (r != cudaSuccess) e = r;
+      });
   return e;
+}
+
+template <int EPI>
+int max_clusters(int prec, int bn, int rb, int ccx, int ccy, dim3 grid) {
+  int n = 0;
+  visit_variant(prec, bn, rb, [&](auto kind, auto npass, auto bnc, auto rbc) {
+    OFA_VARIANT_TYPES;
+    cudaLaunchAttribute attr[2];
+    cudaLaunchConfig_t cfg = make_cfg(grid, Warps<EPI>::THREADS, C::SMEM, 0, attr, ccx, ccy);
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&n, umma_gemm_kernel<K_, NP_, BN_, EPI, RB_>, &cfg) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+  });
+  return n;
 }
 
 EpiArgs base_args(ofa_plan* p) {
@@ -581,31 +821,166 @@ EpiArgs base_args(ofa_plan* p) {
 
 }  // namespace
 
+#ifdef OFA_PHASE_TRACE
+extern "C" int ofa_debug_phase_trace(unsigned long long* out) {
+  return (int)cudaMemcpyFromSymbol(out, g_phase_trace, sizeof(g_phase_trace));  // [2][1024][16]
+}
+#endif
+
 // Opt every kernel variant of a precision into its dynamic shared memory (done
 // once per plan, outside any stream capture; the attribute is per device).
 cudaError_t tc_prepare(int prec) {
-  switch (prec) {
-    case OFA_PREC_TF32: return set_attrs<KIND_TF32, 1>();
-    case OFA_PREC_BF16: return set_attrs<KIND_BF16, 1>();
-    case OFA_PREC_BF16X3: return set_attrs<KIND_BF16, 3>();
-    case OFA_PREC_F16X3: return set_attrs<KIND_F16, 3>();
-    default: return cudaSuccess;
+  cudaError_t e = set_attr_epi<EPI_FWD>(prec);
+  cudaError_t e2 = set_attr_epi<EPI_BWD>(prec);
+  cudaError_t e3 = set_attr_epi<EPI_GRAD>(prec);
+  return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3);
+}
+
+bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err);
+
+namespace {
+struct TuneResult {
+  int fwd_bn, fwd_split, fwd_rb, fwd_ccx, fwd_ccy, bwd_bn, bwd_rb, bwd_ccx, bwd_ccy;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, TuneResult> g_tune_cache;
+
+int cluster_shape_ok(ofa_plan* p, int epi, int bn, int rb, int n_tiles, int m_tiles, int z,
+                     int ccx, int ccy) {
+  if (n_tiles % ccx != 0 || m_tiles % ccy != 0) return 0;
+  if (ccx * ccy == 1) return 1;
+  dim3 grid(n_tiles, m_tiles, z);
+  if (epi == EPI_FWD) return max_clusters<EPI_FWD>(p->precision, bn, rb, ccx, ccy, grid);
+  return max_clusters<EPI_BWD>(p->precision, bn, rb, ccx, ccy, grid);
+}
+
+void apply(TcOperands& t, const TuneResult& r) {
+  t.fwd_bn = r.fwd_bn; t.fwd_split = r.fwd_split; t.fwd_rb = r.fwd_rb;
+  t.fwd_ccx = r.fwd_ccx; t.fwd_ccy = r.fwd_ccy;
+  t.bwd_bn = r.bwd_bn; t.bwd_rb = r.bwd_rb; t.bwd_ccx = r.bwd_ccx; t.bwd_ccy = r.bwd_ccy;
+}
+}  // namespace
+
+bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
+  const auto key = std::make_tuple(p->device, p->nx, p->ny, p->K, p->precision);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      apply(t, it->second);
+      return true;
+    }
   }
+  // Scratch outputs: the inverse candidates must not touch the loop's phase and field.
+  float* phi_scratch = nullptr;
+  const size_t e_bytes = (size_t)p->nyp * 2 * p->nxp * t.elem_bytes;
+  void* e_scr[2] = {nullptr, nullptr};
+  bool ok = cudaMalloc(&phi_scratch, (size_t)p->nx * p->ny * 4) == cudaSuccess &&
+            cudaMalloc(&e_scr[0], e_bytes) == cudaSuccess &&
+            (t.npass == 1 || cudaMalloc(&e_scr[1], e_bytes) == cudaSuccess);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  if (!ok) err = "allocating autotune scratch";
+  const int tiles_m = p->nyp / BM;
+  const int reps = 5;
+  // OFA_AUTOTUNE_VERBOSE=1 prints every candidate's time to stderr
+  const char* venv = getenv("OFA_AUTOTUNE_VERBOSE");
+  const bool verbose = venv != nullptr && venv[0] == '1';
+  auto time_it = [&](auto&& launch) -> float {
+    launch();  // warm-up
+    cudaEventRecord(e0, p->stream);
+    for (int r = 0; r < reps; ++r) launch();
+    cudaEventRecord(e1, p->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (cudaGetLastError() != cudaSuccess) return 1e30f;
+    return ms;
+  };
+  const int cl[4][2] = {{1, 1}, {2, 2}, {2, 1}, {1, 2}};
+  float best_f = 1e30f, best_b = 1e30f;
+  TuneResult res = {t.fwd_bn, t.fwd_split, t.fwd_rb, 1, 1, t.bwd_bn, t.bwd_rb, 1, 1};
+  for (int rb : {128, 64}) {
+    const int kb_fwd = (2 * p->nxp * t.elem_bytes) / rb;
+    for (int bn : {128, 256}) {
+      for (int split = 1; split <= 4 && ok; split *= 2) {
+        if (kb_fwd / split < 4) break;
+        for (auto& c : cl) {
+          const int n_tiles = (2 * p->kp) / bn;
+          if (!cluster_shape_ok(p, EPI_FWD, bn, rb, n_tiles, tiles_m, split, c[0], c[1]))
+            continue;
+          TcOperands cand = t;
+          cand.fwd_bn = bn; cand.fwd_split = split; cand.fwd_rb = rb;
+          cand.fwd_ccx = c[0]; cand.fwd_ccy = c[1];
+          if (!tc_encode_maps(p, cand, err)) { ok = false; break; }
+          const float ms = time_it([&] { launch_fwd_tc(p, cand, nullptr, p->stream, false); });
+          if (verbose)
+            fprintf(stderr, "ofa autotune forward bn=%d split=%d rb=%d cluster=%dx%d: %.2f us\n",
+                    bn, split, rb, c[0], c[1], 1000.f * ms / reps);
+          if (ms < best_f) {
+            best_f = ms;
+            res.fwd_bn = bn; res.fwd_split = split; res.fwd_rb = rb;
+            res.fwd_ccx = c[0]; res.fwd_ccy = c[1];
+          }
+        }
+      }
+    }
+  }
+  for (int rb : {128, 64}) {
+    for (int bn : {128, 256}) {
+      if (!ok) break;
+      for (auto& c : cl) {
+        const int n_tiles = (2 * p->nxp) / bn;
+        if (!cluster_shape_ok(p, EPI_BWD, bn, rb, n_tiles, tiles_m, 1, c[0], c[1])) continue;
+        TcOperands cand = t;
+        cand.e_hi = e_scr[0];
+        cand.e_lo = e_scr[1];
+        cand.bwd_bn = bn; cand.bwd_rb = rb; cand.bwd_ccx = c[0]; cand.bwd_ccy = c[1];
+        if (!tc_encode_maps(p, cand, err)) { ok = false; break; }
+        float* keep = p->phi;
+        p->phi = phi_scratch;
+        const float ms = time_it([&] { launch_bwd_tc(p, cand, nullptr, p->stream); });
+        p->phi = keep;
+        if (verbose)
+          fprintf(stderr, "ofa autotune inverse bn=%d rb=%d cluster=%dx%d: %.2f us\n", bn, rb,
+                  c[0], c[1], 1000.f * ms / reps);
+        if (ms < best_b) {
+          best_b = ms;
+          res.bwd_bn = bn; res.bwd_rb = rb; res.bwd_ccx = c[0]; res.bwd_ccy = c[1];
+        }
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(phi_scratch);
+  cudaFree(e_scr[0]);
+  if (e_scr[1]) cudaFree(e_scr[1]);
+  cudaGetLastError();
+  if (!ok) return false;
+  apply(t, res);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = res;
+  return true;
 }
 
 bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err) {
   const int eb = t.elem_bytes;
   const uint64_t e_cols = 2 * (uint64_t)p->nxp, k_cols = 2 * (uint64_t)p->kp;
   bool ok = true;
-  ok = ok && encode(&t.tm_e_hi, t.e_hi, eb, e_cols, p->nyp, BM, err);
-  ok = ok && encode(&t.tm_bx_hi, t.bx_hi, eb, e_cols, 2 * (uint64_t)p->kp, t.fwd_bn, err);
-  ok = ok && encode(&t.tm_p_hi, t.p_hi, eb, k_cols, p->nyp, BM, err);
-  ok = ok && encode(&t.tm_q_hi, t.q_hi, eb, k_cols, 2 * (uint64_t)p->nxp, t.bwd_bn, err);
+  // boxes are the per-CTA slices of a cluster's multicast (whole tiles without clusters)
+  const uint32_t e_box = BM / t.fwd_ccx, bx_box = t.fwd_bn / t.fwd_ccy;
+  const uint32_t p_box = BM / t.bwd_ccx, q_box = t.bwd_bn / t.bwd_ccy;
+  const int fr = t.fwd_rb, br = t.bwd_rb;
+  ok = ok && encode(&t.tm_e_hi, t.e_hi, eb, e_cols, p->nyp, e_box, fr, err);
+  ok = ok && encode(&t.tm_bx_hi, t.bx_hi, eb, e_cols, 2 * (uint64_t)p->kp, bx_box, fr, err);
+  ok = ok && encode(&t.tm_p_hi, t.p_hi, eb, k_cols, p->nyp, p_box, br, err);
+  ok = ok && encode(&t.tm_q_hi, t.q_hi, eb, k_cols, 2 * (uint64_t)p->nxp, q_box, br, err);
   if (t.npass == 3) {
-    ok = ok && encode(&t.tm_e_lo, t.e_lo, eb, e_cols, p->nyp, BM, err);
-    ok = ok && encode(&t.tm_bx_lo, t.bx_lo, eb, e_cols, 2 * (uint64_t)p->kp, t.fwd_bn, err);
-    ok = ok && encode(&t.tm_p_lo, t.p_lo, eb, k_cols, p->nyp, BM, err);
-    ok = ok && encode(&t.tm_q_lo, t.q_lo, eb, k_cols, 2 * (uint64_t)p->nxp, t.bwd_bn, err);
+    ok = ok && encode(&t.tm_e_lo, t.e_lo, eb, e_cols, p->nyp, e_box, fr, err);
+    ok = ok && encode(&t.tm_bx_lo, t.bx_lo, eb, e_cols, 2 * (uint64_t)p->kp, bx_box, fr, err);
+    ok = ok && encode(&t.tm_p_lo, t.p_lo, eb, k_cols, p->nyp, p_box, br, err);
+    ok = ok && encode(&t.tm_q_lo, t.q_lo, eb, k_cols, 2 * (uint64_t)p->nxp, q_box, br, err);
   } else {
     t.tm_e_lo = t.tm_e_hi;
     t.tm_bx_lo = t.tm_bx_hi;
@@ -615,34 +990,49 @@ bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err) {
   return ok;
 }
 
-void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s) {
-  const int kb_total = (2 * p->nxp * t.elem_bytes) / ROW_BYTES;
+void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s,
+                   bool fuse_focal) {
+  const int kb_total = (2 * p->nxp * t.elem_bytes) / t.fwd_rb;
   const int kbps = (kb_total + t.fwd_split - 1) / t.fwd_split;
   dim3 grid((2 * p->kp) / t.fwd_bn, p->nyp / BM, t.fwd_split);
   EpiArgs ep = base_args(p);
-  dispatch<EPI_FWD>(p->precision, t.fwd_bn, t, t.tm_e_hi, t.tm_e_lo, t.tm_bx_hi, t.tm_bx_lo, grid,
-                    kbps, kb_total, ep, done, s);
+  if (fuse_focal) {
+    ep.fuse = 1;
+    ep.counters = p->counters;
+    ep.n_tiles = (int)grid.x;
+    ep.n_part = (int)(grid.y * grid.z);
+    ep.K = p->K;
+    ep.theta = p->theta;
+    ep.t = p->t;
+    ep.w = p->w;
+    ep.c = p->c;
+    ep.hist = p->hist;
+    ep.stw = p->st;
+    ep.weighting = p->weighting;
+  }
+  launch_gemm<EPI_FWD>(p->precision, t.fwd_bn, t.fwd_rb, t.fwd_ccx, t.fwd_ccy, t.tm_e_hi,
+                       t.tm_e_lo, t.tm_bx_hi, t.tm_bx_lo, grid, kbps, kb_total, ep, done, s);
 }
 
 void launch_bwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s) {
-  const int kb_total = (2 * p->kp * t.elem_bytes) / ROW_BYTES;
+  const int kb_total = (2 * p->kp * t.elem_bytes) / t.bwd_rb;
   dim3 grid((2 * p->nxp) / t.bwd_bn, p->nyp / BM, 1);
   EpiArgs ep = base_args(p);
   ep.out = p->phi;
   ep.e_hi = t.e_hi;
   ep.e_lo = t.e_lo;
-  dispatch<EPI_BWD>(p->precision, t.bwd_bn, t, t.tm_p_hi, t.tm_p_lo, t.tm_q_hi, t.tm_q_lo, grid,
-                    kb_total, kb_total, ep, done, s);
+  launch_gemm<EPI_BWD>(p->precision, t.bwd_bn, t.bwd_rb, t.bwd_ccx, t.bwd_ccy, t.tm_p_hi,
+                       t.tm_p_lo, t.tm_q_hi, t.tm_q_lo, grid, kb_total, kb_total, ep, done, s);
 }
 
 void launch_grad_tc(ofa_plan* p, const TcOperands& t, const float* phi, float scale_unused,
                     float* grad, cudaStream_t s) {
   (void)scale_unused;
-  const int kb_total = (2 * p->kp * t.elem_bytes) / ROW_BYTES;
+  const int kb_total = (2 * p->kp * t.elem_bytes) / t.bwd_rb;
   dim3 grid((2 * p->nxp) / t.bwd_bn, p->nyp / BM, 1);
   EpiArgs ep = base_args(p);
   ep.out = grad;
   ep.phi_in = phi;
-  dispatch<EPI_GRAD>(p->precision, t.bwd_bn, t, t.tm_p_hi, t.tm_p_lo, t.tm_q_hi, t.tm_q_lo, grid,
-                     kb_total, kb_total, ep, nullptr, s);
+  launch_gemm<EPI_GRAD>(p->precision, t.bwd_bn, t.bwd_rb, t.bwd_ccx, t.bwd_ccy, t.tm_p_hi,
+                        t.tm_p_lo, t.tm_q_hi, t.tm_q_lo, grid, kb_total, kb_total, ep, nullptr, s);
 }

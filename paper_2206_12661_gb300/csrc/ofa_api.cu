@@ -59,7 +59,7 @@ void free_tc(TcOperands& t) {
 // Tile choice for the two products (cost model: waves x per-CTA MMA work).
 void choose_tiles(ofa_plan* p, TcOperands& t, int sms) {
   const int tiles_m = p->nyp / 128;
-  const int kb_fwd = (2 * p->nxp * t.elem_bytes) / 128;
+  const int kb_fwd = (2 * p->nxp * t.elem_bytes) / t.fwd_rb;
   double best = 1e30;
   for (int bn : {256, 128}) {
     for (int split = 1; split <= 8; split *= 2) {
@@ -126,9 +126,12 @@ void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
                  p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
     launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->phi, done, s);
   } else {
-    launch_fwd_tc(p, p->tc, done, s);
-    launch_focal(p->part, (p->nyp / 128) * p->tc.fwd_split, p->kp, p->K, p->t, p->w, p->theta,
-                 p->inten, p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
+    // up to 4096 foci the focal step runs in the forward kernel's last CTA
+    const bool fuse = p->K <= 4096;
+    launch_fwd_tc(p, p->tc, done, s, fuse);
+    if (!fuse)
+      launch_focal(p->part, (p->nyp / 128) * p->tc.fwd_split, p->kp, p->K, p->t, p->w, p->theta,
+                   p->inten, p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
     launch_build_p(p->fyT, p->c, done, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
     launch_bwd_tc(p, p->tc, done, s);
   }
@@ -142,7 +145,7 @@ void enqueue_forward_current(ofa_plan* p, cudaStream_t s) {
                  p->c, p->hist, p->st, 1, p->weighting, ldexpf(1.f, p->amp_exp), p->amp_energy,
                  s);
   } else {
-    launch_fwd_tc(p, p->tc, nullptr, s);
+    launch_fwd_tc(p, p->tc, nullptr, s, false);
     launch_focal(p->part, (p->nyp / 128) * p->tc.fwd_split, p->kp, p->K, p->t, p->w, p->theta,
                  p->inten, p->c, p->hist, p->st, 1, p->weighting, ldexpf(1.f, p->amp_exp),
                  p->amp_energy, s);
@@ -243,6 +246,7 @@ ofa_status ofa_options_default(ofa_options* o) {
   o->phi0 = nullptr;
   o->mem_space = OFA_MEM_HOST;
   o->weighting = 1;
+  o->autotune = 1;
   return OFA_OK;
 }
 
@@ -293,6 +297,17 @@ ofa_status ofa_check_foci(int n_foci, const double* xy, double px, double py, do
   return OFA_OK;
 }
 
+ofa_status ofa_plan_config(const ofa_plan* p, int* c) {
+  if (!p || !c) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "NULL argument");
+  for (int i = 0; i < 10; ++i) c[i] = 0;
+  if (!prec_is_tc(p->precision)) return OFA_OK;
+  const TcOperands& t = p->tc;
+  c[0] = t.fwd_bn; c[1] = t.fwd_split; c[2] = t.fwd_ccx; c[3] = t.fwd_ccy;
+  c[4] = t.bwd_bn; c[5] = t.bwd_ccx; c[6] = t.bwd_ccy; c[7] = p->K <= 4096 ? 1 : 0;
+  c[8] = t.fwd_rb; c[9] = t.bwd_rb;
+  return OFA_OK;
+}
+
 ofa_status ofa_plan_info(const ofa_plan* p, int* nx, int* ny, int* n_foci, int* precision) {
   if (!p) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "plan is NULL");
   if (nx) *nx = p->nx;
@@ -309,9 +324,9 @@ ofa_status ofa_destroy(ofa_plan* p) {
   cudaSetDevice(p->device);
   if (p->stream || p->own_stream) cudaStreamSynchronize(p->stream);
   destroy_graphs(p);
-  void* bufs[] = {p->focus_xy, p->t,   p->amp,     p->phi,  p->w,    p->fx,         p->fy,
-                  p->fyT,      p->part, p->theta,  p->inten, p->c,   p->hist,       p->st,
-                  p->scratch_phi};
+  void* bufs[] = {p->focus_xy, p->t,     p->amp,   p->phi,   p->w,    p->fx,
+                  p->fy,       p->fyT,   p->part,  p->theta, p->inten, p->c,
+                  p->hist,     p->st,    p->scratch_phi, p->counters};
   for (void* b : bufs) dfree(b);
   if (p->st_host) cudaFreeHost(p->st_host);
   free_tc(p->tc);
@@ -435,6 +450,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   OFA_TRY(dalloc(&p->inten, n_foci), "alloc");
   OFA_TRY(dalloc(&p->c, p->kp), "alloc");
   OFA_TRY(dalloc(&p->hist, OFA_HIST_CAP), "alloc");
+  OFA_TRY(dalloc(&p->counters, p->kp / 64 + 1), "alloc");
   OFA_TRY(dalloc(&p->st, 1), "alloc");
   OFA_TRY(cudaMallocHost(reinterpret_cast<void**>(&p->st_host), sizeof(OfaDevState)),
           "pinned alloc");
@@ -508,9 +524,16 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
                    p->stream);
     launch_field_planes(p->phi, p->amp, nx, ny, p->nxp, p->precision, p->tc.e_hi, p->tc.e_lo,
                         p->stream);
-    choose_tiles(p, p->tc, prop.multiProcessorCount);
     OFA_TRY(tc_prepare(p->precision), "setting kernel shared-memory attributes");
+    choose_tiles(p, p->tc, prop.multiProcessorCount);
     std::string err;
+    if (opt.autotune) {
+      OFA_TRY(cudaStreamSynchronize(p->stream), "plan set-up");
+      if (!tc_autotune(p, p->tc, err)) {
+        p->last_error = err;
+        return fail(OFA_ERR_CUDA);
+      }
+    }
     if (!tc_encode_maps(p, p->tc, err)) {
       p->last_error = err;
       return fail(OFA_ERR_CUDA);
@@ -680,7 +703,7 @@ ofa_status ofa_forward(ofa_plan* p, const float* phi, float* theta, float* inten
     if (s != OFA_OK) return s;
     launch_field_planes(phi, p->amp, p->nx, p->ny, p->nxp, p->precision, p->tc_aux.e_hi,
                         p->tc_aux.e_lo, p->stream);
-    launch_fwd_tc(p, p->tc_aux, nullptr, p->stream);
+    launch_fwd_tc(p, p->tc_aux, nullptr, p->stream, false);
     launch_focal(p->part, (p->nyp / 128) * p->tc.fwd_split, p->kp, p->K, p->t, p->w, th, in, p->c,
                  p->hist, p->st, 2, p->weighting, out_scale, p->amp_energy, p->stream);
   }
@@ -746,11 +769,12 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   auto run = [&](int which) {
     switch (which) {
       case 0:
-        if (tc) launch_fwd_tc(p, p->tc, nullptr, s);
+        if (tc) launch_fwd_tc(p, p->tc, nullptr, s, p->K <= 4096);  // + fused focal step
         else launch_fwd_simt(p->phi, p->amp, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part,
                              nullptr, s);
         break;
       case 1:
+        if (tc && p->K <= 4096) break;  // fused into the forward kernel
         launch_control(p->st, 0.0, 1, s);
         launch_focal(p->part, n_part, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist,
                      p->st, 0, p->weighting, 1.f, p->amp_energy, s);
@@ -769,8 +793,8 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
   for (int which = 0; which < 4; ++which) {
-    if (which == 2 && !tc) {
-      ms_out[2] = 0.0;
+    if ((which == 2 && !tc) || (which == 1 && tc && p->K <= 4096)) {
+      ms_out[which] = 0.0;
       continue;
     }
     run(which);  // warm-up

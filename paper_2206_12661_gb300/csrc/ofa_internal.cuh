@@ -52,6 +52,8 @@ struct TcOperands {
   void* q_hi = nullptr; void* q_lo = nullptr;
   CUtensorMap tm_e_hi, tm_e_lo, tm_bx_hi, tm_bx_lo, tm_p_hi, tm_p_lo, tm_q_hi, tm_q_lo;
   int fwd_bn = 256, fwd_split = 1, bwd_bn = 256;
+  int fwd_rb = 128, bwd_rb = 128;                          // operand row bytes per stage
+  int fwd_ccx = 1, fwd_ccy = 1, bwd_ccx = 1, bwd_ccy = 1;  // thread-block cluster shapes
 };
 
 struct ofa_plan {
@@ -79,6 +81,7 @@ struct ofa_plan {
   float* inten = nullptr;              // [K]
   float2* c = nullptr;                 // [kp] focused field (scaled), zero padded
   double* hist = nullptr;              // [OFA_HIST_CAP]
+  unsigned int* counters = nullptr;    // [kp / 64 + 1] arrival counters of the fused forward
   OfaDevState* st = nullptr;
   OfaDevState* st_host = nullptr;      // pinned mirror for readback
   float* scratch_phi = nullptr;        // for ofa_forward / ofa_adjoint on the tensor path
@@ -139,8 +142,13 @@ void launch_build_p(const float2* fyT, const float2* c, const int* done, int nyp
 
 // ---------------------------------------------------------------- kernels (k_umma.cu)
 cudaError_t tc_prepare(int prec);
+// Time the candidate shapes of both products on scratch outputs and keep the
+// fastest in t (cached per device, size and precision for the process).
+bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err);
 bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err);
-void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s);
+// fuse_focal: the last CTA runs the focal step of the loop (mode 0) on the final Theta.
+void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s,
+                   bool fuse_focal);
 void launch_bwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s);
 void launch_grad_tc(ofa_plan* p, const TcOperands& t, const float* phi, float scale,
                     float* grad, cudaStream_t s);

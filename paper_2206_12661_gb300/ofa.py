@@ -42,7 +42,7 @@ OFA_MEM_DEVICE = 1
 class ofa_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("seed", C.c_uint64), ("cuda_stream", C.c_void_p),
                 ("amplitude", C.c_void_p), ("waist_frac", C.c_double), ("phi0", C.c_void_p),
-                ("mem_space", C.c_int), ("weighting", C.c_int)]
+                ("mem_space", C.c_int), ("weighting", C.c_int), ("autotune", C.c_int)]
 
 
 class ofa_stats(C.Structure):
@@ -68,6 +68,7 @@ SIGNATURES = [
     ("ofa_forward", _I, [_P, _P, _P, _P]),
     ("ofa_adjoint", _I, [_P, _P, _P, _P, _P]),
     ("ofa_profile_kernels", _I, [_P, _I, _P]),
+    ("ofa_plan_config", _I, [_P, _P]),
     ("ofa_plan_info", _I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     ("ofa_batch_create", _I, [C.POINTER(_P), C.POINTER(_P), _I, _P]),
     ("ofa_batch_iterate", _I, [_P, _I]),
@@ -203,6 +204,14 @@ def ofa_profile_kernels(plan, reps: int = 20) -> np.ndarray:
     return out
 
 
+def ofa_plan_config(plan) -> dict:
+    c = np.zeros(10, dtype=np.int32)
+    _check(_lib.ofa_plan_config(plan, _ptr(c)), plan)
+    keys = ["fwd_bn", "fwd_split", "fwd_cluster_x", "fwd_cluster_y", "inv_bn", "inv_cluster_x",
+            "inv_cluster_y", "focal_fused", "fwd_row_bytes", "inv_row_bytes"]
+    return dict(zip(keys, (int(x) for x in c)))
+
+
 def ofa_plan_info(plan):
     a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     _check(_lib.ofa_plan_info(plan, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), plan)
@@ -253,12 +262,13 @@ class Plan:
 
     def __init__(self, nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy, target,
                  precision="f16x3", amplitude=None, phi0=None, seed=0, weighting=True,
-                 stream=None, waist_frac=0.4, mem_space=OFA_MEM_HOST):
+                 stream=None, waist_frac=0.4, mem_space=OFA_MEM_HOST, autotune=True):
         opt = ofa_options_default()
         opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opt.seed = int(seed)
         opt.cuda_stream = stream
         opt.weighting = 1 if weighting else 0
+        opt.autotune = 1 if autotune else 0
         opt.waist_frac = float(waist_frac)
         opt.mem_space = int(mem_space)
         if mem_space == OFA_MEM_HOST:

@@ -42,6 +42,7 @@ def test_options_default(ofa):
     assert o.precision == ofa.OFA_PREC_F16X3
     assert o.waist_frac == 0.4
     assert o.weighting == 1
+    assert o.autotune == 1
     assert not o.amplitude and not o.phi0 and not o.cuda_stream
 
 
