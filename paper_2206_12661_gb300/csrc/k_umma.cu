@@ -158,6 +158,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (gtimer() - t0 > WAIT_NS) return false;
   }
 }
+// Bounded wait for the long accumulator wait of the epilogue warps: they sleep
+// between polls, so hundreds of waiting threads do not compete with the MMA
+// operand reads for shared memory.
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(bar, parity)) {
+    __nanosleep(128);
+    if (gtimer() - t0 > WAIT_NS) return mbar_try_wait(bar, parity);
+  }
+  return true;
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
                                             int x, int y) {
   asm volatile(
@@ -201,29 +212,58 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// tcgen05 allocation and MMA for one CTA (CG = 1) or a CTA pair (CG = 2: both
+// CTAs of the pair allocate collectively; the even CTA issues the MMAs, which
+// read the A rows and half of the B rows from each CTA's shared memory and write
+// each CTA's 128 accumulator rows).
+template <int CG>
 __device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  if (CG == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  } else {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
 }
+template <int CG>
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
+  if (CG == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+  else
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
 }
-template <int KIND>
+template <int KIND, int CG>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                      uint32_t idesc, uint32_t accumulate) {
-  if (KIND == KIND_TF32) {
+  if (KIND == KIND_TF32 && CG == 1) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
-  } else {
+  } else if (KIND == KIND_TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else if (CG == 1) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
   }
@@ -235,10 +275,33 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 }
 // Arrive on the barrier at this offset in every CTA of cta_mask once all prior
 // tcgen05 operations of this thread have completed.
+template <int CG>
 __device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t cta_mask) {
+  if (CG == 1)
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(bar), "h"(cta_mask)
+        : "memory");
+  else
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(bar), "h"(cta_mask)
+        : "memory");
+}
+// Shared::cluster address of the same shared-memory location in CTA `rank`.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+// Tile load of a CTA pair: the completion is signalled on `bar`, which may be
+// the peer (even) CTA's barrier.
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map,
+                                                 uint32_t bar, int x, int y) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(bar), "h"(cta_mask)
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
       : "memory");
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -303,13 +366,13 @@ struct BarEpi {
   __device__ __forceinline__ void operator()() const { named_bar_epi(); }
 };
 
-template <int KIND, int NPASS, int BN, int EPI, int RB>
+template <int KIND, int NPASS, int BN, int EPI, int RB, int CG>
 struct Cfg {
   static constexpr int EB = KIND == KIND_TF32 ? 4 : 2;
   static constexpr int BK = RB / EB;                      // elements of K per stage
   static constexpr int PLANES = NPASS == 3 ? 2 : 1;
   static constexpr int A_BYTES = BM * RB;
-  static constexpr int B_BYTES = BN * RB;
+  static constexpr int B_BYTES = (BN / CG) * RB;         // a pair holds half of B per CTA
   static constexpr int STAGE_BYTES = PLANES * (A_BYTES + B_BYTES);
   static constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES > 12 ? 12 : SMEM_BUDGET / STAGE_BYTES;
   // the inverse epilogue stages its output through 16 x 11 KB of the freed stages
@@ -318,18 +381,19 @@ struct Cfg {
   static constexpr int RED_BYTES = EPI == EPI_FWD ? 4 * BN * 4 : 0;
   static constexpr int BAR_OFF = STAGES * STAGE_BYTES + RED_BYTES;
   static constexpr int SMEM = BAR_OFF + 256 + 1024;        // barriers, slot, alignment
-  static constexpr uint32_t IDESC = idesc_make(BM, BN, KIND);
+  static constexpr uint32_t IDESC = idesc_make(BM * CG, BN, KIND);
   static_assert(STAGES >= 2, "need at least two stages");
 };
 
-template <int KIND, int NPASS, int BN, int EPI, int RB>
+template <int KIND, int NPASS, int BN, int EPI, int RB, int CG>
 __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tma_hi,
                      const __grid_constant__ CUtensorMap tma_lo,
                      const __grid_constant__ CUtensorMap tmb_hi,
                      const __grid_constant__ CUtensorMap tmb_lo, int kb_per_split, int kb_total,
                      EpiArgs ep, const int* __restrict__ done, int ccx, int ccy) {
-  using C = Cfg<KIND, NPASS, BN, EPI, RB>;
+  using C = Cfg<KIND, NPASS, BN, EPI, RB, CG>;
+  constexpr bool PAIR = CG == 2;
   constexpr int WARP_TMA = Warps<EPI>::TMA, WARP_MMA = Warps<EPI>::MMA;
   constexpr int GROUPS = Warps<EPI>::EPI_THREADS / 128;   // epilogue warps per lane quarter
   constexpr int CPW = BN / (32 * GROUPS);                  // 32-column chunks per epilogue warp
@@ -341,7 +405,10 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
   uint8_t* base = smem_raw + (base_u32 - raw);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_tile = blockIdx.x, m_tile = blockIdx.y, split = blockIdx.z;
+  // 2-SM pairs lie along the cluster's x dimension, so their grids put the row
+  // tiles on x; otherwise the column tiles are on x.
+  const int n_tile = PAIR ? blockIdx.y : blockIdx.x, m_tile = PAIR ? blockIdx.x : blockIdx.y;
+  const int split = blockIdx.z;
   const int kb0 = split * kb_per_split;
   const int nkb = min(kb_per_split, kb_total - kb0);
 
@@ -355,8 +422,12 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
   // Cluster (ccx x ccy CTAs, ccx along the output columns, ccy along the rows):
   // CTAs of one cluster row share the A tile, CTAs of one cluster column the B
   // tile; each loads a 1/ccx slice of A and a 1/ccy slice of B and multicasts it.
-  const bool clustered = (ccx * ccy) > 1;
+  // PAIR: clusters of two CTAs along the rows (cluster shape 2 x 1 over a grid whose x
+  // runs over the row tiles) form a 2-SM MMA pair.
+  const bool mcast = !PAIR && (ccx * ccy) > 1;
+  const bool clustered = PAIR || mcast;
   const int crank = clustered ? (int)cluster_ctarank() : 0;
+  const bool leader = !PAIR || (crank & 1) == 0;
   const int cx = crank % ccx, cy = crank / ccx;
   uint16_t row_mask = 0, col_mask = 0;
   for (int i = 0; i < ccx; ++i) row_mask |= (uint16_t)(1u << (i + cy * ccx));
@@ -365,7 +436,7 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(bar_full + 8 * s, 1);
       // every CTA that writes into this CTA's stages must have consumed them
-      mbar_init(bar_empty + 8 * s, ccx + ccy - 1);
+      mbar_init(bar_empty + 8 * s, mcast ? ccx + ccy - 1 : 1);
     }
     mbar_init(bar_accum, 1);
     fence_mbar_init();
@@ -378,9 +449,9 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
       tmap_prefetch(&tmb_lo);
     }
   }
-  if (warp == WARP_MMA) tmem_alloc(slot_u32, BN);
+  if (warp == WARP_MMA) tmem_alloc<CG>(slot_u32, BN);
   tc_fence_before();
-  if (clustered) cluster_sync_all();  // partners' barriers exist before any multicast
+  if (clustered) cluster_sync_all();  // partners' barriers exist before any remote signal
   else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
@@ -398,18 +469,38 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
     if (lane == 0) {
       int issued = 0;
       bool ok = true;
+#ifdef OFA_PHASE_TRACE
+      long long wait_cycles = 0;
+#endif
       for (int kb = 0; kb < nkb && ok; ++kb) {
         const int s = kb % C::STAGES;
         if (kb >= C::STAGES) {
+#ifdef OFA_PHASE_TRACE
+          const long long w0 = clock64();
+#endif
           if (!mbar_wait(bar_empty + 8 * s, ((kb / C::STAGES) - 1) & 1)) {
             ok = false;
             break;
           }
+#ifdef OFA_PHASE_TRACE
+          wait_cycles += clock64() - w0;
+#endif
         }
         const uint32_t st = base_u32 + s * C::STAGE_BYTES;
         const int x = (kb0 + kb) * C::BK;
-        mbar_expect_tx(bar_full + 8 * s, C::STAGE_BYTES);  // whole stage, all sources
-        if (!clustered) {
+        if (PAIR) {
+          // both CTAs' halves land on the leader's barrier, which expects them all
+          if (leader) mbar_expect_tx(bar_full + 8 * s, 2 * C::STAGE_BYTES);
+          const uint32_t fb = leader ? bar_full + 8 * s : mapa_shared(bar_full + 8 * s, crank & ~1);
+          const int brow = n_tile * BN + (crank & 1) * (BN / 2);
+          tma_load_2d_pair(st, &tma_hi, fb, x, m_tile * BM);
+          tma_load_2d_pair(st + C::PLANES * C::A_BYTES, &tmb_hi, fb, x, brow);
+          if (NPASS == 3) {
+            tma_load_2d_pair(st + C::A_BYTES, &tma_lo, fb, x, m_tile * BM);
+            tma_load_2d_pair(st + C::PLANES * C::A_BYTES + C::B_BYTES, &tmb_lo, fb, x, brow);
+          }
+        } else if (!mcast) {
+          mbar_expect_tx(bar_full + 8 * s, C::STAGE_BYTES);
           tma_load_2d(st, &tma_hi, bar_full + 8 * s, x, m_tile * BM);
           tma_load_2d(st + C::PLANES * C::A_BYTES, &tmb_hi, bar_full + 8 * s, x, n_tile * BN);
           if (NPASS == 3) {
@@ -418,6 +509,7 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
                         n_tile * BN);
           }
         } else {
+          mbar_expect_tx(bar_full + 8 * s, C::STAGE_BYTES);  // whole stage, all sources
           const int ar = BM / ccx, br = BN / ccy;   // slice rows
           const uint32_t ao = (uint32_t)(cx * ar * RB), bo = (uint32_t)(cy * br * RB);
           tma_load_2d_mc(st + ao, &tma_hi, bar_full + 8 * s, x, m_tile * BM + cx * ar, row_mask);
@@ -434,8 +526,16 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
         ++issued;
       }
       if (!ok) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
-      // Drain: every issued copy must have landed before the CTA may exit.
-      for (int kb = max(0, issued - C::STAGES); kb < issued; ++kb)
+#ifdef OFA_PHASE_TRACE
+      {
+        const int lin_ = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        if (lin_ < 1024) g_phase_trace[EPI == EPI_FWD ? 0 : 1][lin_][15] = (unsigned long long)wait_cycles;
+      }
+#endif
+      // Drain: every issued copy must have landed before the CTA may exit.  (The
+      // odd CTA of a pair signals the leader's barriers; its copies have landed
+      // once the leader's MMAs, which read them, complete.)
+      for (int kb = max(0, issued - C::STAGES); leader && kb < issued; ++kb)
         if (!mbar_wait(bar_full + 8 * (kb % C::STAGES), (kb / C::STAGES) & 1)) {
           atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
           break;
@@ -443,14 +543,23 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
     }
   } else if (warp == WARP_MMA) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && leader) {
       bool ok = true;
+#ifdef OFA_PHASE_TRACE
+      long long wait_cycles = 0;
+#endif
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % C::STAGES;
+#ifdef OFA_PHASE_TRACE
+        const long long w0 = clock64();
+#endif
         if (!mbar_wait(bar_full + 8 * s, (kb / C::STAGES) & 1)) {
           ok = false;
           break;
         }
+#ifdef OFA_PHASE_TRACE
+        if (kb > 0) wait_cycles += clock64() - w0;
+#endif
         tc_fence_after();
         const uint32_t st = base_u32 + s * C::STAGE_BYTES;
         const uint64_t a_hi = sdesc<RB>(st);
@@ -461,20 +570,29 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
         for (int kk = 0; kk < C::UMMA_K_STEPS; ++kk) {
           const uint64_t adv = (uint64_t)((kk * 32) >> 4);  // 32 bytes of K per MMA
           if ((kb | kk) == 0) OFA_STAMP(3);
-          umma<KIND>(tmem, a_hi + adv, b_hi + adv, C::IDESC, (kb | kk) != 0);
+          umma<KIND, CG>(tmem, a_hi + adv, b_hi + adv, C::IDESC, (kb | kk) != 0);
           if (NPASS == 3) {
-            umma<KIND>(tmem, a_hi + adv, b_lo + adv, C::IDESC, 1);
-            umma<KIND>(tmem, a_lo + adv, b_hi + adv, C::IDESC, 1);
+            umma<KIND, CG>(tmem, a_hi + adv, b_lo + adv, C::IDESC, 1);
+            umma<KIND, CG>(tmem, a_lo + adv, b_hi + adv, C::IDESC, 1);
           }
         }
         // stage free (in this CTA and for every CTA that writes into it) once
         // these MMAs have read it
-        if (clustered) umma_commit_mc(bar_empty + 8 * s, (uint16_t)(row_mask | col_mask));
+        if (PAIR) umma_commit_mc<CG>(bar_empty + 8 * s, (uint16_t)(3u << (crank & ~1)));
+        else if (mcast) umma_commit_mc<CG>(bar_empty + 8 * s, (uint16_t)(row_mask | col_mask));
         else umma_commit(bar_empty + 8 * s);
       }
       if (!ok) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
       OFA_STAMP(4);
-      umma_commit(bar_accum);  // accumulator complete (or drained, on abort)
+#ifdef OFA_PHASE_TRACE
+      {
+        const int lin_ = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        if (lin_ < 1024) g_phase_trace[EPI == EPI_FWD ? 0 : 1][lin_][13] = (unsigned long long)wait_cycles;
+      }
+#endif
+      // accumulator complete (or drained, on abort), in both CTAs of a pair
+      if (PAIR) umma_commit_mc<CG>(bar_accum, (uint16_t)(3u << (crank & ~1)));
+      else umma_commit(bar_accum);
     }
   } else {
     // ------------------------------------------------------------ epilogue warps
@@ -494,7 +612,7 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
       for (int c = 0; c < CPW; ++c)
 #pragma unroll
         for (int q = 0; q < 8; ++q) fy[c][q] = __ldg(fr + c * 8 + q);
-      const bool ready = mbar_wait(bar_accum, 0);
+      const bool ready = mbar_wait_sleep(bar_accum, 0);
       tc_fence_after();
       if (threadIdx.x == 0) OFA_STAMP(5);
       if (!ready) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
@@ -590,7 +708,7 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
           }
         }
       }
-      const bool ready = mbar_wait(bar_accum, 0);
+      const bool ready = mbar_wait_sleep(bar_accum, 0);
       tc_fence_after();
       if (threadIdx.x == 0) OFA_STAMP(5);
       if (!ready) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
@@ -663,7 +781,7 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
   __syncthreads();
   if (warp == WARP_MMA) {
     tc_fence_after();
-    tmem_dealloc(tmem, BN);
+    tmem_dealloc<CG>(tmem, BN);
   }
   // No CTA may leave while a partner can still multicast into its shared memory
   // or arrive on its barriers.
@@ -711,17 +829,20 @@ bool encode(CUtensorMap* m, void* ptr, int elem_bytes, uint64_t cols, uint64_t r
 template <int V>
 using IC = std::integral_constant<int, V>;
 
-// Calls f(kind, npass, bn, rb) (integral constants) for the kernel variant of a
-// precision, tile width (accumulator columns) and operand row width (bytes).
+// Calls f(kind, npass, bn, rb, cg) (integral constants) for the kernel variant of
+// a precision, tile width (accumulator columns), operand row width (bytes; only
+// the 128-byte rows are instantiated: 64-byte rows never measured faster) and
+// CTA group (1, or 2 for a 2-SM pair).
 template <class F>
-void visit_variant(int prec, int bn, int rb, F&& f) {
-  auto by_rb = [&](auto kind, auto npass, auto bnc) {
-    if (rb == 64) f(kind, npass, bnc, IC<64>{});
-    else f(kind, npass, bnc, IC<128>{});
+void visit_variant(int prec, int bn, int rb, int cg, F&& f) {
+  (void)rb;
+  auto by_cg = [&](auto kind, auto npass, auto bnc) {
+    if (cg == 2) f(kind, npass, bnc, IC<128>{}, IC<2>{});
+    else f(kind, npass, bnc, IC<128>{}, IC<1>{});
   };
   auto by_bn = [&](auto kind, auto npass) {
-    if (bn == 256) by_rb(kind, npass, IC<256>{});
-    else by_rb(kind, npass, IC<128>{});
+    if (bn == 256) by_cg(kind, npass, IC<256>{});
+    else by_cg(kind, npass, IC<128>{});
   };
   switch (prec) {
     case OFA_PREC_TF32: by_bn(IC<KIND_TF32>{}, IC<1>{}); break;
@@ -735,7 +856,8 @@ void visit_variant(int prec, int bn, int rb, F&& f) {
 #define OFA_VARIANT_TYPES                                                        \
   constexpr int K_ = decltype(kind)::value, NP_ = decltype(npass)::value;        \
   constexpr int BN_ = decltype(bnc)::value, RB_ = decltype(rbc)::value;          \
-  using C = Cfg<K_, NP_, BN_, EPI, RB_>;                                          \
+  constexpr int CG_ = decltype(cgc)::value;                                       \
+  using C = Cfg<K_, NP_, BN_, EPI, RB_, CG_>;                                     \
   (void)sizeof(C)
 
 cudaLaunchConfig_t make_cfg(dim3 grid, int threads, int smem, cudaStream_t s,
@@ -757,16 +879,18 @@ cudaLaunchConfig_t make_cfg(dim3 grid, int threads, int smem, cudaStream_t s,
 }
 
 template <int EPI>
-void launch_gemm(int prec, int bn, int rb, int ccx, int ccy, const CUtensorMap& a_hi,
+void launch_gemm(int prec, int bn, int rb, int cg, int ccx, int ccy, const CUtensorMap& a_hi,
                  const CUtensorMap& a_lo, const CUtensorMap& b_hi, const CUtensorMap& b_lo,
                  dim3 grid, int kbps, int kbt, const EpiArgs& ep, const int* done,
                  cudaStream_t s) {
-  visit_variant(prec, bn, rb, [&](auto kind, auto npass, auto bnc, auto rbc) {
+  visit_variant(prec, bn, rb, cg, [&](auto kind, auto npass, auto bnc, auto rbc, auto cgc) {
     OFA_VARIANT_TYPES;
+    const int cx = CG_ == 2 ? 2 : ccx, cy = CG_ == 2 ? 1 : ccy;
+    const dim3 g = CG_ == 2 ? dim3(grid.y, grid.x, grid.z) : grid;  // pairs: rows on x
     cudaLaunchAttribute attr[2];
-    cudaLaunchConfig_t cfg = make_cfg(grid, Warps<EPI>::THREADS, C::SMEM, s, attr, ccx, ccy);
-    cudaLaunchKernelEx(&cfg, umma_gemm_kernel<K_, NP_, BN_, EPI, RB_>, a_hi, a_lo, b_hi, b_lo,
-                       kbps, kbt, ep, done, ccx, ccy);
+    cudaLaunchConfig_t cfg = make_cfg(g, Warps<EPI>::THREADS, C::SMEM, s, attr, cx, cy);
+    cudaLaunchKernelEx(&cfg, umma_gemm_kernel<K_, NP_, BN_, EPI, RB_, CG_>, a_hi, a_lo, b_hi,
+                       b_lo, kbps, kbt, ep, done, cx, cy);
   });
 }
 
@@ -774,10 +898,10 @@ template <int EPI>
 cudaError_t set_attr_epi(int prec) {
   cudaError_t e = cudaSuccess;
   for (int bn : {128, 256})
-    for (int rb : {128, 64})
-      visit_variant(prec, bn, rb, [&](auto kind, auto npass, auto bnc, auto rbc) {
+    for (int cg : {1, 2})
+      visit_variant(prec, bn, 128, cg, [&](auto kind, auto npass, auto bnc, auto rbc, auto cgc) {
         OFA_VARIANT_TYPES;
-        cudaError_t r = cudaFuncSetAttribute(umma_gemm_kernel<K_, NP_, BN_, EPI, RB_>,
+        cudaError_t r = cudaFuncSetAttribute(umma_gemm_kernel<K_, NP_, BN_, EPI, RB_, CG_>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (r != cudaSuccess) e = r;
       });
@@ -785,14 +909,14 @@ cudaError_t set_attr_epi(int prec) {
 }
 
 template <int EPI>
-int max_clusters(int prec, int bn, int rb, int ccx, int ccy, dim3 grid) {
+int max_clusters(int prec, int bn, int rb, int cg, int ccx, int ccy, dim3 grid) {
   int n = 0;
-  visit_variant(prec, bn, rb, [&](auto kind, auto npass, auto bnc, auto rbc) {
+  visit_variant(prec, bn, rb, cg, [&](auto kind, auto npass, auto bnc, auto rbc, auto cgc) {
     OFA_VARIANT_TYPES;
     cudaLaunchAttribute attr[2];
     cudaLaunchConfig_t cfg = make_cfg(grid, Warps<EPI>::THREADS, C::SMEM, 0, attr, ccx, ccy);
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&n, umma_gemm_kernel<K_, NP_, BN_, EPI, RB_>, &cfg) !=
+    if (cudaOccupancyMaxActiveClusters(&n, umma_gemm_kernel<K_, NP_, BN_, EPI, RB_, CG_>, &cfg) !=
         cudaSuccess) {
       cudaGetLastError();
       n = 0;
@@ -840,24 +964,32 @@ bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err);
 
 namespace {
 struct TuneResult {
-  int fwd_bn, fwd_split, fwd_rb, fwd_ccx, fwd_ccy, bwd_bn, bwd_rb, bwd_ccx, bwd_ccy;
+  int fwd_bn, fwd_split, fwd_rb, fwd_ccx, fwd_ccy, fwd_cg, bwd_bn, bwd_rb, bwd_ccx, bwd_ccy,
+      bwd_cg;
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, TuneResult> g_tune_cache;
 
-int cluster_shape_ok(ofa_plan* p, int epi, int bn, int rb, int n_tiles, int m_tiles, int z,
-                     int ccx, int ccy) {
-  if (n_tiles % ccx != 0 || m_tiles % ccy != 0) return 0;
-  if (ccx * ccy == 1) return 1;
+int cluster_shape_ok(ofa_plan* p, int epi, int bn, int rb, int cg, int n_tiles, int m_tiles,
+                     int z, int ccx, int ccy) {
   dim3 grid(n_tiles, m_tiles, z);
-  if (epi == EPI_FWD) return max_clusters<EPI_FWD>(p->precision, bn, rb, ccx, ccy, grid);
-  return max_clusters<EPI_BWD>(p->precision, bn, rb, ccx, ccy, grid);
+  if (cg == 2) {  // a 2-SM pair: 2 x 1 cluster over a grid with the row tiles on x
+    if (ccx * ccy != 1 || m_tiles % 2 != 0) return 0;
+    grid = dim3(m_tiles, n_tiles, z);
+    ccx = 2;
+  } else if (n_tiles % ccx != 0 || m_tiles % ccy != 0) {
+    return 0;
+  }
+  if (ccx * ccy == 1) return 1;
+  if (epi == EPI_FWD) return max_clusters<EPI_FWD>(p->precision, bn, rb, cg, ccx, ccy, grid);
+  return max_clusters<EPI_BWD>(p->precision, bn, rb, cg, ccx, ccy, grid);
 }
 
 void apply(TcOperands& t, const TuneResult& r) {
   t.fwd_bn = r.fwd_bn; t.fwd_split = r.fwd_split; t.fwd_rb = r.fwd_rb;
-  t.fwd_ccx = r.fwd_ccx; t.fwd_ccy = r.fwd_ccy;
+  t.fwd_ccx = r.fwd_ccx; t.fwd_ccy = r.fwd_ccy; t.fwd_cg = r.fwd_cg;
   t.bwd_bn = r.bwd_bn; t.bwd_rb = r.bwd_rb; t.bwd_ccx = r.bwd_ccx; t.bwd_ccy = r.bwd_ccy;
+  t.bwd_cg = r.bwd_cg;
 }
 }  // namespace
 
@@ -871,6 +1003,9 @@ bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
       return true;
     }
   }
+  // OFA_AUTOTUNE_VERBOSE=1 prints every candidate's time to stderr
+  const char* venv = getenv("OFA_AUTOTUNE_VERBOSE");
+  const bool verbose = venv != nullptr && venv[0] == '1';
   // Scratch outputs: the inverse candidates must not touch the loop's phase and field.
   float* phi_scratch = nullptr;
   const size_t e_bytes = (size_t)p->nyp * 2 * p->nxp * t.elem_bytes;
@@ -883,11 +1018,14 @@ bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
   if (!ok) err = "allocating autotune scratch";
   const int tiles_m = p->nyp / BM;
   const int reps = 5;
-  // OFA_AUTOTUNE_VERBOSE=1 prints every candidate's time to stderr
-  const char* venv = getenv("OFA_AUTOTUNE_VERBOSE");
-  const bool verbose = venv != nullptr && venv[0] == '1';
   auto time_it = [&](auto&& launch) -> float {
     launch();  // warm-up
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) {
+      if (verbose) fprintf(stderr, "ofa autotune: candidate not launchable: %s\n",
+                           cudaGetErrorString(le));
+      return 1e30f;
+    }
     cudaEventRecord(e0, p->stream);
     for (int r = 0; r < reps; ++r) launch();
     cudaEventRecord(e1, p->stream);
@@ -899,54 +1037,57 @@ bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
   };
   const int cl[4][2] = {{1, 1}, {2, 2}, {2, 1}, {1, 2}};
   float best_f = 1e30f, best_b = 1e30f;
-  TuneResult res = {t.fwd_bn, t.fwd_split, t.fwd_rb, 1, 1, t.bwd_bn, t.bwd_rb, 1, 1};
-  for (int rb : {128, 64}) {
-    const int kb_fwd = (2 * p->nxp * t.elem_bytes) / rb;
+  TuneResult res = {t.fwd_bn, t.fwd_split, 128, 1, 1, 1, t.bwd_bn, 128, 1, 1, 1};
+  const int rb = 128;
+  const int kb_fwd = (2 * p->nxp * t.elem_bytes) / rb;
+  for (int cg : {1, 2}) {
     for (int bn : {128, 256}) {
       for (int split = 1; split <= 4 && ok; split *= 2) {
         if (kb_fwd / split < 4) break;
         for (auto& c : cl) {
           const int n_tiles = (2 * p->kp) / bn;
-          if (!cluster_shape_ok(p, EPI_FWD, bn, rb, n_tiles, tiles_m, split, c[0], c[1]))
+          if (!cluster_shape_ok(p, EPI_FWD, bn, rb, cg, n_tiles, tiles_m, split, c[0], c[1]))
             continue;
           TcOperands cand = t;
-          cand.fwd_bn = bn; cand.fwd_split = split; cand.fwd_rb = rb;
+          cand.fwd_bn = bn; cand.fwd_split = split; cand.fwd_rb = rb; cand.fwd_cg = cg;
           cand.fwd_ccx = c[0]; cand.fwd_ccy = c[1];
           if (!tc_encode_maps(p, cand, err)) { ok = false; break; }
           const float ms = time_it([&] { launch_fwd_tc(p, cand, nullptr, p->stream, false); });
           if (verbose)
-            fprintf(stderr, "ofa autotune forward bn=%d split=%d rb=%d cluster=%dx%d: %.2f us\n",
-                    bn, split, rb, c[0], c[1], 1000.f * ms / reps);
+            fprintf(stderr, "ofa autotune forward bn=%d split=%d cg=%d cluster=%dx%d: %.2f us\n",
+                    bn, split, cg, c[0], c[1], 1000.f * ms / reps);
           if (ms < best_f) {
             best_f = ms;
-            res.fwd_bn = bn; res.fwd_split = split; res.fwd_rb = rb;
+            res.fwd_bn = bn; res.fwd_split = split; res.fwd_rb = rb; res.fwd_cg = cg;
             res.fwd_ccx = c[0]; res.fwd_ccy = c[1];
           }
         }
       }
     }
   }
-  for (int rb : {128, 64}) {
+  for (int cg : {1, 2}) {
     for (int bn : {128, 256}) {
       if (!ok) break;
       for (auto& c : cl) {
         const int n_tiles = (2 * p->nxp) / bn;
-        if (!cluster_shape_ok(p, EPI_BWD, bn, rb, n_tiles, tiles_m, 1, c[0], c[1])) continue;
+        if (!cluster_shape_ok(p, EPI_BWD, bn, rb, cg, n_tiles, tiles_m, 1, c[0], c[1])) continue;
         TcOperands cand = t;
         cand.e_hi = e_scr[0];
         cand.e_lo = e_scr[1];
-        cand.bwd_bn = bn; cand.bwd_rb = rb; cand.bwd_ccx = c[0]; cand.bwd_ccy = c[1];
+        cand.bwd_bn = bn; cand.bwd_rb = rb; cand.bwd_cg = cg;
+        cand.bwd_ccx = c[0]; cand.bwd_ccy = c[1];
         if (!tc_encode_maps(p, cand, err)) { ok = false; break; }
         float* keep = p->phi;
         p->phi = phi_scratch;
         const float ms = time_it([&] { launch_bwd_tc(p, cand, nullptr, p->stream); });
         p->phi = keep;
         if (verbose)
-          fprintf(stderr, "ofa autotune inverse bn=%d rb=%d cluster=%dx%d: %.2f us\n", bn, rb,
+          fprintf(stderr, "ofa autotune inverse bn=%d cg=%d cluster=%dx%d: %.2f us\n", bn, cg,
                   c[0], c[1], 1000.f * ms / reps);
         if (ms < best_b) {
           best_b = ms;
-          res.bwd_bn = bn; res.bwd_rb = rb; res.bwd_ccx = c[0]; res.bwd_ccy = c[1];
+          res.bwd_bn = bn; res.bwd_rb = rb; res.bwd_cg = cg;
+          res.bwd_ccx = c[0]; res.bwd_ccy = c[1];
         }
       }
     }
@@ -969,8 +1110,9 @@ bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err) {
   const uint64_t e_cols = 2 * (uint64_t)p->nxp, k_cols = 2 * (uint64_t)p->kp;
   bool ok = true;
   // boxes are the per-CTA slices of a cluster's multicast (whole tiles without clusters)
-  const uint32_t e_box = BM / t.fwd_ccx, bx_box = t.fwd_bn / t.fwd_ccy;
-  const uint32_t p_box = BM / t.bwd_ccx, q_box = t.bwd_bn / t.bwd_ccy;
+  // a 2-SM pair loads half of the B tile per CTA
+  const uint32_t e_box = BM / t.fwd_ccx, bx_box = t.fwd_bn / (t.fwd_ccy * t.fwd_cg);
+  const uint32_t p_box = BM / t.bwd_ccx, q_box = t.bwd_bn / (t.bwd_ccy * t.bwd_cg);
   const int fr = t.fwd_rb, br = t.bwd_rb;
   ok = ok && encode(&t.tm_e_hi, t.e_hi, eb, e_cols, p->nyp, e_box, fr, err);
   ok = ok && encode(&t.tm_bx_hi, t.bx_hi, eb, e_cols, 2 * (uint64_t)p->kp, bx_box, fr, err);
@@ -1010,7 +1152,7 @@ void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream
     ep.stw = p->st;
     ep.weighting = p->weighting;
   }
-  launch_gemm<EPI_FWD>(p->precision, t.fwd_bn, t.fwd_rb, t.fwd_ccx, t.fwd_ccy, t.tm_e_hi,
+  launch_gemm<EPI_FWD>(p->precision, t.fwd_bn, t.fwd_rb, t.fwd_cg, t.fwd_ccx, t.fwd_ccy, t.tm_e_hi,
                        t.tm_e_lo, t.tm_bx_hi, t.tm_bx_lo, grid, kbps, kb_total, ep, done, s);
 }
 
@@ -1021,7 +1163,7 @@ void launch_bwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream
   ep.out = p->phi;
   ep.e_hi = t.e_hi;
   ep.e_lo = t.e_lo;
-  launch_gemm<EPI_BWD>(p->precision, t.bwd_bn, t.bwd_rb, t.bwd_ccx, t.bwd_ccy, t.tm_p_hi,
+  launch_gemm<EPI_BWD>(p->precision, t.bwd_bn, t.bwd_rb, t.bwd_cg, t.bwd_ccx, t.bwd_ccy, t.tm_p_hi,
                        t.tm_p_lo, t.tm_q_hi, t.tm_q_lo, grid, kb_total, kb_total, ep, done, s);
 }
 
@@ -1033,6 +1175,6 @@ void launch_grad_tc(ofa_plan* p, const TcOperands& t, const float* phi, float sc
   EpiArgs ep = base_args(p);
   ep.out = grad;
   ep.phi_in = phi;
-  launch_gemm<EPI_GRAD>(p->precision, t.bwd_bn, t.bwd_rb, t.bwd_ccx, t.bwd_ccy, t.tm_p_hi,
+  launch_gemm<EPI_GRAD>(p->precision, t.bwd_bn, t.bwd_rb, t.bwd_cg, t.bwd_ccx, t.bwd_ccy, t.tm_p_hi,
                         t.tm_p_lo, t.tm_q_hi, t.tm_q_lo, grid, kb_total, kb_total, ep, nullptr, s);
 }

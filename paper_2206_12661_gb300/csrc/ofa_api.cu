@@ -299,12 +299,12 @@ ofa_status ofa_check_foci(int n_foci, const double* xy, double px, double py, do
 
 ofa_status ofa_plan_config(const ofa_plan* p, int* c) {
   if (!p || !c) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "NULL argument");
-  for (int i = 0; i < 10; ++i) c[i] = 0;
+  for (int i = 0; i < 12; ++i) c[i] = 0;
   if (!prec_is_tc(p->precision)) return OFA_OK;
   const TcOperands& t = p->tc;
   c[0] = t.fwd_bn; c[1] = t.fwd_split; c[2] = t.fwd_ccx; c[3] = t.fwd_ccy;
   c[4] = t.bwd_bn; c[5] = t.bwd_ccx; c[6] = t.bwd_ccy; c[7] = p->K <= 4096 ? 1 : 0;
-  c[8] = t.fwd_rb; c[9] = t.bwd_rb;
+  c[8] = t.fwd_rb; c[9] = t.bwd_rb; c[10] = t.fwd_cg; c[11] = t.bwd_cg;
   return OFA_OK;
 }
 

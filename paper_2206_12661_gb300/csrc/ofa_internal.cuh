@@ -53,6 +53,7 @@ struct TcOperands {
   CUtensorMap tm_e_hi, tm_e_lo, tm_bx_hi, tm_bx_lo, tm_p_hi, tm_p_lo, tm_q_hi, tm_q_lo;
   int fwd_bn = 256, fwd_split = 1, bwd_bn = 256;
   int fwd_rb = 128, bwd_rb = 128;                          // operand row bytes per stage
+  int fwd_cg = 1, bwd_cg = 1;                              // 2 = 2-SM MMA pairs
   int fwd_ccx = 1, fwd_ccy = 1, bwd_ccx = 1, bwd_ccy = 1;  // thread-block cluster shapes
 };
 

@@ -205,10 +205,11 @@ def ofa_profile_kernels(plan, reps: int = 20) -> np.ndarray:
 
 
 def ofa_plan_config(plan) -> dict:
-    c = np.zeros(10, dtype=np.int32)
+    c = np.zeros(12, dtype=np.int32)
     _check(_lib.ofa_plan_config(plan, _ptr(c)), plan)
     keys = ["fwd_bn", "fwd_split", "fwd_cluster_x", "fwd_cluster_y", "inv_bn", "inv_cluster_x",
-            "inv_cluster_y", "focal_fused", "fwd_row_bytes", "inv_row_bytes"]
+            "inv_cluster_y", "focal_fused", "fwd_row_bytes", "inv_row_bytes", "fwd_cta_group",
+            "inv_cta_group"]
     return dict(zip(keys, (int(x) for x in c)))
 
 
