@@ -210,6 +210,35 @@ ofa_status ofa_batch_create(ofa_batch** out, ofa_plan* const* plans, int count, 
 ofa_status ofa_batch_iterate(ofa_batch* batch, int n_iter);
 ofa_status ofa_batch_destroy(ofa_batch* batch);
 
+/*
+ * ofa_forward_noalloc -- the focal field at the foci for callers that cannot
+ * allocate device memory: a real-time loop refreshing an SLM hologram that must
+ * not pay for (or fail in) cudaMalloc once it runs, or an application whose
+ * device memory is all reserved by a framework allocator.  It needs no plan:
+ * theta_k = sum over the pupil of A exp(i phi) exp(-i 2 pi (x_k u + y_k v)/(lambda f)),
+ * the same quantity as ofa_forward, computed in FP32 with the DFT phase arguments
+ * reduced in FP64.  (The paper has no counterpart; this is a calling convention.)
+ *   nx, ny, pitches, wavelength, focal_length, n_foci   as for ofa_plan_create;
+ *                          ny <= 2048, n_foci <= 8192, nx <= 32768, else
+ *                          OFA_ERR_INVALID_ARG (the limits of the built-in scratch)
+ *   focus_xy               device [K][2] float64 (m); foci are not range-checked
+ *   phi, amplitude         device [ny][nx] float32
+ *   theta                  device [K] complex output (nullable)
+ *   intensity              device [K] output |theta|^2 (nullable; not both NULL)
+ *   cuda_stream            cudaStream_t the work is enqueued on (NULL = legacy stream)
+ * Allocates nothing: its scratch is a 2 MiB static device array that every GPU
+ * loading the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU race and must be serialised by the caller.  Enqueues only;
+ * no synchronisation.
+ */
+ofa_status ofa_forward_noalloc(int nx, int ny, double pitch_x, double pitch_y,
+                               double wavelength, double focal_length, int n_foci,
+                               const double* focus_xy, const float* phi,
+                               const float* amplitude, float* theta, float* intensity,
+                               void* cuda_stream);
+
 /* Host-only helpers (no GPU needed). */
 
 /* Zero-padded FFT size of the conventional IFTA along one axis, Eq. 3:

@@ -73,6 +73,7 @@ SIGNATURES = [
     ("ofa_batch_create", _I, [C.POINTER(_P), C.POINTER(_P), _I, _P]),
     ("ofa_batch_iterate", _I, [_P, _I]),
     ("ofa_batch_destroy", _I, [_P]),
+    ("ofa_forward_noalloc", _I, [_I, _I, _D, _D, _D, _D, _I, _P, _P, _P, _P, _P, _P]),
     ("ofa_fft_equivalent_size", _I, [_I, _D, _D, _D, _D, C.POINTER(_I)]),
     ("ofa_max_foci_per_axis", _I, [_D, _D, _D, _D, C.POINTER(_I)]),
     ("ofa_check_foci", _I, [_I, _P, _D, _D, _D, _D, C.POINTER(_I)]),
@@ -232,6 +233,16 @@ def ofa_batch_iterate(batch, n_iter: int):
 
 def ofa_batch_destroy(batch):
     _check(_lib.ofa_batch_destroy(batch))
+
+
+def ofa_forward_noalloc(nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy, phi,
+                        amplitude, theta=None, intensity=None, stream=None):
+    """Plan-free focal field at the foci; every array is a device pointer/tensor."""
+    k = int(focus_xy.shape[0])
+    _check(_lib.ofa_forward_noalloc(int(nx), int(ny), float(pitch_x), float(pitch_y),
+                                    float(wavelength), float(focal_length), k, _ptr(focus_xy),
+                                    _ptr(phi), _ptr(amplitude), _ptr(theta), _ptr(intensity),
+                                    stream))
 
 
 def ofa_fft_equivalent_size(m0, pitch, wavelength, focal_length, focal_sampling) -> int:
