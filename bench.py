@@ -37,6 +37,10 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # FP32 FMA peak of the CUDA cores: 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu --set full
+# capture of the kernel as it stands (cold caches, 1024^2 pupil, 1000 foci); an entry
+# is removed whenever that kernel changes.
+NCU_TRAFFIC_BYTES = {("f16x3", "forward"): 33638912}
 
 
 def load_peaks():
@@ -142,6 +146,38 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- distributed
+def bench_differentiation(ofa, I, torch, stream, flush, precision: str = "f16x3",
+                          steps: int = 200) -> dict:
+    """Adam on the focal-intensity loss (1024^2 pupil, 20x20 grid, random targets).
+
+    One step = FocusIntensity forward (field planes, forward product, focal output),
+    the loss and its gradient in torch, the library's adjoint (c_k = g_k Theta_k,
+    inverse left operand, inverse product with the gradient epilogue), and
+    torch's Adam update.  Timed with CUDA events on the plan's stream."""
+    from paper_2206_12661_gb300 import autograd as AG
+    w = I.named("pupil1024_grid400_adam")
+    with torch.cuda.stream(stream):
+        plan = ofa.Plan.from_workload(w, precision=precision, stream=stream.cuda_stream)
+        phi0 = torch.from_numpy(w.phi0).cuda()
+        tgt = torch.from_numpy(w.target).cuda()
+        AG.optimize_adam(plan, phi0, tgt, 10, lr=0.05)          # warm-up
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, losses = AG.optimize_adam(plan, phi0, tgt, steps, lr=0.05)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan.close()
+    ms = e0.elapsed_time(e1)
+    flop = 2 * 8.0 * w.nx * w.ny * w.n_foci
+    return {"workload": "pupil1024_grid400_adam", "precision": precision, "steps": steps,
+            "adam_steps_per_s": steps / (ms / 1000.0), "ms_per_step": ms / steps,
+            "tflops_products": flop * steps / (ms / 1000.0) / 1e12,
+            "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+            "library_launches_per_step": 6}
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -266,7 +302,9 @@ def main():
         roof = {"bound": "tensor", "peak": peaks["bf16_tflops"],
                 "peak_source": f"{peak_src} bf16 dense burst (kernel timed alone)"}
     roofline = {"bound": roof["bound"], "achieved": achieved, "peak": roof["peak"],
-                "unit": "TFLOP/s", "frac": achieved / roof["peak"], "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / roof["peak"],
+                "traffic": NCU_TRAFFIC_BYTES.get((args.precision,
+                                                  "forward" if dom == 0 else "inverse")),
                 "kernel": "forward product + per-focus dot" if dom == 0
                 else "inverse product + phase projection",
                 "algorithmic_flop_per_launch": flops_per_product,
@@ -288,7 +326,9 @@ def main():
                          "parallelism": f"replicas x{world}",
                          "kernels": kernel_config},
               "roofline": roofline, "clocks": clocks}
-    kernels_per_iter = 3 if args.precision == "fp32" else 4
+    # fp32: forward, focal, inverse; tensor-core forms: forward (+ fused focal step up
+    # to 4096 foci, else a separate focal kernel), inverse operand build, inverse
+    kernels_per_iter = 3 if (args.precision == "fp32" or w.n_foci <= 4096) else 4
     result["gpu_launches"] = args.steps * (n_iter * kernels_per_iter + 1)
 
     if rank == 0 and not args.no_e2e:
@@ -333,6 +373,7 @@ def main():
                            "kernels": ofa.ofa_plan_config(p.handle)}
             p.close()
         result["forms"] = forms
+        result["differentiation"] = bench_differentiation(ofa, I, torch, stream, flush)
 
     plan.close()
     if rank == 0 and not args.no_cpu_baseline:
