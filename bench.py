@@ -153,21 +153,24 @@ def bench_differentiation(ofa, I, torch, stream, flush, precision: str = "f16x3"
     One step = FocusIntensity forward (field planes, forward product, focal output),
     the loss and its gradient in torch, the library's adjoint (c_k = g_k Theta_k,
     inverse left operand, inverse product with the gradient epilogue), and
-    torch's Adam update.  Timed with CUDA events on the plan's stream."""
+    torch's Adam update, captured once as a CUDA graph and replayed.  Timed with
+    CUDA events on the plan's stream after 10 warm-up steps."""
     from paper_2206_12661_gb300 import autograd as AG
     w = I.named("pupil1024_grid400_adam")
     with torch.cuda.stream(stream):
         plan = ofa.Plan.from_workload(w, precision=precision, stream=stream.cuda_stream)
         phi0 = torch.from_numpy(w.phi0).cuda()
         tgt = torch.from_numpy(w.target).cuda()
-        AG.optimize_adam(plan, phi0, tgt, 10, lr=0.05)          # warm-up
+        loop = AG.AdamLoop(plan, phi0, tgt, steps + 10, lr=0.05, stream=stream, graph=True)
+        loop.run(10)                                           # warm-up
         torch.cuda.synchronize()
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, losses = AG.optimize_adam(plan, phi0, tgt, steps, lr=0.05)
+        loop.run(steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        losses = loop.losses.cpu().numpy()
         plan.close()
     ms = e0.elapsed_time(e1)
     flop = 2 * 8.0 * w.nx * w.ny * w.n_foci
@@ -175,7 +178,57 @@ def bench_differentiation(ofa, I, torch, stream, flush, precision: str = "f16x3"
             "adam_steps_per_s": steps / (ms / 1000.0), "ms_per_step": ms / steps,
             "tflops_products": flop * steps / (ms / 1000.0) / 1e12,
             "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
-            "library_launches_per_step": 6}
+            "cuda_graph": True, "library_launches_per_step": 6}
+
+
+def bench_batch(ofa, I, torch, stream, flush, n_iter: int = 50) -> dict:
+    """256 holograms, pupils 512^2 / 768^2 / 1024^2, 16..4096 foci (log-uniform),
+    jittered grids, 50 iterations: the grouped batch (f16x3), the same plans run
+    plan after plan, and the plain FP32 form plan after plan.  Unit: hologram
+    iterations per second.  Timed with CUDA events on one stream after a warm-up."""
+    ws = I.batch_workloads(count=256, n_iter=n_iter, seed=5)
+    flop = sum(16.0 * w.nx * w.ny * w.n_foci for w in ws) * n_iter
+    units = len(ws) * n_iter
+    out = {"workload": "256 holograms, N in {512, 768, 1024}, K log-uniform 16..4096, "
+                       f"{n_iter} iterations each, seed 5", "holograms": len(ws),
+           "iterations": n_iter, "unit": "hologram-iterations/s",
+           "flop_per_run": flop}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0
+
+    plans = [ofa.Plan.from_workload(w, precision="f16x3", stream=stream.cuda_stream,
+                                    autotune=False) for w in ws]
+    b = ofa.ofa_batch_create([p.handle for p in plans], stream.cuda_stream)
+    out["grouped"] = ofa.ofa_batch_info(b)
+    ofa.ofa_batch_iterate(b, 2)                        # warm-up (graph for 2)
+    ofa.ofa_batch_iterate(b, n_iter)                   # builds the n-iteration graph
+    t = timed(lambda: ofa.ofa_batch_iterate(b, n_iter))
+    ofa.ofa_batch_destroy(b)
+    out["batched_f16x3"] = units / t
+    out["batched_tflops"] = flop / t / 1e12
+    for p in plans:
+        p.iterate(1)
+    t = timed(lambda: [p.iterate(n_iter) for p in plans])
+    out["plan_after_plan_f16x3"] = units / t
+    for p in plans:
+        p.close()
+    fp32 = [ofa.Plan.from_workload(w, precision="fp32", stream=stream.cuda_stream)
+            for w in ws]
+    for p in fp32:
+        p.iterate(1)
+    t = timed(lambda: [p.iterate(n_iter) for p in fp32])
+    out["plain_fp32_plan_after_plan"] = units / t
+    for p in fp32:
+        p.close()
+    return out
 
 
 def dist_setup(args):
@@ -374,6 +427,7 @@ def main():
             p.close()
         result["forms"] = forms
         result["differentiation"] = bench_differentiation(ofa, I, torch, stream, flush)
+        result["batch"] = bench_batch(ofa, I, torch, stream, flush)
 
     plan.close()
     if rank == 0 and not args.no_cpu_baseline:

@@ -202,13 +202,27 @@ ofa_status ofa_plan_info(const ofa_plan* plan, int* nx, int* ny, int* n_foci, in
 
 /*
  * Batched holograms: many independent problems of uneven pupil size and focus
- * count advanced together, every iteration of all of them in one persistent
- * kernel launch per phase, captured in a CUDA graph.  The plans keep their own
- * buffers and state and must share one device; the batch owns its scheduler.
+ * count advanced together (the paper optimises one hologram at a time; batching is
+ * a calling convention over the same loop).  When every plan uses one tensor-core
+ * precision and has at most 4096 foci, each iteration of all plans is three
+ * grouped launches (forward product with the per-plan focal step fused, inverse
+ * operand build, inverse product), each covering the tiles of every plan, largest
+ * problems first, with the tile widths timed on this batch at creation; otherwise
+ * the plans' own iterations run one after another.  n iterations are one CUDA
+ * graph launch on cuda_stream.
+ *   plans        host array of count (>= 1) plan handles on one device; the plans
+ *                keep their own buffers and state and must outlive the batch
+ *   cuda_stream  cudaStream_t the batch's iterations are enqueued on
+ * ofa_batch_create synchronises the device (the grouped set-up times candidate
+ * kernels); ofa_batch_iterate only enqueues.  A plan must not be iterated on its
+ * own while a batch iteration of it is in flight.
  */
 ofa_status ofa_batch_create(ofa_batch** out, ofa_plan* const* plans, int count, void* cuda_stream);
 ofa_status ofa_batch_iterate(ofa_batch* batch, int n_iter);
 ofa_status ofa_batch_destroy(ofa_batch* batch);
+/* 1 in *grouped when the batch runs grouped launches (then the forward and inverse
+ * tile widths), else 0 and zeros.  Any output may be NULL. */
+ofa_status ofa_batch_info(const ofa_batch* batch, int* grouped, int* fwd_bn, int* inv_bn);
 
 /*
  * ofa_forward_noalloc -- the focal field at the foci for callers that cannot

@@ -46,20 +46,65 @@ def intensity_loss(inten: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
     return torch.sum((inten / inten.sum() - t) ** 2)
 
 
-def optimize_adam(plan: "ofa.Plan", phi0: torch.Tensor, target: torch.Tensor, steps: int,
-                  lr: float = 0.05, betas=(0.9, 0.999), eps: float = 1e-8):
-    """Adam on phi for the intensity loss; returns (phi, per-step losses).
+class AdamLoop:
+    """Adam on phi for the intensity loss, one step at a time or as a CUDA graph.
 
-    The plan must have been created with stream=torch.cuda.current_stream().cuda_stream
-    so that the library's kernels and torch's run in one order.
+    The plan must enqueue on the stream the torch work runs on: `stream` if given
+    (the plan created with stream=stream.cuda_stream), else torch's current stream.
+    graph=True captures one whole step (forward, loss, backward through the adjoint
+    kernels, Adam update, loss record) in a CUDA graph that run() replays; one eager
+    step first creates the optimiser state and the plan's field planes and is then
+    undone, so the trajectory is the eager one.  A graph needs a stream other than
+    the legacy default stream.
     """
-    phi = phi0.detach().clone().requires_grad_(True)
-    opt = torch.optim.Adam([phi], lr=lr, betas=betas, eps=eps)
-    losses = torch.empty(steps, device=phi.device)
-    for i in range(steps):
-        opt.zero_grad(set_to_none=True)
-        loss = intensity_loss(focus_intensity(phi, plan), target)
+
+    def __init__(self, plan: "ofa.Plan", phi0: torch.Tensor, target: torch.Tensor,
+                 max_steps: int, lr: float = 0.05, betas=(0.9, 0.999), eps: float = 1e-8,
+                 stream: torch.cuda.Stream | None = None, graph: bool = False):
+        self.plan, self.target = plan, target
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.graph = None
+        with torch.cuda.stream(self.stream):
+            self.phi = phi0.detach().clone().requires_grad_(True)
+            self.losses = torch.zeros(max_steps, device=self.phi.device)
+            self.idx = torch.zeros(1, dtype=torch.long, device=self.phi.device)
+            self.opt = torch.optim.Adam([self.phi], lr=lr, betas=betas, eps=eps,
+                                        capturable=graph)
+            if graph:
+                self._step()           # warm-up: optimiser state, field planes
+                with torch.no_grad():
+                    self.phi.copy_(phi0)
+                    for st in self.opt.state.values():
+                        for v in st.values():
+                            v.zero_()
+                    self.idx.zero_()
+                self.opt.zero_grad(set_to_none=True)
+                self.graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.graph, stream=self.stream):
+                    self._step()
+
+    def _step(self):
+        loss = intensity_loss(focus_intensity(self.phi, self.plan), self.target)
         loss.backward()
-        opt.step()
-        losses[i] = loss.detach()
-    return phi.detach(), losses
+        self.opt.step()
+        self.losses.index_copy_(0, self.idx, loss.detach().view(1))
+        self.idx.add_(1)
+
+    def run(self, steps: int):
+        """Enqueue `steps` Adam steps (no synchronisation)."""
+        with torch.cuda.stream(self.stream):
+            for _ in range(steps):
+                if self.graph is not None:
+                    self.graph.replay()
+                else:
+                    self.opt.zero_grad(set_to_none=True)
+                    self._step()
+
+
+def optimize_adam(plan: "ofa.Plan", phi0: torch.Tensor, target: torch.Tensor, steps: int,
+                  lr: float = 0.05, betas=(0.9, 0.999), eps: float = 1e-8,
+                  stream: torch.cuda.Stream | None = None, graph: bool = False):
+    """`steps` Adam steps from phi0; returns (phi, per-step losses) (see AdamLoop)."""
+    loop = AdamLoop(plan, phi0, target, steps, lr, betas, eps, stream, graph)
+    loop.run(steps)
+    return loop.phi.detach(), loop.losses

@@ -323,7 +323,57 @@ __global__ void build_p_kernel(const float2* __restrict__ fyT, const float2* __r
   }
 }
 
+// The same operand build over many plans: block b converts quads
+// [chunks[b].y, chunks[b].z) of plan chunks[b].x.
+__global__ void build_p_group_kernel(const BpGroupItem* __restrict__ items,
+                                     const int4* __restrict__ chunks, int prec) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int4 ch = chunks[blockIdx.x];
+  const BpGroupItem it = items[ch.x];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const bool wide = prec == OFA_PREC_TF32;
+  for (int i = ch.y + (int)threadIdx.x; i < ch.z; i += blockDim.x) {
+    const size_t e0 = 4 * (size_t)i;
+    const int k0 = (int)(e0 % it.kp);
+    const float4 f01 = __ldg(reinterpret_cast<const float4*>(it.fyT + e0));
+    const float4 f23 = __ldg(reinterpret_cast<const float4*>(it.fyT + e0) + 1);
+    const float4 c01 = __ldg(reinterpret_cast<const float4*>(it.c + k0));
+    const float4 c23 = __ldg(reinterpret_cast<const float4*>(it.c + k0) + 1);
+    const float fr[4] = {f01.x, f01.z, f23.x, f23.z}, fi[4] = {f01.y, f01.w, f23.y, f23.w};
+    const float cr[4] = {c01.x, c01.z, c23.x, c23.z}, ci[4] = {c01.y, c01.w, c23.y, c23.w};
+    uint2 h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      split_pack(prec, fr[j] * cr[j] + fi[j] * ci[j], fr[j] * ci[j] - fi[j] * cr[j], h[j], l[j]);
+    if (wide) {
+      uint4* dst = reinterpret_cast<uint4*>(static_cast<float*>(it.hi) + 2 * e0);
+      dst[0] = make_uint4(h[0].x, h[0].y, h[1].x, h[1].y);
+      dst[1] = make_uint4(h[2].x, h[2].y, h[3].x, h[3].y);
+    } else {
+      reinterpret_cast<uint4*>(static_cast<uint16_t*>(it.hi) + 2 * e0)[0] =
+          make_uint4(h[0].x, h[1].x, h[2].x, h[3].x);
+      if (it.lo != nullptr)
+        reinterpret_cast<uint4*>(static_cast<uint16_t*>(it.lo) + 2 * e0)[0] =
+            make_uint4(l[0].x, l[1].x, l[2].x, l[3].x);
+    }
+  }
+}
+
 }  // namespace
+
+void launch_build_p_group(const BpGroupItem* items, const int4* chunks, int n_chunks, int prec,
+                          cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)n_chunks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, build_p_group_kernel, items, chunks, prec);
+}
 
 void launch_focal(const float2* part, int n_part, int kp, int K, const float* t, float* w,
                   float2* theta, float* inten, float2* c, double* hist, OfaDevState* st, int mode,

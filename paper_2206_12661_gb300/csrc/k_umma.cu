@@ -27,6 +27,7 @@
 // raises OFA_ERRBIT_TIMEOUT and the CTA drains and frees TMEM before exiting.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -34,6 +35,7 @@
 #include <mutex>
 #include <tuple>
 #include <type_traits>
+#include <vector>
 
 #include "ofa_internal.cuh"
 #ifdef OFA_PHASE_TRACE
@@ -385,13 +387,17 @@ struct Cfg {
   static_assert(STAGES >= 2, "need at least two stages");
 };
 
+// One output tile (rows m_tile*128.., accumulator columns n_tile*BN..) over the
+// k-blocks [kb0, kb0 + nkb) of the operands behind the four tensor maps, with the
+// epilogue EPI.  tail_count: CTAs that arrive on ep.counters before the fused
+// focal step may run (all tiles of the problem).
 template <int KIND, int NPASS, int BN, int EPI, int RB, int CG>
-__global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
-    umma_gemm_kernel(const __grid_constant__ CUtensorMap tma_hi,
-                     const __grid_constant__ CUtensorMap tma_lo,
-                     const __grid_constant__ CUtensorMap tmb_hi,
-                     const __grid_constant__ CUtensorMap tmb_lo, int kb_per_split, int kb_total,
-                     EpiArgs ep, const int* __restrict__ done, int ccx, int ccy) {
+__device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUtensorMap* tma_lo,
+                                          const CUtensorMap* tmb_hi, const CUtensorMap* tmb_lo,
+                                          const int m_tile, const int n_tile, const int split,
+                                          const int kb0, const int nkb, const EpiArgs& ep,
+                                          const int* __restrict__ done, const int ccx,
+                                          const int ccy, const unsigned tail_count) {
   using C = Cfg<KIND, NPASS, BN, EPI, RB, CG>;
   constexpr bool PAIR = CG == 2;
   constexpr int WARP_TMA = Warps<EPI>::TMA, WARP_MMA = Warps<EPI>::MMA;
@@ -405,12 +411,6 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
   uint8_t* base = smem_raw + (base_u32 - raw);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // 2-SM pairs lie along the cluster's x dimension, so their grids put the row
-  // tiles on x; otherwise the column tiles are on x.
-  const int n_tile = PAIR ? blockIdx.y : blockIdx.x, m_tile = PAIR ? blockIdx.x : blockIdx.y;
-  const int split = blockIdx.z;
-  const int kb0 = split * kb_per_split;
-  const int nkb = min(kb_per_split, kb_total - kb0);
 
   const uint32_t bar_full = base_u32 + C::BAR_OFF;          // STAGES x 8 bytes
   const uint32_t bar_empty = bar_full + 8 * C::STAGES;      // STAGES x 8 bytes
@@ -442,11 +442,11 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
     fence_mbar_init();
   }
   if (warp == WARP_TMA && lane == 0) {
-    tmap_prefetch(&tma_hi);
-    tmap_prefetch(&tmb_hi);
+    tmap_prefetch(tma_hi);
+    tmap_prefetch(tmb_hi);
     if (NPASS == 3) {
-      tmap_prefetch(&tma_lo);
-      tmap_prefetch(&tmb_lo);
+      tmap_prefetch(tma_lo);
+      tmap_prefetch(tmb_lo);
     }
   }
   if (warp == WARP_MMA) tmem_alloc<CG>(slot_u32, BN);
@@ -493,32 +493,32 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
           if (leader) mbar_expect_tx(bar_full + 8 * s, 2 * C::STAGE_BYTES);
           const uint32_t fb = leader ? bar_full + 8 * s : mapa_shared(bar_full + 8 * s, crank & ~1);
           const int brow = n_tile * BN + (crank & 1) * (BN / 2);
-          tma_load_2d_pair(st, &tma_hi, fb, x, m_tile * BM);
-          tma_load_2d_pair(st + C::PLANES * C::A_BYTES, &tmb_hi, fb, x, brow);
+          tma_load_2d_pair(st, tma_hi, fb, x, m_tile * BM);
+          tma_load_2d_pair(st + C::PLANES * C::A_BYTES, tmb_hi, fb, x, brow);
           if (NPASS == 3) {
-            tma_load_2d_pair(st + C::A_BYTES, &tma_lo, fb, x, m_tile * BM);
-            tma_load_2d_pair(st + C::PLANES * C::A_BYTES + C::B_BYTES, &tmb_lo, fb, x, brow);
+            tma_load_2d_pair(st + C::A_BYTES, tma_lo, fb, x, m_tile * BM);
+            tma_load_2d_pair(st + C::PLANES * C::A_BYTES + C::B_BYTES, tmb_lo, fb, x, brow);
           }
         } else if (!mcast) {
           mbar_expect_tx(bar_full + 8 * s, C::STAGE_BYTES);
-          tma_load_2d(st, &tma_hi, bar_full + 8 * s, x, m_tile * BM);
-          tma_load_2d(st + C::PLANES * C::A_BYTES, &tmb_hi, bar_full + 8 * s, x, n_tile * BN);
+          tma_load_2d(st, tma_hi, bar_full + 8 * s, x, m_tile * BM);
+          tma_load_2d(st + C::PLANES * C::A_BYTES, tmb_hi, bar_full + 8 * s, x, n_tile * BN);
           if (NPASS == 3) {
-            tma_load_2d(st + C::A_BYTES, &tma_lo, bar_full + 8 * s, x, m_tile * BM);
-            tma_load_2d(st + C::PLANES * C::A_BYTES + C::B_BYTES, &tmb_lo, bar_full + 8 * s, x,
+            tma_load_2d(st + C::A_BYTES, tma_lo, bar_full + 8 * s, x, m_tile * BM);
+            tma_load_2d(st + C::PLANES * C::A_BYTES + C::B_BYTES, tmb_lo, bar_full + 8 * s, x,
                         n_tile * BN);
           }
         } else {
           mbar_expect_tx(bar_full + 8 * s, C::STAGE_BYTES);  // whole stage, all sources
           const int ar = BM / ccx, br = BN / ccy;   // slice rows
           const uint32_t ao = (uint32_t)(cx * ar * RB), bo = (uint32_t)(cy * br * RB);
-          tma_load_2d_mc(st + ao, &tma_hi, bar_full + 8 * s, x, m_tile * BM + cx * ar, row_mask);
-          tma_load_2d_mc(st + C::PLANES * C::A_BYTES + bo, &tmb_hi, bar_full + 8 * s, x,
+          tma_load_2d_mc(st + ao, tma_hi, bar_full + 8 * s, x, m_tile * BM + cx * ar, row_mask);
+          tma_load_2d_mc(st + C::PLANES * C::A_BYTES + bo, tmb_hi, bar_full + 8 * s, x,
                          n_tile * BN + cy * br, col_mask);
           if (NPASS == 3) {
-            tma_load_2d_mc(st + C::A_BYTES + ao, &tma_lo, bar_full + 8 * s, x,
+            tma_load_2d_mc(st + C::A_BYTES + ao, tma_lo, bar_full + 8 * s, x,
                            m_tile * BM + cx * ar, row_mask);
-            tma_load_2d_mc(st + C::PLANES * C::A_BYTES + C::B_BYTES + bo, &tmb_lo,
+            tma_load_2d_mc(st + C::PLANES * C::A_BYTES + C::B_BYTES + bo, tmb_lo,
                            bar_full + 8 * s, x, n_tile * BN + cy * br, col_mask);
           }
         }
@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
         if (t == 0) {
           __threadfence();  // ... and, cumulatively, visible GPU-wide before the arrival
           const unsigned prev = atomicAdd(ep.counters, 1u);
-          tail_flag = prev == (unsigned)(gridDim.x * gridDim.y * gridDim.z - 1);
+          tail_flag = prev == tail_count - 1u;
           if (tail_flag) {
             __threadfence();  // acquire the other CTAs' partials
             *ep.counters = 0u;
@@ -787,6 +787,46 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
   // or arrive on its barriers.
   if (clustered) cluster_sync_all();
   if (threadIdx.x == 0) OFA_STAMP(7);
+}
+
+// One plan: tile coordinates from the grid (2-SM pairs lie along the cluster's x
+// dimension, so their grids put the row tiles on x; otherwise the column tiles
+// are on x), split-K over grid z.
+template <int KIND, int NPASS, int BN, int EPI, int RB, int CG>
+__global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
+    umma_gemm_kernel(const __grid_constant__ CUtensorMap tma_hi,
+                     const __grid_constant__ CUtensorMap tma_lo,
+                     const __grid_constant__ CUtensorMap tmb_hi,
+                     const __grid_constant__ CUtensorMap tmb_lo, int kb_per_split, int kb_total,
+                     const __grid_constant__ EpiArgs ep, const int* __restrict__ done, int ccx,
+                     int ccy) {
+  constexpr bool PAIR = CG == 2;
+  const int n_tile = PAIR ? blockIdx.y : blockIdx.x, m_tile = PAIR ? blockIdx.x : blockIdx.y;
+  const int split = blockIdx.z;
+  const int kb0 = split * kb_per_split;
+  const int nkb = min(kb_per_split, kb_total - kb0);
+  umma_tile<KIND, NPASS, BN, EPI, RB, CG>(&tma_hi, &tma_lo, &tmb_hi, &tmb_lo, m_tile, n_tile,
+                                          split, kb0, nkb, ep, done, ccx, ccy,
+                                          gridDim.x * gridDim.y * gridDim.z);
+}
+
+// Many problems in one launch: block b computes tile tiles[b] = (problem, m_tile,
+// n_tile) of problem items[problem], whose tensor maps and epilogue arguments sit
+// in device memory (written once before the first launch and never modified).
+struct alignas(64) GroupItem {
+  CUtensorMap a_hi, a_lo, b_hi, b_lo;
+  EpiArgs ep;
+  int kb_total;
+  unsigned tail_count;
+};
+
+template <int KIND, int NPASS, int BN, int EPI, int RB>
+__global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
+    umma_group_kernel(const GroupItem* __restrict__ items, const int4* __restrict__ tiles) {
+  const int4 t = tiles[blockIdx.x];
+  const GroupItem* g = items + t.x;
+  umma_tile<KIND, NPASS, BN, EPI, RB, 1>(&g->a_hi, &g->a_lo, &g->b_hi, &g->b_lo, t.y, t.z, 0, 0,
+                                         g->kb_total, g->ep, nullptr, 1, 1, g->tail_count);
 }
 
 // ------------------------------------------------------------------ host side
@@ -1177,4 +1217,277 @@ void launch_grad_tc(ofa_plan* p, const TcOperands& t, const float* phi, float sc
   ep.phi_in = phi;
   launch_gemm<EPI_GRAD>(p->precision, t.bwd_bn, t.bwd_rb, t.bwd_cg, t.bwd_ccx, t.bwd_ccy, t.tm_p_hi,
                         t.tm_p_lo, t.tm_q_hi, t.tm_q_lo, grid, kb_total, kb_total, ep, nullptr, s);
+}
+
+// ------------------------------------------------------------------ batched (grouped) launches
+// Every problem of a batch shares the precision and one tile width per product;
+// each grouped launch covers all tiles of all problems, largest problems first.
+namespace {
+
+struct TcGroupSet {
+  int bn = 0;
+  GroupItem* items = nullptr;  // device [problems]
+  int4* tiles = nullptr;       // device [n_tiles]: (problem, m_tile, n_tile, 0)
+  int n_tiles = 0;
+};
+
+void free_set(TcGroupSet& s) {
+  if (s.items) cudaFree(s.items);
+  if (s.tiles) cudaFree(s.tiles);
+  s = TcGroupSet();
+}
+
+// Items of one product (EPI_FWD: forward with the fused focal step when fuse;
+// EPI_BWD: inverse, writing phi and the field planes, or the scratch outputs when
+// given) at tile width bn.
+bool build_set(const std::vector<ofa_plan*>& plans, const std::vector<int>& order, int epi,
+               int bn, bool fuse, float* out_scratch, void* e_scratch_hi, void* e_scratch_lo,
+               TcGroupSet& set, std::string& err) {
+  std::vector<GroupItem> items(plans.size());
+  std::vector<int4> tiles;
+  for (size_t h = 0; h < plans.size(); ++h) {
+    ofa_plan* p = plans[h];
+    const TcOperands& t = p->tc;
+    GroupItem& g = items[h];
+    std::memset(&g, 0, sizeof(g));
+    const int eb = t.elem_bytes;
+    const uint64_t e_cols = 2 * (uint64_t)p->nxp, k_cols = 2 * (uint64_t)p->kp;
+    bool ok = true;
+    g.ep = base_args(p);
+    if (epi == EPI_FWD) {
+      ok = ok && encode(&g.a_hi, t.e_hi, eb, e_cols, p->nyp, BM, 128, err);
+      ok = ok && encode(&g.b_hi, t.bx_hi, eb, e_cols, k_cols, bn, 128, err);
+      if (t.npass == 3) {
+        ok = ok && encode(&g.a_lo, t.e_lo, eb, e_cols, p->nyp, BM, 128, err);
+        ok = ok && encode(&g.b_lo, t.bx_lo, eb, e_cols, k_cols, bn, 128, err);
+      }
+      g.kb_total = (int)(e_cols * eb / 128);
+      g.tail_count = (unsigned)((k_cols / bn) * (p->nyp / BM));
+      if (fuse) {
+        g.ep.fuse = 1;
+        g.ep.counters = p->counters;
+        g.ep.n_tiles = (int)(k_cols / bn);
+        g.ep.n_part = p->nyp / BM;
+        g.ep.K = p->K;
+        g.ep.theta = p->theta;
+        g.ep.t = p->t;
+        g.ep.w = p->w;
+        g.ep.c = p->c;
+        g.ep.hist = p->hist;
+        g.ep.stw = p->st;
+        g.ep.weighting = p->weighting;
+      }
+    } else {
+      ok = ok && encode(&g.a_hi, t.p_hi, eb, k_cols, p->nyp, BM, 128, err);
+      ok = ok && encode(&g.b_hi, t.q_hi, eb, k_cols, e_cols, bn, 128, err);
+      if (t.npass == 3) {
+        ok = ok && encode(&g.a_lo, t.p_lo, eb, k_cols, p->nyp, BM, 128, err);
+        ok = ok && encode(&g.b_lo, t.q_lo, eb, k_cols, e_cols, bn, 128, err);
+      }
+      g.kb_total = (int)(k_cols * eb / 128);
+      g.ep.out = out_scratch ? out_scratch : p->phi;
+      g.ep.e_hi = e_scratch_hi ? e_scratch_hi : t.e_hi;
+      g.ep.e_lo = e_scratch_hi ? e_scratch_lo : t.e_lo;
+    }
+    if (t.npass != 3) {
+      g.a_lo = g.a_hi;
+      g.b_lo = g.b_hi;
+    }
+    if (!ok) return false;
+  }
+  for (int h : order) {
+    ofa_plan* p = plans[h];
+    const int cols = epi == EPI_FWD ? 2 * p->kp : 2 * p->nxp;
+    for (int m = 0; m < p->nyp / BM; ++m)
+      for (int n = 0; n < cols / bn; ++n) tiles.push_back(make_int4(h, m, n, 0));
+  }
+  set.bn = bn;
+  set.n_tiles = (int)tiles.size();
+  if (cudaMalloc(&set.items, items.size() * sizeof(GroupItem)) != cudaSuccess ||
+      cudaMalloc(&set.tiles, tiles.size() * sizeof(int4)) != cudaSuccess) {
+    err = "allocating batch tile tables";
+    return false;
+  }
+  if (cudaMemcpy(set.items, items.data(), items.size() * sizeof(GroupItem),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(set.tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    err = "uploading batch tile tables";
+    return false;
+  }
+  return true;
+}
+
+template <int EPI>
+void launch_group(int prec, const TcGroupSet& set, cudaStream_t s) {
+  visit_variant(prec, set.bn, 128, 1, [&](auto kind, auto npass, auto bnc, auto rbc, auto cgc) {
+    OFA_VARIANT_TYPES;
+    if constexpr (CG_ == 1) {
+      cudaLaunchAttribute attr[2];
+      cudaLaunchConfig_t cfg =
+          make_cfg(dim3(set.n_tiles), Warps<EPI>::THREADS, C::SMEM, s, attr, 1, 1);
+      cudaLaunchKernelEx(&cfg, umma_group_kernel<K_, NP_, BN_, EPI, RB_>, set.items, set.tiles);
+    }
+  });
+}
+
+template <int EPI>
+cudaError_t set_attr_group(int prec) {
+  cudaError_t e = cudaSuccess;
+  for (int bn : {128, 256})
+    visit_variant(prec, bn, 128, 1, [&](auto kind, auto npass, auto bnc, auto rbc, auto cgc) {
+      OFA_VARIANT_TYPES;
+      if constexpr (CG_ == 1) {
+        cudaError_t r = cudaFuncSetAttribute(umma_group_kernel<K_, NP_, BN_, EPI, RB_>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (r != cudaSuccess) e = r;
+      }
+    });
+  return e;
+}
+
+}  // namespace
+
+struct TcBatch {
+  int prec = 0;
+  std::vector<ofa_plan*> plans;
+  TcGroupSet fwd, bwd;
+  BpGroupItem* bp_items = nullptr;  // device [problems]
+  int4* bp_chunks = nullptr;        // device [n_bp]: (problem, first quad, end quad, 0)
+  int n_bp = 0;
+};
+
+void tc_batch_destroy(TcBatch* b) {
+  if (!b) return;
+  free_set(b->fwd);
+  free_set(b->bwd);
+  if (b->bp_items) cudaFree(b->bp_items);
+  if (b->bp_chunks) cudaFree(b->bp_chunks);
+  delete b;
+}
+
+void tc_batch_enqueue_iteration(const TcBatch* b, cudaStream_t s) {
+  launch_group<EPI_FWD>(b->prec, b->fwd, s);
+  launch_build_p_group(b->bp_items, b->bp_chunks, b->n_bp, b->prec, s);
+  launch_group<EPI_BWD>(b->prec, b->bwd, s);
+}
+
+void tc_batch_config(const TcBatch* b, int* fwd_bn, int* bwd_bn) {
+  *fwd_bn = b->fwd.bn;
+  *bwd_bn = b->bwd.bn;
+}
+
+bool tc_batch_create(ofa_plan* const* plans, int count, cudaStream_t s, TcBatch** out,
+                     std::string& err) {
+  *out = nullptr;
+  TcBatch* b = new TcBatch();
+  b->prec = plans[0]->precision;
+  b->plans.assign(plans, plans + count);
+  // largest problems first (per-tile work is proportional to the contraction length)
+  std::vector<int> fwd_order(count), bwd_order(count);
+  for (int i = 0; i < count; ++i) fwd_order[i] = bwd_order[i] = i;
+  std::stable_sort(fwd_order.begin(), fwd_order.end(),
+                   [&](int a, int c) { return plans[a]->nxp > plans[c]->nxp; });
+  std::stable_sort(bwd_order.begin(), bwd_order.end(),
+                   [&](int a, int c) { return plans[a]->kp > plans[c]->kp; });
+  cudaError_t ae = set_attr_group<EPI_FWD>(b->prec);
+  if (ae == cudaSuccess) ae = set_attr_group<EPI_BWD>(b->prec);
+  if (ae != cudaSuccess) {
+    err = std::string("setting grouped kernel attributes: ") + cudaGetErrorString(ae);
+    tc_batch_destroy(b);
+    return false;
+  }
+  // inverse operand build: chunks of up to 4096 quads (4 complex elements each)
+  {
+    std::vector<BpGroupItem> items(count);
+    std::vector<int4> chunks;
+    for (int h = 0; h < count; ++h) {
+      ofa_plan* p = plans[h];
+      items[h].fyT = p->fyT;
+      items[h].c = p->c;
+      items[h].hi = p->tc.p_hi;
+      items[h].lo = p->tc.p_lo;
+      items[h].kp = p->kp;
+      const int quads = p->nyp * p->kp / 4;
+      for (int q = 0; q < quads; q += 4096) chunks.push_back(make_int4(h, q, std::min(quads, q + 4096), 0));
+    }
+    b->n_bp = (int)chunks.size();
+    if (cudaMalloc(&b->bp_items, items.size() * sizeof(BpGroupItem)) != cudaSuccess ||
+        cudaMalloc(&b->bp_chunks, chunks.size() * sizeof(int4)) != cudaSuccess ||
+        cudaMemcpy(b->bp_items, items.data(), items.size() * sizeof(BpGroupItem),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->bp_chunks, chunks.data(), chunks.size() * sizeof(int4),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      err = "allocating the batch's operand-build tables";
+      tc_batch_destroy(b);
+      return false;
+    }
+  }
+  // Tile widths: time both for each product on this batch.  The forward candidates
+  // run without the focal step (they only write partials); the inverse candidates
+  // write scratch outputs, so the loop state is untouched.
+  size_t max_pix = 0, max_e = 0;
+  for (ofa_plan* p : b->plans) {
+    max_pix = std::max(max_pix, (size_t)p->nx * p->ny);
+    max_e = std::max(max_e, (size_t)p->nyp * 2 * p->nxp * p->tc.elem_bytes);
+  }
+  float* out_scr = nullptr;
+  void* e_scr[2] = {nullptr, nullptr};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok = cudaMalloc(&out_scr, max_pix * 4) == cudaSuccess &&
+            cudaMalloc(&e_scr[0], max_e) == cudaSuccess &&
+            (prec_npass(b->prec) == 1 || cudaMalloc(&e_scr[1], max_e) == cudaSuccess) &&
+            cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  if (!ok) err = "allocating batch autotune scratch";
+  auto time_it = [&](auto&& launch) -> float {
+    launch();
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3; ++r) launch();
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return cudaGetLastError() == cudaSuccess ? ms : 1e30f;
+  };
+  const char* venv = getenv("OFA_AUTOTUNE_VERBOSE");
+  const bool verbose = venv != nullptr && venv[0] == '1';
+  float best_f = 1e30f, best_b = 1e30f;
+  int bn_f = 128, bn_b = 128;
+  for (int bn : {128, 256}) {
+    if (!ok) break;
+    TcGroupSet f, w;
+    ok = build_set(b->plans, fwd_order, EPI_FWD, bn, false, nullptr, nullptr, nullptr, f, err) &&
+         build_set(b->plans, bwd_order, EPI_BWD, bn, false, out_scr, e_scr[0], e_scr[1], w, err);
+    if (ok) {
+      const float tf = time_it([&] { launch_group<EPI_FWD>(b->prec, f, s); });
+      const float tb = time_it([&] { launch_group<EPI_BWD>(b->prec, w, s); });
+      if (verbose)
+        fprintf(stderr, "ofa batch autotune bn=%d: forward %.1f us, inverse %.1f us\n", bn,
+                1000.f * tf / 3, 1000.f * tb / 3);
+      if (tf < best_f) { best_f = tf; bn_f = bn; }
+      if (tb < best_b) { best_b = tb; bn_b = bn; }
+    }
+    cudaStreamSynchronize(s);
+    free_set(f);
+    free_set(w);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out_scr);
+  cudaFree(e_scr[0]);
+  if (e_scr[1]) cudaFree(e_scr[1]);
+  ok = ok && best_f < 1e29f && best_b < 1e29f;
+  if (!ok && err.empty()) err = "no grouped kernel variant could be launched";
+  ok = ok &&
+       build_set(b->plans, fwd_order, EPI_FWD, bn_f, true, nullptr, nullptr, nullptr, b->fwd,
+                 err) &&
+       build_set(b->plans, bwd_order, EPI_BWD, bn_b, false, nullptr, nullptr, nullptr, b->bwd,
+                 err);
+  cudaGetLastError();
+  if (!ok) {
+    tc_batch_destroy(b);
+    return false;
+  }
+  *out = b;
+  return true;
 }

@@ -827,6 +827,7 @@ struct ofa_batch {
   cudaGraphExec_t exec = nullptr;
   int exec_iters = 0;
   int device = 0;
+  TcBatch* tc = nullptr;  // grouped tensor-core launches (NULL: plan after plan)
   std::string last_error;
 };
 
@@ -849,7 +850,37 @@ ofa_status ofa_batch_create(ofa_batch** out, ofa_plan* const* plans, int count, 
     delete b;
     return ofa_fail(nullptr, OFA_ERR_CUDA, "creating batch capture stream");
   }
+  // Grouped launches when every plan is on the tensor-core path with one precision
+  // and its focal step fits the forward kernel's last CTA; otherwise plan after plan.
+  bool grouped = true;
+  for (ofa_plan* p : b->plans)
+    grouped = grouped && prec_is_tc(p->precision) && p->precision == plans[0]->precision &&
+              p->K <= 4096;
+  if (grouped) {
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      cudaStreamDestroy(b->cap_stream);
+      delete b;
+      return ofa_fail(nullptr, OFA_ERR_CUDA, "synchronising before the batch set-up");
+    }
+    std::string err;
+    if (!tc_batch_create(plans, count, b->cap_stream, &b->tc, err)) {
+      cudaStreamDestroy(b->cap_stream);
+      delete b;
+      return ofa_fail(nullptr, OFA_ERR_CUDA, "batch set-up: " + err);
+    }
+    cudaStreamSynchronize(b->cap_stream);
+  }
   *out = b;
+  return OFA_OK;
+}
+
+ofa_status ofa_batch_info(const ofa_batch* b, int* grouped, int* fwd_bn, int* inv_bn) {
+  if (!b) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "batch is NULL");
+  int f = 0, i = 0;
+  if (b->tc) tc_batch_config(b->tc, &f, &i);
+  if (grouped) *grouped = b->tc != nullptr;
+  if (fwd_bn) *fwd_bn = f;
+  if (inv_bn) *inv_bn = i;
   return OFA_OK;
 }
 
@@ -864,8 +895,11 @@ ofa_status ofa_batch_iterate(ofa_batch* b, int n_iter) {
     cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return ofa_fail(nullptr, OFA_ERR_CUDA, "batch capture");
     for (ofa_plan* p : b->plans) launch_control(p->st, 0.0, 1, b->cap_stream);
-    for (int it = 0; it < n_iter; ++it)
-      for (ofa_plan* p : b->plans) enqueue_iteration(p, b->cap_stream);
+    for (int it = 0; it < n_iter; ++it) {
+      if (b->tc) tc_batch_enqueue_iteration(b->tc, b->cap_stream);
+      else
+        for (ofa_plan* p : b->plans) enqueue_iteration(p, b->cap_stream);
+    }
     e = cudaStreamEndCapture(b->cap_stream, &g);
     if (e != cudaSuccess) return ofa_fail(nullptr, OFA_ERR_CUDA, "batch capture end");
     e = cudaGraphInstantiate(&b->exec, g, 0);
@@ -885,6 +919,7 @@ ofa_status ofa_batch_destroy(ofa_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  tc_batch_destroy(b->tc);
   delete b;
   return OFA_OK;
 }

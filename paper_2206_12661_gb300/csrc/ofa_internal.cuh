@@ -154,6 +154,25 @@ void launch_bwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream
 void launch_grad_tc(ofa_plan* p, const TcOperands& t, const float* phi, float scale,
                     float* grad, cudaStream_t s);
 
+// Batched holograms on the tensor-core path: one grouped launch per product over
+// the tiles of every plan (same precision), the inverse operand build grouped too.
+struct BpGroupItem {
+  const float2* fyT;
+  const float2* c;
+  void* hi;
+  void* lo;
+  int kp;
+  int pad_;
+};
+void launch_build_p_group(const BpGroupItem* items, const int4* chunks, int n_chunks, int prec,
+                          cudaStream_t s);
+struct TcBatch;
+bool tc_batch_create(ofa_plan* const* plans, int count, cudaStream_t s, TcBatch** out,
+                     std::string& err);
+void tc_batch_enqueue_iteration(const TcBatch* b, cudaStream_t s);
+void tc_batch_config(const TcBatch* b, int* fwd_bn, int* bwd_bn);
+void tc_batch_destroy(TcBatch* b);
+
 inline bool prec_is_tc(int prec) { return prec != OFA_PREC_FP32; }
 inline int prec_elem_bytes(int prec) { return prec == OFA_PREC_TF32 ? 4 : 2; }
 inline int prec_npass(int prec) {

@@ -73,6 +73,7 @@ SIGNATURES = [
     ("ofa_batch_create", _I, [C.POINTER(_P), C.POINTER(_P), _I, _P]),
     ("ofa_batch_iterate", _I, [_P, _I]),
     ("ofa_batch_destroy", _I, [_P]),
+    ("ofa_batch_info", _I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     ("ofa_forward_noalloc", _I, [_I, _I, _D, _D, _D, _D, _I, _P, _P, _P, _P, _P, _P]),
     ("ofa_fft_equivalent_size", _I, [_I, _D, _D, _D, _D, C.POINTER(_I)]),
     ("ofa_max_foci_per_axis", _I, [_D, _D, _D, _D, C.POINTER(_I)]),
@@ -233,6 +234,12 @@ def ofa_batch_iterate(batch, n_iter: int):
 
 def ofa_batch_destroy(batch):
     _check(_lib.ofa_batch_destroy(batch))
+
+
+def ofa_batch_info(batch) -> dict:
+    g, f, i = C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(_lib.ofa_batch_info(batch, C.byref(g), C.byref(f), C.byref(i)))
+    return {"grouped": bool(g.value), "fwd_bn": f.value, "inv_bn": i.value}
 
 
 def ofa_forward_noalloc(nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy, phi,

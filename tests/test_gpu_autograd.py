@@ -155,3 +155,25 @@ def test_adam_full_size_converges(ofa, ag, prec):
     # near the optimum the FP32 loss is dominated by rounding of I: bound, not compare
     assert L < 1e-9 and xi > 0.9995, (L, xi)
     assert L_gpu < 1e-8, L_gpu
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_adam_cuda_graph_matches_oracle(ofa, ag, prec):
+    """The graph-captured step (replayed) follows the same trajectory."""
+    w = small(160, 96, 24, seed=14)
+    steps = 15
+    ref = oracle_adam(w, steps, 0.05)
+    s = torch.cuda.Stream()
+    plan = ofa.Plan.from_workload(w, precision=prec, stream=s.cuda_stream)
+    phi0 = torch.from_numpy(w.phi0).cuda()
+    tgt = torch.from_numpy(w.target).cuda()
+    torch.cuda.synchronize()
+    phi_g, loss_g = ag.optimize_adam(plan, phi0, tgt, steps, lr=0.05, stream=s, graph=True)
+    phi_e, loss_e = ag.optimize_adam(plan, phi0, tgt, steps, lr=0.05, stream=s, graph=False)
+    torch.cuda.synchronize()
+    got_g = loss_g.cpu().numpy().astype(np.float64)
+    got_e = loss_e.cpu().numpy().astype(np.float64)
+    plan.close()
+    assert np.max(np.abs(got_g - ref) / ref) < 2e-3, (got_g, ref)
+    # capturable Adam forms its bias corrections with tensor ops: rounding differs
+    assert np.max(np.abs(got_g - got_e) / got_e) < 1e-3, (got_g, got_e)

@@ -307,17 +307,87 @@ def test_create_errors_on_gpu(ofa, dev):
     assert e.value.status == ofa.OFA_ERR_INVALID_ARG
 
 
-def test_batch_matches_individual(ofa, dev):
-    ws = I.batch_workloads(count=6, sizes=(256, 384), k_min=8, k_max=300, n_iter=6, seed=11)
-    plans = [ofa.Plan.from_workload(w, precision="f16x3") for w in ws]
+def run_batch(ofa, ws, prec, n_iter, autotune=False):
+    plans = [ofa.Plan.from_workload(w, precision=prec, autotune=autotune) for w in ws]
     stream = torch.cuda.Stream()
     b = ofa.ofa_batch_create([p.handle for p in plans], stream.cuda_stream)
+    info = ofa.ofa_batch_info(b)
+    ofa.ofa_batch_iterate(b, n_iter)
+    stream.synchronize()
+    ofa.ofa_batch_destroy(b)
+    return plans, info
+
+
+def test_batch_plan_after_plan_is_bitwise(ofa, dev):
+    """Mixed precisions: the batch runs the plans' own iterations, bit for bit."""
+    ws = I.batch_workloads(count=4, sizes=(256, 384), k_min=8, k_max=300, n_iter=6, seed=11)
+    precs = ["f16x3", "fp32", "bf16", "f16x3"]
+    plans = [ofa.Plan.from_workload(w, precision=pr) for w, pr in zip(ws, precs)]
+    stream = torch.cuda.Stream()
+    b = ofa.ofa_batch_create([p.handle for p in plans], stream.cuda_stream)
+    assert ofa.ofa_batch_info(b)["grouped"] is False
     ofa.ofa_batch_iterate(b, 6)
     stream.synchronize()
     ofa.ofa_batch_destroy(b)
-    for w, p in zip(ws, plans):
-        q = ofa.Plan.from_workload(w, precision="f16x3")
+    for w, p, pr in zip(ws, plans, precs):
+        q = ofa.Plan.from_workload(w, precision=pr)
         q.iterate(6)
         assert np.array_equal(p.phase(), q.phase())
+        q.close()
+        p.close()
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "bf16"])
+def test_batch_grouped_matches_individual(ofa, dev, prec):
+    """Grouped launches over uneven holograms follow each plan's own loop: the xi
+    histories agree to rounding (the tile shapes, hence partial-sum orders, differ)."""
+    ws = I.batch_workloads(count=7, sizes=(256, 384, 512), k_min=8, k_max=700, n_iter=6,
+                           seed=12)
+    plans, info = run_batch(ofa, ws, prec, 6)
+    assert info["grouped"] is True and info["fwd_bn"] in (128, 256)
+    # the first iteration agrees to FP32 rounding; rounding differences are amplified
+    # while xi climbs steeply (seen: 2e-5 at iteration 4 of a 384^2 / 552-focus plan)
+    tol = 1e-3 if prec == "f16x3" else 1e-2
+    for w, p in zip(ws, plans):
+        q = ofa.Plan.from_workload(w, precision=prec)
+        q.iterate(6)
+        hb, hq = p.xi_history(), q.xi_history()
+        assert len(hb) == len(hq) == 6
+        assert abs(hb[0] - hq[0]) < 1e-6 and np.max(np.abs(hb - hq)) < tol, (w.name, hb, hq)
+        assert p.stats().iterations == 6
+        q.close()
+        p.close()
+
+
+def test_batch_grouped_matches_oracle(ofa, dev):
+    """Three holograms of the batch against the FP64 oracle run on each alone."""
+    ws = I.batch_workloads(count=3, sizes=(256, 384), k_min=16, k_max=200, n_iter=5, seed=13)
+    plans, info = run_batch(ofa, ws, "f16x3", 5)
+    assert info["grouped"] is True
+    for w, p in zip(ws, plans):
+        fx, fy = oracle_mats(w)
+        ref = O.gsw(w.amplitude.astype(np.float64), w.phi0.astype(np.float64), fx, fy,
+                    w.target, 5)
+        h = p.xi_history()
+        assert np.max(np.abs(h - ref["xi_hist"])) < 1e-3, (h, ref["xi_hist"])
+        p.close()
+
+
+def test_batch_grouped_uneven_large(ofa, dev):
+    """The uneven shape mix of the batched workload (N in 512..1024, K 16..4096) on a
+    subset of 12 holograms.  The first two xi values (forward, inverse, forward)
+    agree with each plan's own loop to rounding (the second within 2e-5: the two
+    inverse products accumulate in different tile shapes); later ones are not compared:
+    early GSW iterations amplify rounding (a 1024^2 / 1309-focus plan passes through
+    xi = 1.4e-4, where a 6e-8 difference grew to 2.4e-3 one iteration later)."""
+    ws = I.batch_workloads(count=12, n_iter=3, seed=5)
+    plans, info = run_batch(ofa, ws, "f16x3", 3)
+    assert info["grouped"] is True
+    for w, p in zip(ws, plans):
+        q = ofa.Plan.from_workload(w, precision="f16x3", autotune=False)
+        q.iterate(3)
+        hb, hq = p.xi_history(), q.xi_history()
+        assert len(hb) == 3 and np.all(np.isfinite(hb))
+        assert abs(hb[0] - hq[0]) < 1e-6 and abs(hb[1] - hq[1]) < 2e-5, (w.name, hb, hq)
         q.close()
         p.close()
