@@ -238,6 +238,21 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest x over all ranks (every rank gets it); x itself without a group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, iters_per_step: int, slowest_ms: float) -> float:
+    """Whole-job iterations/s: every rank's iterations over the slowest rank's time."""
+    return world * steps * iters_per_step / (slowest_ms / 1000.0)
+
+
 def run_reference(args, world, rank):
     """FP64 CPU oracle as the reference arm (rank 0 only)."""
     if rank != 0:
@@ -333,12 +348,8 @@ def main():
         pg.barrier()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if pg:
-        t = torch.tensor([total_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * n_iter / (total_ms / 1000.0)
+    total_ms = max_over_ranks(float(sum(step_ms)), pg, device="cuda")
+    value = job_value(world, args.steps, n_iter, total_ms)
 
     # live per-kernel timing (CUDA events on the plan's stream) for the roofline
     kms = ofa.ofa_profile_kernels(plan.handle, reps=50)
