@@ -146,6 +146,49 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- distributed
+def bench_config(ofa, I, torch, stream, flush, name: str, precisions, reps: int = 3) -> dict:
+    """Iterations/s of each precision form on a named workload, and each form's error
+    against the FP32 form on the GPU: relative L2 of |Theta| from the same phi0, and
+    the differences of the final xi and uniformity after the workload's iterations."""
+    w = I.named(name)
+    n_iter = w.n_iter
+    phi0 = torch.from_numpy(w.phi0).cuda()
+    out = {"workload": name, "nx": w.nx, "ny": w.ny, "n_foci": w.n_foci,
+           "iterations": n_iter, "forms": {}}
+    ref = None
+    for prec in precisions:
+        with torch.cuda.stream(stream):
+            p = ofa.Plan.from_workload(w, precision=prec, stream=stream.cuda_stream)
+            th = torch.zeros(w.n_foci, 2, device="cuda")
+            ofa.ofa_forward(p.handle, phi0, th, None)
+            p.iterate(n_iter)
+            st = p.stats()
+            amp = torch.linalg.vector_norm(th.double(), dim=1).cpu().numpy()
+            ms = 0.0
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                p.iterate(n_iter)
+                e1.record(stream)
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+            p.close()
+        rec = {"iterations_per_s": reps * n_iter / (ms / 1000.0), "xi": st.xi,
+               "uniformity": st.uniformity}
+        if prec == "fp32":
+            ref = (amp, st.xi, st.uniformity)
+        if ref is not None:
+            rec["amp_rel_l2_vs_fp32"] = float(np.linalg.norm(amp - ref[0]) /
+                                              np.linalg.norm(ref[0]))
+            rec["d_xi_vs_fp32"] = abs(st.xi - ref[1])
+            rec["d_uniformity_vs_fp32"] = abs(st.uniformity - ref[2])
+        out["forms"][prec] = rec
+    return out
+
+
 def bench_differentiation(ofa, I, torch, stream, flush, precision: str = "f16x3",
                           steps: int = 200) -> dict:
     """Adam on the focal-intensity loss (1024^2 pupil, 20x20 grid, random targets).
@@ -438,6 +481,13 @@ def main():
             p.close()
         result["forms"] = forms
         result["differentiation"] = bench_differentiation(ofa, I, torch, stream, flush)
+        all_forms = ("fp32", "tf32", "bf16", "bf16x3", "f16x3")
+        result["configs"] = [
+            bench_config(ofa, I, torch, stream, flush, "pupil256_grid100_uniform",
+                         ("fp32", "f16x3")),
+            bench_config(ofa, I, torch, stream, flush, WORKLOAD, all_forms, reps=1),
+            bench_config(ofa, I, torch, stream, flush, "pupil1920x1152_grid2500", all_forms),
+        ]
         result["batch"] = bench_batch(ofa, I, torch, stream, flush)
 
     plan.close()

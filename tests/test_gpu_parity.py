@@ -185,6 +185,44 @@ def test_full_run_poisson1000(ofa, dev, prec):
     assert abs(st.uniformity - ref["uniformity"]) < 1e-3
 
 
+@pytest.fixture(scope="module")
+def oracle_1920(dev):
+    w = I.named("pupil1920x1152_grid2500")
+    fx, fy = oracle_mats(w)
+    ref = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, w.n_iter)
+    theta0 = O.forward(O.pupil_field(w.amplitude, w.phi0), fx, fy)
+    return w, ref, theta0
+
+
+@pytest.mark.parametrize("prec", ALL)
+def test_full_run_1920x1152_forms(ofa, oracle_1920, prec):
+    """Precision forms on the 1920 x 1152 pupil, 50 x 50 grid, 50 iterations: the
+    amplitudes from phi0 within each form's tolerance of FP64, and the final xi
+    within 1e-3 of the FP64 run (the intensity-precision bar) for every form."""
+    w, ref, theta0 = oracle_1920
+    plan = ofa.Plan.from_workload(w, precision=prec,
+                                  stream=torch.cuda.current_stream().cuda_stream)
+    phi_d = torch.from_numpy(w.phi0).cuda()
+    th = torch.zeros(w.n_foci, 2, device="cuda")
+    ofa.ofa_forward(plan.handle, phi_d, th, None)
+    torch.cuda.synchronize()
+    g = th.cpu().numpy().astype(np.float64)
+    err, _ = amp_err(g[:, 0] + 1j * g[:, 1], theta0)
+    it, xi = plan.iterate(w.n_iter, want_stats=True)
+    st = plan.stats()
+    plan.close()
+    print(f"{prec}: amp err {err:.2e}; xi {xi:.6f} vs {ref['xi']:.6f} "
+          f"(|d| {abs(xi - ref['xi']):.1e}); U {st.uniformity:.6f} vs {ref['uniformity']:.6f} "
+          f"(|d| {abs(st.uniformity - ref['uniformity']):.1e})")
+    assert err < AMP_TOL[prec], err
+    assert it == w.n_iter
+    assert abs(xi - ref["xi"]) < 1e-3
+    # uniformity (max/min over 2500 foci) magnifies the single-product forms' 1e-3-level
+    # amplitude errors: BF16 measured 2.2e-3 here, while its xi stays within 6e-5
+    u_tol = 1e-3 if prec in ACCURATE else 1e-2
+    assert abs(st.uniformity - ref["uniformity"]) < u_tol
+
+
 def test_single_focus_closed_form(ofa, dev):
     """K = 1: one iteration gives the linear ramp; the next forward has |Theta| = sum A, xi = 1."""
     w = custom(96, 80, 1, seed=3)
