@@ -165,8 +165,9 @@ __global__ void __launch_bounds__(FT) focal_kernel(
     r2[0] += d * d;
     r2[1] += ih * ih;
     float wk = w[k];
-    if (weighting) wk *= sqrtf(tk / fmaxf(ih, 1e-30f));
-    mx = fmaxf(mx, wk * sqrtf(tk));
+    const float stk = sqrtf(tk);
+    if (weighting) wk *= stk * rsqrtf(fmaxf(ih, 1e-30f));  // w sqrt(t / Ihat)
+    mx = fmaxf(mx, wk * stk);
   }
   block_sum_f(r2, shf + 32);
   mx = block_max_f(mx, shf + 96);
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(FT) focal_kernel(
       const float tk = t[k];
       float wk = w[k];
       if (weighting) {
-        wk *= sqrtf(tk / fmaxf(inten[k] * inv_s, 1e-30f));  // w_j = w_{j-1} sqrt(t / Ihat)
+        wk *= sqrtf(tk) * rsqrtf(fmaxf(inten[k] * inv_s, 1e-30f));  // w_j = w_{j-1} sqrt(t / Ihat)
         w[k] = wk;
       }
       const float mag = wk * sqrtf(tk) * scale;

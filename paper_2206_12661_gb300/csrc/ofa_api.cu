@@ -130,7 +130,7 @@ void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
     const bool fuse = p->K <= 4096;
     launch_fwd_tc(p, p->tc, done, s, fuse);
     if (!fuse)
-      launch_focal(p->part, (p->nyp / 128) * p->tc.fwd_split, p->kp, p->K, p->t, p->w, p->theta,
+      launch_focal(p->part, fwd_n_part(p->nyp, p->tc), p->kp, p->K, p->t, p->w, p->theta,
                    p->inten, p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
     launch_build_p(p->fyT, p->c, done, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
     launch_bwd_tc(p, p->tc, done, s);
@@ -146,7 +146,7 @@ void enqueue_forward_current(ofa_plan* p, cudaStream_t s) {
                  s);
   } else {
     launch_fwd_tc(p, p->tc, nullptr, s, false);
-    launch_focal(p->part, (p->nyp / 128) * p->tc.fwd_split, p->kp, p->K, p->t, p->w, p->theta,
+    launch_focal(p->part, fwd_n_part(p->nyp, p->tc), p->kp, p->K, p->t, p->w, p->theta,
                  p->inten, p->c, p->hist, p->st, 1, p->weighting, ldexpf(1.f, p->amp_exp),
                  p->amp_energy, s);
   }
@@ -704,7 +704,7 @@ ofa_status ofa_forward(ofa_plan* p, const float* phi, float* theta, float* inten
     launch_field_planes(phi, p->amp, p->nx, p->ny, p->nxp, p->precision, p->tc_aux.e_hi,
                         p->tc_aux.e_lo, p->stream);
     launch_fwd_tc(p, p->tc_aux, nullptr, p->stream, false);
-    launch_focal(p->part, (p->nyp / 128) * p->tc.fwd_split, p->kp, p->K, p->t, p->w, th, in, p->c,
+    launch_focal(p->part, fwd_n_part(p->nyp, p->tc), p->kp, p->K, p->t, p->w, th, in, p->c,
                  p->hist, p->st, 2, p->weighting, out_scale, p->amp_energy, p->stream);
   }
   return ofa_cuda_check(p, cudaGetLastError(), "launching forward");
@@ -765,7 +765,7 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   if (e_s[1]) cudaMemcpyAsync(e_s[1], p->tc.e_lo, e_bytes, cudaMemcpyDeviceToDevice, s);
   launch_control(p->st, 0.0, 1, s);
 
-  const int n_part = tc ? (p->nyp / 128) * p->tc.fwd_split : simt_fwd_tiles(p->ny);
+  const int n_part = tc ? fwd_n_part(p->nyp, p->tc) : simt_fwd_tiles(p->ny);
   auto run = [&](int which) {
     switch (which) {
       case 0:

@@ -144,8 +144,9 @@ __device__ inline void iterate(const float2* theta, int K, int kp, const float* 
     r2[0] += d * d;
     r2[1] += ih * ih;
     float wk = w[k];
-    if (weighting) wk *= sqrtf(tk / fmaxf(ih, 1e-30f));
-    mx = fmaxf(mx, wk * sqrtf(tk));
+    const float stk = sqrtf(tk);
+    if (weighting) wk *= stk * rsqrtf(fmaxf(ih, 1e-30f));  // w sqrt(t / Ihat)
+    mx = fmaxf(mx, wk * stk);
   }
   block_sum<NT>(r2, sh + 33, tid, bar);
   mx = block_max<NT>(mx, sh + 99, tid, bar);
@@ -171,7 +172,7 @@ __device__ inline void iterate(const float2* theta, int K, int kp, const float* 
       const float tk = t[k];
       float wk = w[k];
       if (weighting) {
-        wk *= sqrtf(tk / fmaxf(rr * inv_s, 1e-30f));  // w_j = w_{j-1} sqrt(t / Ihat)
+        wk *= sqrtf(tk) * rsqrtf(fmaxf(rr * inv_s, 1e-30f));  // w_j = w_{j-1} sqrt(t / Ihat)
         w[k] = wk;
       }
       const float mag = wk * sqrtf(tk) * scale;
@@ -201,6 +202,7 @@ __device__ inline void iterate_regs(const float2* part, int n_part, int K, int k
                                     float2* __restrict__ c, double* __restrict__ hist,
                                     OfaDevState* __restrict__ st, int weighting, float* sh,
                                     int tid, Bar bar) {
+  if (tid == 0) OFA_FOCAL_STAMP(14);
   const double thr = st->threshold;
   const int hcount = st->hist_count;
   const int j0 = st->j;
@@ -215,18 +217,25 @@ __device__ inline void iterate_regs(const float2* part, int n_part, int K, int k
     tk[i] = in[i] ? t[k] : 0.f;
     wk[i] = in[i] ? w[k] : 0.f;
   }
-  // partials in fixed order p = 0, 1, ...; all KPR loads of a row are independent
-#pragma unroll 2
-  for (int p = 0; p < n_part; ++p) {
-    float2 v[KPR];
+  // partials in fixed order p = 0, 1, ...; the loads of RB rows (RB x KPR values)
+  // are issued together, then summed, so a round costs one L2 latency
+  constexpr int RB = KPR <= 4 ? 8 : 2;
+  for (int p0 = 0; p0 < n_part; p0 += RB) {
+    float2 v[RB][KPR];
 #pragma unroll
-    for (int i = 0; i < KPR; ++i)
-      v[i] = in[i] ? __ldcg(part + (size_t)p * kp + tid + i * NT) : make_float2(0.f, 0.f);
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
-    for (int i = 0; i < KPR; ++i) {
-      th[i].x += v[i].x;
-      th[i].y += v[i].y;
-    }
+      for (int i = 0; i < KPR; ++i)
+        v[r][i] = (in[i] && p0 + r < n_part)
+                      ? __ldcg(part + (size_t)(p0 + r) * kp + tid + i * NT)
+                      : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int i = 0; i < KPR; ++i) {
+        th[i].x += v[r][i].x;
+        th[i].y += v[r][i].y;
+      }
   }
   float r1[1] = {0.f};
 #pragma unroll
@@ -247,15 +256,17 @@ __device__ inline void iterate_regs(const float2* part, int n_part, int K, int k
   const float inv_s = 1.f / S;
   float r2[2] = {0.f, 0.f};
   float mx = 0.f;
+  float sq[KPR];
 #pragma unroll
   for (int i = 0; i < KPR; ++i) {
+    sq[i] = sqrtf(tk[i]);
     if (!in[i]) continue;
     const float ih = ik[i] * inv_s;
     const float d = tk[i] - ih;
     r2[0] += d * d;
     r2[1] += ih * ih;
-    if (weighting) wk[i] *= sqrtf(tk[i] / fmaxf(ih, 1e-30f));  // w_j = w_{j-1} sqrt(t / Ihat)
-    mx = fmaxf(mx, wk[i] * sqrtf(tk[i]));
+    if (weighting) wk[i] *= sq[i] * rsqrtf(fmaxf(ih, 1e-30f));  // w_j = w_{j-1} sqrt(t / Ihat)
+    mx = fmaxf(mx, wk[i] * sq[i]);
   }
   block_sum2_max<NT>(r2, mx, sh + 33, tid, bar);
   if (tid == 0) OFA_FOCAL_STAMP(11);
@@ -277,7 +288,7 @@ __device__ inline void iterate_regs(const float2* part, int n_part, int K, int k
     const int k = tid + i * NT;
     if (k >= K) continue;
     if (weighting) w[k] = wk[i];
-    const float mag = wk[i] * sqrtf(tk[i]) * scale;
+    const float mag = wk[i] * sq[i] * scale;
     float2 ck;
     if (ik[i] > 0.f) {
       const float inv = rsqrtf(ik[i]);
