@@ -190,8 +190,7 @@ ofa_status ofa_adjoint(ofa_plan* plan, const float* phi, const float* theta,
 ofa_status ofa_profile_kernels(ofa_plan* plan, int reps, double* ms_out);
 
 /* Kernel configuration chosen at creation (host output, 12 ints): forward tile width
- * (accumulator columns), forward split-K factor (0: one persistent CTA per SM, each
- * taking an equal share of the (tile, k-block) work), forward multicast cluster shape x and
+ * (accumulator columns), forward split-K factor, forward multicast cluster shape x and
  * y, inverse tile width, inverse cluster shape x and y, 1 if the focal step runs in the
  * forward kernel's last CTA, forward and inverse operand row width per pipeline stage
  * (bytes of K), forward and inverse CTA group (1, or 2 for 2-SM MMA pairs of 256

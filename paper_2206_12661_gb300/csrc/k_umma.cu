@@ -138,9 +138,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -365,18 +362,6 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
 
 __device__ __forceinline__ void named_bar_epi() {
   asm volatile("bar.sync 1, 256;" ::: "memory");
-}
-// Barrier of the 256 forward epilogue threads that also returns, to every one of
-// them, whether any of them passed v = true.
-__device__ __forceinline__ bool named_bar_epi_any(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
-      "bar.red.or.pred p, 1, 256, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)v)
-      : "memory");
-  return r != 0;
 }
 struct BarEpi {
   __device__ __forceinline__ void operator()() const { named_bar_epi(); }
@@ -843,272 +828,6 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
                                          g->kb_total, g->ep, nullptr, 1, 1, g->tail_count);
 }
 
-// ------------------------------------------------------------------ stream-K forward
-// The forward product as a persistent kernel over all SMs.  The work is U =
-// tiles x kb_total (tile, k-block) units; CTA p takes the contiguous units
-// [p U / P, (p + 1) U / P), so every SM gets the same number of MMAs whatever the
-// tile count.  A CTA's units fall into segments, one per tile it touches; each
-// segment accumulates into one of two TMEM buffers, and while the MMAs of the next
-// segment run, the epilogue warps turn the finished buffer into that segment's
-// partial per-focus dot (the dot is linear, so partial k-ranges need no fix-up).
-// Partial rows are indexed (row tile, segment of the tile), at most seg_max
-// segments per tile; rows a schedule never writes stay zero.  Tiles are 128 rows
-// by SK_BN = 256 accumulator columns, one CTA per tile (no pairs, no clusters).
-constexpr int SK_BN = 256;
-
-__host__ __device__ __forceinline__ int sk_owner(long long u, int ctas, int units) {
-  // the CTA whose range [p U / P, (p + 1) U / P) holds unit u
-  return (int)(((u + 1) * ctas - 1) / units);
-}
-
-template <int KIND, int NPASS>
-__global__ void __launch_bounds__(Warps<EPI_FWD>::THREADS, 1)
-    umma_fwd_stream_kernel(const __grid_constant__ CUtensorMap tma_hi,
-                           const __grid_constant__ CUtensorMap tma_lo,
-                           const __grid_constant__ CUtensorMap tmb_hi,
-                           const __grid_constant__ CUtensorMap tmb_lo, const int tiles_n,
-                           const int kb_total, const int units, const int seg_max,
-                           const __grid_constant__ EpiArgs ep, const int* __restrict__ done) {
-  constexpr int BN = SK_BN, RB = 128, EPI = EPI_FWD;
-  using C = Cfg<KIND, NPASS, BN, EPI, RB, 1>;
-  constexpr int WARP_TMA = Warps<EPI>::TMA, WARP_MMA = Warps<EPI>::MMA;
-  constexpr int GROUPS = Warps<EPI>::EPI_THREADS / 128;
-  constexpr int CPW = BN / (32 * GROUPS);
-  if (threadIdx.x == 0) OFA_STAMP(0);
-  pdl_launch_dependents();
-  extern __shared__ uint8_t smem_raw[];
-  const uint32_t raw = smem_u32(smem_raw);
-  const uint32_t base_u32 = (raw + 1023u) & ~1023u;
-  uint8_t* base = smem_raw + (base_u32 - raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  const int ctas = (int)gridDim.x;
-  const int u_begin = (int)((long long)blockIdx.x * units / ctas);
-  const int u_end = (int)((long long)(blockIdx.x + 1) * units / ctas);
-
-  const uint32_t bar_full = base_u32 + C::BAR_OFF;        // STAGES x 8
-  const uint32_t bar_empty = bar_full + 8 * C::STAGES;    // STAGES x 8
-  const uint32_t bar_afull = bar_empty + 8 * C::STAGES;   // 2 x 8: accumulator b complete
-  const uint32_t bar_aempty = bar_afull + 16;             // 2 x 8: accumulator b drained
-  const uint32_t slot_u32 = bar_aempty + 16;
-  volatile uint32_t* slot =
-      reinterpret_cast<volatile uint32_t*>(base + C::BAR_OFF + 16 * C::STAGES + 32);
-  static_assert(C::BAR_OFF + 16 * C::STAGES + 40 <= C::SMEM - 1024, "barrier area");
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < C::STAGES; ++s) {
-      mbar_init(bar_full + 8 * s, 1);
-      mbar_init(bar_empty + 8 * s, 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(bar_afull + 8 * b, 1);
-      mbar_init(bar_aempty + 8 * b, 1);
-    }
-    fence_mbar_init();
-  }
-  if (warp == WARP_TMA && lane == 0) {
-    tmap_prefetch(&tma_hi);
-    tmap_prefetch(&tmb_hi);
-    if (NPASS == 3) {
-      tmap_prefetch(&tma_lo);
-      tmap_prefetch(&tmb_lo);
-    }
-  }
-  if (warp == WARP_MMA) tmem_alloc<1>(slot_u32, 2 * BN);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *slot;
-  pdl_wait();
-  const bool skip = (done != nullptr && *done) || (*ep.err & OFA_ERRBIT_TIMEOUT);
-  if (threadIdx.x == 0) OFA_STAMP(1);
-
-  if (skip) {
-  } else if (warp == WARP_TMA) {
-    if (lane == 0) {
-      int g = 0;
-      bool ok = true;
-      for (int u = u_begin; u < u_end && ok;) {
-        const int t = u / kb_total, kb0 = u % kb_total;
-        const int kb1 = min(kb_total, kb0 + (u_end - u));
-        const int m_tile = t / tiles_n, n_tile = t % tiles_n;
-        for (int kb = kb0; kb < kb1; ++kb, ++g) {
-          const int s = g % C::STAGES;
-          if (g >= C::STAGES && !mbar_wait(bar_empty + 8 * s, ((g / C::STAGES) - 1) & 1)) {
-            ok = false;
-            break;
-          }
-          const uint32_t st = base_u32 + s * C::STAGE_BYTES;
-          const int x = kb * C::BK;
-          mbar_expect_tx(bar_full + 8 * s, C::STAGE_BYTES);
-          tma_load_2d(st, &tma_hi, bar_full + 8 * s, x, m_tile * BM);
-          tma_load_2d(st + C::PLANES * C::A_BYTES, &tmb_hi, bar_full + 8 * s, x, n_tile * BN);
-          if (NPASS == 3) {
-            tma_load_2d(st + C::A_BYTES, &tma_lo, bar_full + 8 * s, x, m_tile * BM);
-            tma_load_2d(st + C::PLANES * C::A_BYTES + C::B_BYTES, &tmb_lo, bar_full + 8 * s, x,
-                        n_tile * BN);
-          }
-        }
-        u += kb1 - kb0;
-      }
-      if (!ok) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
-      // every issued copy must have landed before the CTA may exit
-      for (int q = max(0, g - C::STAGES); q < g; ++q)
-        if (!mbar_wait(bar_full + 8 * (q % C::STAGES), (q / C::STAGES) & 1)) {
-          atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
-          break;
-        }
-    }
-  } else if (warp == WARP_MMA) {
-    if (lane == 0) {
-      int g = 0, seg = 0;
-      bool ok = true;
-      for (int u = u_begin; u < u_end && ok; ++seg) {
-        const int kb0 = u % kb_total;
-        const int kb1 = min(kb_total, kb0 + (u_end - u));
-        const int b = seg & 1;
-        // accumulator b is free once the epilogue has drained segment seg - 2
-        if (seg >= 2 && !mbar_wait(bar_aempty + 8 * b, ((seg >> 1) - 1) & 1)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t acc = tmem + (uint32_t)(b * BN);
-        for (int kb = kb0; kb < kb1; ++kb, ++g) {
-          const int s = g % C::STAGES;
-          if (!mbar_wait(bar_full + 8 * s, (g / C::STAGES) & 1)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          if (g == 0) OFA_STAMP(3);
-          const uint32_t st = base_u32 + s * C::STAGE_BYTES;
-          const uint64_t a_hi = sdesc<RB>(st);
-          const uint64_t a_lo = sdesc<RB>(st + C::A_BYTES);
-          const uint64_t b_hi = sdesc<RB>(st + C::PLANES * C::A_BYTES);
-          const uint64_t b_lo = sdesc<RB>(st + C::PLANES * C::A_BYTES + C::B_BYTES);
-#pragma unroll
-          for (int kk = 0; kk < C::UMMA_K_STEPS; ++kk) {
-            const uint64_t adv = (uint64_t)((kk * 32) >> 4);
-            umma<KIND, 1>(acc, a_hi + adv, b_hi + adv, C::IDESC, (kb != kb0 || kk != 0) ? 1u : 0u);
-            if (NPASS == 3) {
-              umma<KIND, 1>(acc, a_hi + adv, b_lo + adv, C::IDESC, 1);
-              umma<KIND, 1>(acc, a_lo + adv, b_hi + adv, C::IDESC, 1);
-            }
-          }
-          umma_commit(bar_empty + 8 * s);
-        }
-        umma_commit(bar_afull + 8 * b);  // accumulator complete (or drained, on abort)
-        u += kb1 - kb0;
-      }
-      if (!ok) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
-      // the last accumulator's MMAs have completed before the teardown frees TMEM
-      if (seg > 0 && !mbar_wait(bar_afull + 8 * ((seg - 1) & 1), ((seg - 1) >> 1) & 1))
-        atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
-    }
-  } else {
-    // ------------------------------------------------------------ epilogue warps
-    const int quarter = warp & 3, half = warp >> 2;
-    const int r = quarter * 32 + lane;
-    const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16);
-    const int col0 = half * CPW * 32;
-    const int t = threadIdx.x;  // 0..255
-    float* red = reinterpret_cast<float*>(base + C::STAGES * C::STAGE_BYTES);
-    int seg = 0;
-    for (int u = u_begin; u < u_end; ++seg) {
-      const int tile = u / kb_total, kb0 = u % kb_total;
-      const int kb1 = min(kb_total, kb0 + (u_end - u));
-      const int m_tile = tile / tiles_n, n_tile = tile % tiles_n;
-      const int sidx = (int)blockIdx.x - sk_owner((long long)tile * kb_total, ctas, units);
-      const int b = seg & 1;
-      const int n = m_tile * BM + r;
-      float4 fy[CPW][8];
-      const float4* fr = reinterpret_cast<const float4*>(
-          ep.fyT + (size_t)n * ep.kp + ((n_tile * BN + col0) >> 1));
-#pragma unroll
-      for (int c = 0; c < CPW; ++c)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) fy[c][q] = __ldg(fr + c * 8 + q);
-      const bool ready = mbar_wait_sleep(bar_afull + 8 * b, (seg >> 1) & 1);
-      tc_fence_after();
-      if (t == 0 && seg < 4) OFA_STAMP(8 + 2 * seg);
-      if (named_bar_epi_any(!ready)) {  // uniform over the epilogue threads
-        if (t == 0) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
-        break;
-      }
-#pragma unroll
-      for (int c = 0; c < CPW; ++c) {
-        const int ch = half * CPW + c;
-        uint32_t v[32];
-        float pp[32];
-        tmem_ld32(tw + (uint32_t)(b * BN + ch * 32), v);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 f = fy[c][q];
-          const float g0r = __uint_as_float(v[4 * q]), g0i = __uint_as_float(v[4 * q + 1]);
-          const float g1r = __uint_as_float(v[4 * q + 2]), g1i = __uint_as_float(v[4 * q + 3]);
-          pp[4 * q] = f.x * g0r - f.y * g0i;
-          pp[4 * q + 1] = f.x * g0i + f.y * g0r;
-          pp[4 * q + 2] = f.z * g1r - f.w * g1i;
-          pp[4 * q + 3] = f.z * g1i + f.w * g1r;
-        }
-        red[quarter * BN + ch * 32 + lane] = warp_reduce_scatter32(pp);
-      }
-      tc_fence_before();
-      named_bar_epi();  // all TMEM reads of buffer b done, red complete
-      if (t == 0) mbar_arrive(bar_aempty + 8 * b);
-      float* dst = ep.part + (size_t)(m_tile * seg_max + sidx) * 2 * ep.kp + n_tile * BN;
-      for (int col = t; col < BN; col += NUM_EPI_THREADS)
-        dst[col] = ((red[col] + red[BN + col]) + red[2 * BN + col]) + red[3 * BN + col];
-      // the tile's last segment clears the slots its tile leaves unused, so the sum
-      // over seg_max slots never sees values of an earlier schedule
-      if (kb1 == kb_total)
-        for (int q = sidx + 1; q < seg_max; ++q)
-          for (int col = t; col < BN; col += NUM_EPI_THREADS)
-            ep.part[(size_t)(m_tile * seg_max + q) * 2 * ep.kp + n_tile * BN + col] = 0.f;
-      named_bar_epi();  // red is reused by the next segment
-      if (t == 0 && seg < 4) OFA_STAMP(9 + 2 * seg);
-      u += kb1 - kb0;
-    }
-    if (t == 0) OFA_STAMP(6);
-    if (ep.fuse) {
-      // the last CTA to finish runs the focal step on every tile's partials
-      __shared__ int tail_flag;
-      __shared__ float focal_sh[4 * 33];
-      named_bar_epi();
-      if (t == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(ep.counters, 1u);
-        tail_flag = prev == (unsigned)(ctas - 1);
-        if (tail_flag) {
-          __threadfence();
-          *ep.counters = 0u;
-        }
-      }
-      named_bar_epi();
-      if (tail_flag) {
-        const float2* pt = reinterpret_cast<const float2*>(ep.part);
-        if (ep.K <= NUM_EPI_THREADS * 4)
-          ofa_focal::iterate_regs<NUM_EPI_THREADS, 4>(pt, ep.n_part, ep.K, ep.kp, ep.t, ep.w,
-                                                      ep.c, ep.hist, ep.stw, ep.weighting,
-                                                      focal_sh, t, BarEpi());
-        else
-          ofa_focal::iterate_regs<NUM_EPI_THREADS, 16>(pt, ep.n_part, ep.K, ep.kp, ep.t, ep.w,
-                                                       ep.c, ep.hist, ep.stw, ep.weighting,
-                                                       focal_sh, t, BarEpi());
-      }
-    }
-  }
-
-  tc_fence_before();
-  __syncthreads();
-  if (warp == WARP_MMA) {
-    tc_fence_after();
-    tmem_dealloc<1>(tmem, 2 * BN);
-  }
-  if (threadIdx.x == 0) OFA_STAMP(7);
-}
-
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1271,42 +990,9 @@ extern "C" int ofa_debug_phase_trace(unsigned long long* out) {
 }
 #endif
 
-namespace {
-// Calls f(kind, npass) for the stream-K forward variant of a precision.
-template <class F>
-void visit_stream(int prec, F&& f) {
-  switch (prec) {
-    case OFA_PREC_TF32: f(IC<KIND_TF32>{}, IC<1>{}); break;
-    case OFA_PREC_BF16: f(IC<KIND_BF16>{}, IC<1>{}); break;
-    case OFA_PREC_BF16X3: f(IC<KIND_BF16>{}, IC<3>{}); break;
-    case OFA_PREC_F16X3: f(IC<KIND_F16>{}, IC<3>{}); break;
-    default: break;
-  }
-}
-}  // namespace
-
-// Most segments any tile of the stream-K schedule is cut into.
-static int sk_seg_max(int tiles, int kb_total, int ctas) {
-  const int units = tiles * kb_total;
-  int best = 0;
-  for (int tl = 0; tl < tiles; ++tl) {
-    const long long u0 = (long long)tl * kb_total, u1 = u0 + kb_total - 1;
-    best = std::max(best, sk_owner(u1, ctas, units) - sk_owner(u0, ctas, units) + 1);
-  }
-  return best;
-}
-
 // Opt every kernel variant of a precision into its dynamic shared memory (done
 // once per plan, outside any stream capture; the attribute is per device).
 cudaError_t tc_prepare(int prec) {
-  cudaError_t es = cudaSuccess;
-  visit_stream(prec, [&](auto kind, auto npass) {
-    constexpr int K_ = decltype(kind)::value, NP_ = decltype(npass)::value;
-    using C = Cfg<K_, NP_, SK_BN, EPI_FWD, 128, 1>;
-    es = cudaFuncSetAttribute(umma_fwd_stream_kernel<K_, NP_>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-  });
-  if (es != cudaSuccess) return es;
   cudaError_t e = set_attr_epi<EPI_FWD>(prec);
   cudaError_t e2 = set_attr_epi<EPI_BWD>(prec);
   cudaError_t e3 = set_attr_epi<EPI_GRAD>(prec);
@@ -1318,7 +1004,7 @@ bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err);
 namespace {
 struct TuneResult {
   int fwd_bn, fwd_split, fwd_rb, fwd_ccx, fwd_ccy, fwd_cg, bwd_bn, bwd_rb, bwd_ccx, bwd_ccy,
-      bwd_cg, fwd_seg, fwd_ctas;
+      bwd_cg;
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, TuneResult> g_tune_cache;
@@ -1343,7 +1029,6 @@ void apply(TcOperands& t, const TuneResult& r) {
   t.fwd_ccx = r.fwd_ccx; t.fwd_ccy = r.fwd_ccy; t.fwd_cg = r.fwd_cg;
   t.bwd_bn = r.bwd_bn; t.bwd_rb = r.bwd_rb; t.bwd_ccx = r.bwd_ccx; t.bwd_ccy = r.bwd_ccy;
   t.bwd_cg = r.bwd_cg;
-  t.fwd_seg = r.fwd_seg; t.fwd_ctas = r.fwd_ctas;
 }
 }  // namespace
 
@@ -1391,8 +1076,7 @@ bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
   };
   const int cl[4][2] = {{1, 1}, {2, 2}, {2, 1}, {1, 2}};
   float best_f = 1e30f, best_b = 1e30f;
-  TuneResult res = {t.fwd_bn, t.fwd_split, 128, 1, 1, 1, t.bwd_bn, 128, 1, 1, 1, t.fwd_seg,
-                    t.fwd_ctas};
+  TuneResult res = {t.fwd_bn, t.fwd_split, 128, 1, 1, 1, t.bwd_bn, 128, 1, 1, 1};
   const int rb = 128;
   const int kb_fwd = (2 * p->nxp * t.elem_bytes) / rb;
   for (int cg : {1, 2}) {
@@ -1416,32 +1100,6 @@ bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
             res.fwd_bn = bn; res.fwd_split = split; res.fwd_rb = rb; res.fwd_cg = cg;
             res.fwd_ccx = c[0]; res.fwd_ccy = c[1];
           }
-        }
-      }
-    }
-  }
-  // the persistent stream-K forward: 256-column tiles, one CTA per SM
-  if (ok) {
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    const int tiles = ((2 * p->kp) / SK_BN) * tiles_m;
-    const int ctas = std::min(sms, tiles * kb_fwd);
-    const int seg = ctas > 0 ? sk_seg_max(tiles, kb_fwd, ctas) : 0;
-    if (ctas > 0 && seg >= 1 && seg <= 8) {
-      TcOperands cand = t;
-      cand.fwd_bn = SK_BN; cand.fwd_split = 0; cand.fwd_rb = rb; cand.fwd_cg = 1;
-      cand.fwd_ccx = 1; cand.fwd_ccy = 1; cand.fwd_seg = seg; cand.fwd_ctas = ctas;
-      if (!tc_encode_maps(p, cand, err)) {
-        ok = false;
-      } else {
-        const float ms = time_it([&] { launch_fwd_tc(p, cand, nullptr, p->stream, false); });
-        if (verbose)
-          fprintf(stderr, "ofa autotune forward stream-K ctas=%d seg=%d: %.2f us\n", ctas, seg,
-                  1000.f * ms / reps);
-        if (ms < best_f) {
-          best_f = ms;
-          res.fwd_bn = SK_BN; res.fwd_split = 0; res.fwd_rb = rb; res.fwd_cg = 1;
-          res.fwd_ccx = 1; res.fwd_ccy = 1; res.fwd_seg = seg; res.fwd_ctas = ctas;
         }
       }
     }
@@ -1516,9 +1174,8 @@ bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err) {
 void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s,
                    bool fuse_focal) {
   const int kb_total = (2 * p->nxp * t.elem_bytes) / t.fwd_rb;
-  const bool stream_k = t.fwd_split == 0;
-  const int kbps = stream_k ? kb_total : (kb_total + t.fwd_split - 1) / t.fwd_split;
-  dim3 grid((2 * p->kp) / t.fwd_bn, p->nyp / BM, stream_k ? 1 : t.fwd_split);
+  const int kbps = (kb_total + t.fwd_split - 1) / t.fwd_split;
+  dim3 grid((2 * p->kp) / t.fwd_bn, p->nyp / BM, t.fwd_split);
   EpiArgs ep = base_args(p);
   if (fuse_focal) {
     ep.fuse = 1;
@@ -1533,19 +1190,6 @@ void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream
     ep.hist = p->hist;
     ep.stw = p->st;
     ep.weighting = p->weighting;
-  }
-  if (stream_k) {
-    const int tiles_n = (2 * p->kp) / SK_BN, tiles = tiles_n * (p->nyp / BM);
-    visit_stream(p->precision, [&](auto kind, auto npass) {
-      constexpr int K_ = decltype(kind)::value, NP_ = decltype(npass)::value;
-      using C = Cfg<K_, NP_, SK_BN, EPI_FWD, 128, 1>;
-      cudaLaunchAttribute attr[2];
-      cudaLaunchConfig_t cfg = make_cfg(dim3(t.fwd_ctas), Warps<EPI_FWD>::THREADS, C::SMEM, s,
-                                        attr, 1, 1);
-      cudaLaunchKernelEx(&cfg, umma_fwd_stream_kernel<K_, NP_>, t.tm_e_hi, t.tm_e_lo, t.tm_bx_hi,
-                         t.tm_bx_lo, tiles_n, kb_total, tiles * kb_total, t.fwd_seg, ep, done);
-    });
-    return;
   }
   launch_gemm<EPI_FWD>(p->precision, t.fwd_bn, t.fwd_rb, t.fwd_cg, t.fwd_ccx, t.fwd_ccy, t.tm_e_hi,
                        t.tm_e_lo, t.tm_bx_hi, t.tm_bx_lo, grid, kbps, kb_total, ep, done, s);

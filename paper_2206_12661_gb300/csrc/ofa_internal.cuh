@@ -51,10 +51,7 @@ struct TcOperands {
   void* p_hi = nullptr; void* p_lo = nullptr;
   void* q_hi = nullptr; void* q_lo = nullptr;
   CUtensorMap tm_e_hi, tm_e_lo, tm_bx_hi, tm_bx_lo, tm_p_hi, tm_p_lo, tm_q_hi, tm_q_lo;
-  // fwd_split 0: the persistent stream-K forward over fwd_ctas CTAs (fwd_bn 256), at
-  // most fwd_seg segments per tile
   int fwd_bn = 256, fwd_split = 1, bwd_bn = 256;
-  int fwd_seg = 0, fwd_ctas = 0;
   int fwd_rb = 128, bwd_rb = 128;                          // operand row bytes per stage
   int fwd_cg = 1, bwd_cg = 1;                              // 2 = 2-SM MMA pairs
   int fwd_ccx = 1, fwd_ccy = 1, bwd_ccx = 1, bwd_ccy = 1;  // thread-block cluster shapes
@@ -178,9 +175,7 @@ void tc_batch_destroy(TcBatch* b);
 
 inline bool prec_is_tc(int prec) { return prec != OFA_PREC_FP32; }
 // Rows of forward partials [n_part][kp] complex the focal step sums.
-inline int fwd_n_part(int nyp, const TcOperands& t) {
-  return (nyp / 128) * (t.fwd_split > 0 ? t.fwd_split : t.fwd_seg);
-}
+inline int fwd_n_part(int nyp, const TcOperands& t) { return (nyp / 128) * t.fwd_split; }
 inline int prec_elem_bytes(int prec) { return prec == OFA_PREC_TF32 ? 4 : 2; }
 inline int prec_npass(int prec) {
   return (prec == OFA_PREC_BF16X3 || prec == OFA_PREC_F16X3) ? 3 : 1;
