@@ -363,6 +363,11 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
 __device__ __forceinline__ void named_bar_epi() {
   asm volatile("bar.sync 1, 256;" ::: "memory");
 }
+// Barrier of the four inverse-epilogue warps that read one TMEM lane quarter
+// (barriers 2-5, 128 threads each).
+__device__ __forceinline__ void named_bar_quarter(int quarter) {
+  asm volatile("bar.sync %0, 128;" ::"r"(2 + quarter) : "memory");
+}
 struct BarEpi {
   __device__ __forceinline__ void operator()() const { named_bar_epi(); }
 };
@@ -376,8 +381,8 @@ struct Cfg {
   static constexpr int B_BYTES = (BN / CG) * RB;         // a pair holds half of B per CTA
   static constexpr int STAGE_BYTES = PLANES * (A_BYTES + B_BYTES);
   static constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES > 12 ? 12 : SMEM_BUDGET / STAGE_BYTES;
-  // the inverse epilogue stages its output through 16 x 11 KB of the freed stages
-  static_assert(EPI == 0 || STAGES * STAGE_BYTES >= 16 * 11264, "epilogue staging");
+  // the inverse epilogue stages its output through 4 x 3 x 32 x 65 words of the freed stages
+  static_assert(EPI == 0 || STAGES * STAGE_BYTES >= 4 * 3 * 32 * 65 * 4, "epilogue staging");
   static constexpr int UMMA_K_STEPS = RB / 32;            // 32 bytes of K per MMA
   static constexpr int RED_BYTES = EPI == EPI_FWD ? 4 * BN * 4 : 0;
   static constexpr int BAR_OFF = STAGES * STAGE_BYTES + RED_BYTES;
@@ -678,32 +683,37 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
       }
     } else {
       // Per-pixel work (thread = row).  Inputs are prefetched into registers while
-      // the mainloop runs; outputs are staged through shared memory (free once the
-      // accumulator is complete) so every warp store covers whole row segments.
-      const int m0 = (n_tile * BN + col0) >> 1;    // first pupil column of this warp
+      // the mainloop runs.  Warp `half` of a lane quarter takes accumulator chunks
+      // c * GROUPS + half, so in pass c the quarter's four warps cover 64 consecutive
+      // pixels of its 32 rows; they stage them in shared memory (free once the
+      // accumulator is complete) and each warp then stores 8 whole 64-pixel row
+      // segments, every warp store 128 consecutive bytes.
       const bool row_ok = n < ep.ny;
       if (threadIdx.x == 0) OFA_STAMP(14);
       float av[CPW * 16];
       float pv[EPI == EPI_GRAD ? CPW * 16 : 1];
-      {
-        const size_t rb = (size_t)n * ep.nx;
-        const bool vec = ((ep.nx & 3) == 0) && row_ok && (m0 + CPW * 16 <= ep.nx);
-        if (vec) {
 #pragma unroll
-          for (int j = 0; j < CPW * 4; ++j) {
-            const float4 a4 = __ldg(reinterpret_cast<const float4*>(ep.amp + rb + m0) + j);
-            av[4 * j] = a4.x; av[4 * j + 1] = a4.y; av[4 * j + 2] = a4.z; av[4 * j + 3] = a4.w;
+      for (int c = 0; c < CPW; ++c) {
+        const int mc = (n_tile * BN + (c * GROUPS + half) * 32) >> 1;  // first pixel of chunk
+        const size_t rb = (size_t)n * ep.nx + mc;
+        if (((ep.nx & 3) == 0) && row_ok && (mc + 16 <= ep.nx)) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 a4 = __ldg(reinterpret_cast<const float4*>(ep.amp + rb) + j);
+            av[c * 16 + 4 * j] = a4.x; av[c * 16 + 4 * j + 1] = a4.y;
+            av[c * 16 + 4 * j + 2] = a4.z; av[c * 16 + 4 * j + 3] = a4.w;
             if (EPI == EPI_GRAD) {
-              const float4 p4 = __ldg(reinterpret_cast<const float4*>(ep.phi_in + rb + m0) + j);
-              pv[4 * j] = p4.x; pv[4 * j + 1] = p4.y; pv[4 * j + 2] = p4.z; pv[4 * j + 3] = p4.w;
+              const float4 p4 = __ldg(reinterpret_cast<const float4*>(ep.phi_in + rb) + j);
+              pv[c * 16 + 4 * j] = p4.x; pv[c * 16 + 4 * j + 1] = p4.y;
+              pv[c * 16 + 4 * j + 2] = p4.z; pv[c * 16 + 4 * j + 3] = p4.w;
             }
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < CPW * 16; ++j) {
-            const bool ok = row_ok && (m0 + j) < ep.nx;
-            av[j] = ok ? __ldg(ep.amp + rb + m0 + j) : 0.f;
-            if (EPI == EPI_GRAD) pv[j] = ok ? __ldg(ep.phi_in + rb + m0 + j) : 0.f;
+          for (int j = 0; j < 16; ++j) {
+            const bool ok = row_ok && (mc + j) < ep.nx;
+            av[c * 16 + j] = ok ? __ldg(ep.amp + rb + j) : 0.f;
+            if (EPI == EPI_GRAD) pv[c * 16 + j] = ok ? __ldg(ep.phi_in + rb + j) : 0.f;
           }
         }
       }
@@ -712,63 +722,78 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
       if (threadIdx.x == 0) OFA_STAMP(5);
       if (!ready) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
       const bool valid = ready && nkb > 0;
-      uint8_t* wb = base + warp * 11264;   // 16 warps x 11 KB of the freed stages
-      float* s_o = reinterpret_cast<float*>(wb);                 // [32][17] phase / gradient
-      uint2* s_h = reinterpret_cast<uint2*>(wb + 32 * 17 * 4 + 16);  // [32][17] field, hi bits
-      uint2* s_l = s_h + 32 * 17;                                // [32][17] field, lo bits
+      constexpr int PITCH = 65;                    // words per staged row of 64 pixels
+      constexpr int ARR = 32 * PITCH;              // one staged array of a quarter
+      uint32_t* sq = reinterpret_cast<uint32_t*>(base) + quarter * 3 * ARR;
+      float* s_o = reinterpret_cast<float*>(sq);   // phase or gradient
+      uint32_t* s_a = sq + ARR;                    // field hi (TF32: real part bits)
+      uint32_t* s_b = sq + 2 * ARR;                // field lo (TF32: imaginary part bits)
       const int nbase = m_tile * BM + quarter * 32;
-      const int lr = lane >> 4, lc = lane & 15;
       const bool wide = ep.prec == OFA_PREC_TF32;
       float factor = 0.f;
       if (EPI == EPI_GRAD) factor = 2.f * ep.amp_factor / ep.st->c_scale;
 #pragma unroll
       for (int c = 0; c < CPW; ++c) {
-        if (!valid) break;
-        const int ch = half * CPW + c;
-        uint32_t v[32];
-        tmem_ld32(tw + ch * 32, v);
-        if (threadIdx.x == 0 && c < 2) OFA_STAMP(8 + 3 * c);
+        const int ch = c * GROUPS + half;
+        if (valid) {
+          uint32_t v[32];
+          tmem_ld32(tw + ch * 32, v);
+          if (threadIdx.x == 0 && c < 2) OFA_STAMP(8 + 3 * c);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
-          const float a = av[c * 16 + q];
-          if (EPI == EPI_BWD) {
-            // phi = arg(E') (atan2(0,0) = 0), then the next pupil field A exp(i phi),
-            // formed exactly as the field-plane builder forms it from a stored phi
-            const float ph = ofa_arg(im, re);
-            s_o[lane * 17 + q] = ph;
-            float sn, cs;
-            __sincosf(ph, &sn, &cs);
-            uint2 h, l;
-            split_pack(ep.prec, a * cs, a * sn, h, l);
-            s_h[lane * 17 + q] = h;
-            s_l[lane * 17 + q] = l;
-          } else {
-            float sn, cs;
-            sincosf(pv[c * 16 + q], &sn, &cs);
-            s_o[lane * 17 + q] = factor * a * (cs * im - sn * re);
-          }
-        }
-        __syncwarp();
-        if (threadIdx.x == 0 && c < 2) OFA_STAMP(9 + 3 * c);
-        const int gm = m0 + c * 16 + lc;
-#pragma unroll 4
-        for (int it = 0; it < 16; ++it) {
-          const int row = 2 * it + lr, gn = nbase + row;
-          if (gn >= ep.ny || gm >= ep.nx) continue;
-          ep.out[(size_t)gn * ep.nx + gm] = s_o[row * 17 + lc];
-          if (EPI == EPI_BWD) {
-            const size_t e = (size_t)gn * ep.nxp + gm;   // complex element index
-            const uint2 h = s_h[row * 17 + lc];
-            if (wide) {
-              reinterpret_cast<uint2*>(ep.e_hi)[e] = h;
+          for (int q = 0; q < 16; ++q) {
+            const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
+            const float a = av[c * 16 + q];
+            const int slot = lane * PITCH + half * 16 + q;
+            if (EPI == EPI_BWD) {
+              // phi = arg(E') (atan2(0,0) = 0), then the next pupil field A exp(i phi),
+              // formed exactly as the field-plane builder forms it from a stored phi
+              const float ph = ofa_arg(im, re);
+              s_o[slot] = ph;
+              float sn, cs;
+              __sincosf(ph, &sn, &cs);
+              uint2 h, l;
+              split_pack(ep.prec, a * cs, a * sn, h, l);
+              s_a[slot] = h.x;
+              s_b[slot] = wide ? h.y : l.x;
             } else {
-              reinterpret_cast<uint32_t*>(ep.e_hi)[e] = h.x;
-              if (ep.e_lo) reinterpret_cast<uint32_t*>(ep.e_lo)[e] = s_l[row * 17 + lc].x;
+              float sn, cs;
+              sincosf(pv[c * 16 + q], &sn, &cs);
+              s_o[slot] = factor * a * (cs * im - sn * re);
             }
           }
         }
-        __syncwarp();
+        named_bar_quarter(quarter);
+        if (threadIdx.x == 0 && c < 2) OFA_STAMP(9 + 3 * c);
+        if (valid) {
+          const int px0 = ((n_tile * BN) >> 1) + c * 64;  // first pixel of this pass
+#pragma unroll 2
+          for (int rr = 0; rr < 8; ++rr) {
+            const int row = half * 8 + rr, gn = nbase + row;
+            if (gn >= ep.ny) continue;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const int px = lane + 32 * j, gm = px0 + px;
+              if (gm >= ep.nx) continue;
+              ep.out[(size_t)gn * ep.nx + gm] = s_o[row * PITCH + px];
+              if (EPI == EPI_BWD && !wide) {
+                const size_t e = (size_t)gn * ep.nxp + gm;   // complex element index
+                reinterpret_cast<uint32_t*>(ep.e_hi)[e] = s_a[row * PITCH + px];
+                if (ep.e_lo) reinterpret_cast<uint32_t*>(ep.e_lo)[e] = s_b[row * PITCH + px];
+              }
+            }
+            if (EPI == EPI_BWD && wide) {
+              // two words per pixel: 128 consecutive words per row segment
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int wi = lane + 32 * j, px = wi >> 1, gm = px0 + px;
+                if (gm >= ep.nx) continue;
+                const uint32_t word = (wi & 1) ? s_b[row * PITCH + px] : s_a[row * PITCH + px];
+                reinterpret_cast<uint32_t*>(ep.e_hi)[2 * ((size_t)gn * ep.nxp + px0) + wi] = word;
+              }
+            }
+          }
+        }
+        named_bar_quarter(quarter);
         if (threadIdx.x == 0 && c < 2) OFA_STAMP(10 + 3 * c);
       }
     }
