@@ -1,16 +1,19 @@
 // FP32 CUDA-core form of the two MTP products (kernels (b) and (d), OFA_PREC_FP32).
 //
-// Forward (Eq. 2 at the foci): G[n,k] = sum_m E[n,m] Fx[k,m] with the pupil
-// field E = A exp(i phi) formed on the fly from phi and A (fused phase->field
-// prologue), then the per-focus dot Theta_k = sum_n Fy[k,n] G[n,k] reduced
-// inside the tile; each 64-row tile writes one deterministic partial Theta.
+// Forward (Eq. 2 at the foci): G[n,k] = sum_m E[n,m] Fx[k,m] over the pupil field
+// E = A exp(i phi) kept as complex planes (written by the inverse's epilogue, or by
+// field_f32_kernel for a given phase), then the per-focus dot
+// Theta_k = sum_n Fy[k,n] G[n,k] reduced inside the tile; each 64-row tile writes
+// one deterministic partial Theta.
 //
 // Inverse (Algorithm 1, inverse propagation read as the adjoint of Eq. 2):
 // E'[n,m] = sum_k conj(Fy[k,n]) c_k conj(Fx[k,m]), fused with the phase-only
-// projection phi = arg(E') (or, for the gradient, 2 Im(conj(E) E')).
+// projection phi = arg(E') and the next field A exp(i phi) (or, for the
+// gradient, 2 Im(conj(E) E')).
 //
 // Both are 64 x 64 complex tiles, 256 threads, 4 x 4 complex accumulators per
-// thread, 16-deep steps staged through shared memory with register prefetch.
+// thread, 16-deep steps through double-buffered shared memory (one barrier per
+// step) with the next step's global loads in flight during the current one.
 #include "ofa_internal.cuh"
 #include "ofa_math.cuh"
 
@@ -26,16 +29,55 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(a.y, b.x, acc.y);
 }
 
+// 16 steps of the 4 x 4 complex outer products of one shared-memory stage:
+// rows a[.][ty*4 ..], columns b[.][tx*4 ..].
+// UNROLL: steps unrolled (the forward runs best with 4, the inverse with 16).
+template <int UNROLL>
+__device__ __forceinline__ void mma_stage(const float2 (*a)[T64], const float2 (*b)[T64], int ty,
+                                          int tx, float2 (&acc)[4][4]) {
+#pragma unroll UNROLL
+  for (int mm = 0; mm < TS; ++mm) {
+    const float4 a01 = *reinterpret_cast<const float4*>(&a[mm][ty * 4]);
+    const float4 a23 = *reinterpret_cast<const float4*>(&a[mm][ty * 4 + 2]);
+    const float4 b01 = *reinterpret_cast<const float4*>(&b[mm][tx * 4]);
+    const float4 b23 = *reinterpret_cast<const float4*>(&b[mm][tx * 4 + 2]);
+    const float2 e[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
+                         make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
+    const float2 f[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
+                         make_float2(b23.x, b23.y), make_float2(b23.z, b23.w)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cmac(acc[i][j], e[i], f[j]);
+  }
+}
+
+// E = A exp(i phi), complex planes [ny][nx] (accurate sincosf: the FP32 form keeps
+// full FP32 accuracy).
+__global__ void field_f32_kernel(const float* __restrict__ phi, const float* __restrict__ amp,
+                                 size_t n, float2* __restrict__ e) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float s, c;
+    sincosf(phi[i], &s, &c);
+    const float a = amp[i];
+    e[i] = make_float2(a * c, a * s);
+  }
+}
+
 __global__ void __launch_bounds__(256) fwd_simt_kernel(
-    const float* __restrict__ phi, const float* __restrict__ amp, const float2* __restrict__ fx,
-    const float2* __restrict__ fy, int nx, int ny, int K, int kp, float2* __restrict__ part,
-    const int* __restrict__ done) {
+    const float2* __restrict__ e32, const float2* __restrict__ fx, const float2* __restrict__ fy,
+    int nx, int ny, int K, int kp, float2* __restrict__ part, const int* __restrict__ done) {
   if (done != nullptr && *done) return;
-  __shared__ __align__(16) float2 Es[TS][T64];
-  __shared__ __align__(16) float2 Fs[TS][T64];
+  __shared__ __align__(16) float2 Es[2][TS][T64];
+  __shared__ __align__(16) float2 Fs[2][TS][T64];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int n0 = blockIdx.y * T64, k0 = blockIdx.x * T64;
   const int lr = tid >> 2, lc = (tid & 3) * 4;
+  // this block's share of the contraction: whole TS-deep steps [m_begin, m_end)
+  const int steps = (nx + TS - 1) / TS;
+  const int m_begin = (int)(blockIdx.z * steps / gridDim.z) * TS;
+  const int m_end = min(nx, (int)((blockIdx.z + 1) * steps / gridDim.z) * TS);
 
   float2 acc[4][4];
 #pragma unroll
@@ -43,51 +85,38 @@ __global__ void __launch_bounds__(256) fwd_simt_kernel(
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
-  float pv[4], av[4];
-  float2 fv[4];
+  float2 ev[4], fv[4];
   auto gload = [&](int m0) {
     const int n = n0 + lr, k = k0 + lr;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int m = m0 + lc + q;
-      const bool ok_e = n < ny && m < nx;
-      pv[q] = ok_e ? phi[(size_t)n * nx + m] : 0.f;
-      av[q] = ok_e ? amp[(size_t)n * nx + m] : 0.f;
+      ev[q] = (n < ny && m < nx) ? e32[(size_t)n * nx + m] : make_float2(0.f, 0.f);
       fv[q] = (k < K && m < nx) ? fx[(size_t)k * nx + m] : make_float2(0.f, 0.f);
     }
   };
-  gload(0);
-  for (int m0 = 0; m0 < nx; m0 += TS) {
-    __syncthreads();
+  auto sstore = [&](int b) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      float s, c;
-      sincosf(pv[q], &s, &c);
-      Es[lc + q][lr] = make_float2(av[q] * c, av[q] * s);   // E = A exp(i phi)
-      Fs[lc + q][lr] = fv[q];
+      Es[b][lc + q][lr] = ev[q];
+      Fs[b][lc + q][lr] = fv[q];
     }
+  };
+  gload(m_begin);
+  sstore(0);
+  __syncthreads();
+  int b = 0;
+  for (int m0 = m_begin; m0 < m_end; m0 += TS) {
+    const bool more = m0 + TS < m_end;
+    if (more) gload(m0 + TS);
+    mma_stage<4>(Es[b], Fs[b], ty, tx, acc);
+    if (more) sstore(b ^ 1);  // its readers finished before the previous barrier
     __syncthreads();
-    if (m0 + TS < nx) gload(m0 + TS);
-#pragma unroll
-    for (int mm = 0; mm < TS; ++mm) {
-      const float4 e01 = *reinterpret_cast<const float4*>(&Es[mm][ty * 4]);
-      const float4 e23 = *reinterpret_cast<const float4*>(&Es[mm][ty * 4 + 2]);
-      const float4 f01 = *reinterpret_cast<const float4*>(&Fs[mm][tx * 4]);
-      const float4 f23 = *reinterpret_cast<const float4*>(&Fs[mm][tx * 4 + 2]);
-      const float2 e[4] = {make_float2(e01.x, e01.y), make_float2(e01.z, e01.w),
-                           make_float2(e23.x, e23.y), make_float2(e23.z, e23.w)};
-      const float2 f[4] = {make_float2(f01.x, f01.y), make_float2(f01.z, f01.w),
-                           make_float2(f23.x, f23.y), make_float2(f23.z, f23.w)};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cmac(acc[i][j], e[i], f[j]);
-    }
+    b ^= 1;
   }
 
   // Per-focus dot with the Fy rows, reduced over the tile's 64 rows in fixed order.
-  __syncthreads();
-  float2* red = &Es[0][0];  // 16 x 64 float2
+  float2* red = &Es[0][0][0];  // 16 x 64 float2
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int k = k0 + tx * 4 + j;
@@ -111,20 +140,22 @@ __global__ void __launch_bounds__(256) fwd_simt_kernel(
       a.y += v.y;
     }
     const int k = k0 + tid;
-    if (k < kp) part[(size_t)blockIdx.y * kp + k] = a;
+    if (k < kp) part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * kp + k] = a;
   }
 }
 
-// EPI 0: phi = atan2(Im E', Re E').  EPI 1: grad = f 2 A (cos phi Im B - sin phi Re B).
+// EPI 0: phi = arg(E') (atan2(0,0) = 0) and the next field A exp(i phi), formed
+// exactly as field_f32_kernel forms it from a stored phi.
+// EPI 1: grad = f 2 A (cos phi Im B - sin phi Re B).
 template <int EPI>
 __global__ void __launch_bounds__(256) bwd_simt_kernel(
     const float2* __restrict__ c, const float2* __restrict__ fx, const float2* __restrict__ fy,
-    int nx, int ny, int K, float* __restrict__ out, const float* __restrict__ phi_in,
-    const float* __restrict__ amp, float amp_factor, const OfaDevState* __restrict__ st,
-    const int* __restrict__ done) {
+    int nx, int ny, int K, float* __restrict__ out, float2* __restrict__ e_out,
+    const float* __restrict__ phi_in, const float* __restrict__ amp, float amp_factor,
+    const OfaDevState* __restrict__ st, const int* __restrict__ done) {
   if (done != nullptr && *done) return;
-  __shared__ __align__(16) float2 Ps[TS][T64];
-  __shared__ __align__(16) float2 Qs[TS][T64];
+  __shared__ __align__(16) float2 Ps[2][TS][T64];
+  __shared__ __align__(16) float2 Qs[2][TS][T64];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int n0 = blockIdx.y * T64, m0 = blockIdx.x * T64;
   const int lk = tid >> 4, lc = (tid & 15) * 4;
@@ -149,31 +180,24 @@ __global__ void __launch_bounds__(256) bwd_simt_kernel(
       qv[q] = make_float2(b.x, -b.y);  // conj(Fx[k,m])
     }
   };
-  gload(0);
-  for (int k0 = 0; k0 < K; k0 += TS) {
-    __syncthreads();
+  auto sstore = [&](int b) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      Ps[lk][lc + q] = pv[q];
-      Qs[lk][lc + q] = qv[q];
+      Ps[b][lk][lc + q] = pv[q];
+      Qs[b][lk][lc + q] = qv[q];
     }
+  };
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  int b = 0;
+  for (int k0 = 0; k0 < K; k0 += TS) {
+    const bool more = k0 + TS < K;
+    if (more) gload(k0 + TS);
+    mma_stage<16>(Ps[b], Qs[b], ty, tx, acc);
+    if (more) sstore(b ^ 1);
     __syncthreads();
-    if (k0 + TS < K) gload(k0 + TS);
-#pragma unroll
-    for (int kk = 0; kk < TS; ++kk) {
-      const float4 p01 = *reinterpret_cast<const float4*>(&Ps[kk][ty * 4]);
-      const float4 p23 = *reinterpret_cast<const float4*>(&Ps[kk][ty * 4 + 2]);
-      const float4 q01 = *reinterpret_cast<const float4*>(&Qs[kk][tx * 4]);
-      const float4 q23 = *reinterpret_cast<const float4*>(&Qs[kk][tx * 4 + 2]);
-      const float2 p[4] = {make_float2(p01.x, p01.y), make_float2(p01.z, p01.w),
-                           make_float2(p23.x, p23.y), make_float2(p23.z, p23.w)};
-      const float2 qq[4] = {make_float2(q01.x, q01.y), make_float2(q01.z, q01.w),
-                            make_float2(q23.x, q23.y), make_float2(q23.z, q23.w)};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cmac(acc[i][j], p[i], qq[j]);
-    }
+    b ^= 1;
   }
 
   float factor = 0.f;
@@ -183,15 +207,20 @@ __global__ void __launch_bounds__(256) bwd_simt_kernel(
     const int n = n0 + ty * 4 + i;
     if (n >= ny) continue;
     float v[4];
+    float2 ev[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int m = m0 + tx * 4 + j;
       if (EPI == 0) {
         v[j] = ofa_arg(acc[i][j].y, acc[i][j].x);
+        float s, cs;
+        sincosf(v[j], &s, &cs);
+        const float a = m < nx ? amp[(size_t)n * nx + m] : 0.f;
+        ev[j] = make_float2(a * cs, a * s);
       } else if (m < nx) {
-        float s, cc;
-        sincosf(phi_in[(size_t)n * nx + m], &s, &cc);
-        v[j] = factor * amp[(size_t)n * nx + m] * (cc * acc[i][j].y - s * acc[i][j].x);
+        float s, cs;
+        sincosf(phi_in[(size_t)n * nx + m], &s, &cs);
+        v[j] = factor * amp[(size_t)n * nx + m] * (cs * acc[i][j].y - s * acc[i][j].x);
       } else {
         v[j] = 0.f;
       }
@@ -200,29 +229,46 @@ __global__ void __launch_bounds__(256) bwd_simt_kernel(
     float* dst = out + (size_t)n * nx + m;
     if ((nx & 3) == 0 && m + 3 < nx) {
       *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+      if (EPI == 0) {
+        float4* ed = reinterpret_cast<float4*>(e_out + (size_t)n * nx + m);
+        ed[0] = make_float4(ev[0].x, ev[0].y, ev[1].x, ev[1].y);
+        ed[1] = make_float4(ev[2].x, ev[2].y, ev[3].x, ev[3].y);
+      }
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (m + j < nx) dst[j] = v[j];
+        if (m + j < nx) {
+          dst[j] = v[j];
+          if (EPI == 0) e_out[(size_t)n * nx + m + j] = ev[j];
+        }
     }
   }
 }
 
 }  // namespace
 
-int simt_fwd_tiles(int ny) { return (ny + T64 - 1) / T64; }
+constexpr int FWD_SPLIT = 1;  // contraction parts of the forward (grid z)
 
-void launch_fwd_simt(const float* phi, const float* amp, const float2* fx, const float2* fy,
-                     int nx, int ny, int K, int kp, float2* part, const int* done,
-                     cudaStream_t s) {
-  dim3 grid((K + T64 - 1) / T64, (ny + T64 - 1) / T64);
-  fwd_simt_kernel<<<grid, 256, 0, s>>>(phi, amp, fx, fy, nx, ny, K, kp, part, done);
+int simt_fwd_tiles(int ny) { return FWD_SPLIT * ((ny + T64 - 1) / T64); }
+
+void launch_field_f32(const float* phi, const float* amp, int nx, int ny, float2* e,
+                      cudaStream_t s) {
+  const size_t n = (size_t)nx * ny;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  field_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(phi, amp, n, e);
+}
+
+void launch_fwd_simt(const float2* e32, const float2* fx, const float2* fy, int nx, int ny, int K,
+                     int kp, float2* part, const int* done, cudaStream_t s) {
+  dim3 grid((K + T64 - 1) / T64, (ny + T64 - 1) / T64, FWD_SPLIT);
+  fwd_simt_kernel<<<grid, 256, 0, s>>>(e32, fx, fy, nx, ny, K, kp, part, done);
 }
 
 void launch_bwd_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,
-                     float* phi, const int* done, cudaStream_t s) {
+                     const float* amp, float* phi, float2* e32, const int* done, cudaStream_t s) {
   dim3 grid((nx + T64 - 1) / T64, (ny + T64 - 1) / T64);
-  bwd_simt_kernel<0><<<grid, 256, 0, s>>>(c, fx, fy, nx, ny, K, phi, nullptr, nullptr, 0.f,
+  bwd_simt_kernel<0><<<grid, 256, 0, s>>>(c, fx, fy, nx, ny, K, phi, e32, nullptr, amp, 0.f,
                                           nullptr, done);
 }
 
@@ -230,6 +276,6 @@ void launch_grad_simt(const float2* c, const float2* fx, const float2* fy, int n
                       const float* phi, const float* amp, float amp_factor,
                       const OfaDevState* st, float* grad, cudaStream_t s) {
   dim3 grid((nx + T64 - 1) / T64, (ny + T64 - 1) / T64);
-  bwd_simt_kernel<1><<<grid, 256, 0, s>>>(c, fx, fy, nx, ny, K, grad, phi, amp, amp_factor, st,
-                                          nullptr);
+  bwd_simt_kernel<1><<<grid, 256, 0, s>>>(c, fx, fy, nx, ny, K, grad, nullptr, phi, amp,
+                                          amp_factor, st, nullptr);
 }

@@ -121,10 +121,10 @@ int* done_ptr(ofa_plan* p) { return &p->st->done; }
 void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
   const int* done = done_ptr(p);
   if (!prec_is_tc(p->precision)) {
-    launch_fwd_simt(p->phi, p->amp, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, done, s);
+    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, done, s);
     launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
                  p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
-    launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->phi, done, s);
+    launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->amp, p->phi, p->e32, done, s);
   } else {
     // up to 4096 foci the focal step runs in the forward kernel's last CTA
     const bool fuse = p->K <= 4096;
@@ -140,7 +140,7 @@ void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
 // Forward at the loop's current phase + statistics (mode 1) or output (mode 2).
 void enqueue_forward_current(ofa_plan* p, cudaStream_t s) {
   if (!prec_is_tc(p->precision)) {
-    launch_fwd_simt(p->phi, p->amp, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, s);
+    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, s);
     launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
                  p->c, p->hist, p->st, 1, p->weighting, ldexpf(1.f, p->amp_exp), p->amp_energy,
                  s);
@@ -326,7 +326,7 @@ ofa_status ofa_destroy(ofa_plan* p) {
   destroy_graphs(p);
   void* bufs[] = {p->focus_xy, p->t,     p->amp,   p->phi,   p->w,    p->fx,
                   p->fy,       p->fyT,   p->part,  p->theta, p->inten, p->c,
-                  p->hist,     p->st,    p->scratch_phi, p->counters};
+                  p->hist,     p->st,    p->scratch_phi, p->counters, p->e32, p->e32_aux};
   for (void* b : bufs) dfree(b);
   if (p->st_host) cudaFreeHost(p->st_host);
   free_tc(p->tc);
@@ -454,6 +454,10 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   OFA_TRY(dalloc(&p->st, 1), "alloc");
   OFA_TRY(cudaMallocHost(reinterpret_cast<void**>(&p->st_host), sizeof(OfaDevState)),
           "pinned alloc");
+  if (!tc) {
+    OFA_TRY(dalloc(&p->e32, npix), "alloc");
+    OFA_TRY(dalloc(&p->e32_aux, npix), "alloc");
+  }
   if (tc) {
     OFA_TRY(dalloc(&p->fyT, (size_t)p->nyp * p->kp), "alloc");
     if (alloc_tc(p, p->tc, true) != OFA_OK)
@@ -539,6 +543,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
       return fail(OFA_ERR_CUDA);
     }
   }
+  if (!tc) launch_field_f32(p->phi, p->amp, nx, ny, p->e32, p->stream);
   launch_set_j(p->st, 0, 1, p->stream);
   launch_control(p->st, 0.0, 1, p->stream);
   OFA_TRY(cudaGetLastError(), "launching set-up kernels");
@@ -683,6 +688,8 @@ ofa_status ofa_set_state(ofa_plan* p, const float* phi, const float* w, int j, i
   if (prec_is_tc(p->precision))
     launch_field_planes(p->phi, p->amp, p->nx, p->ny, p->nxp, p->precision, p->tc.e_hi,
                         p->tc.e_lo, p->stream);
+  else
+    launch_field_f32(p->phi, p->amp, p->nx, p->ny, p->e32, p->stream);
   launch_set_j(p->st, j, 1, p->stream);
   return sync_and_check(p);
 }
@@ -694,7 +701,8 @@ ofa_status ofa_forward(ofa_plan* p, const float* phi, float* theta, float* inten
   float* in = intensity ? intensity : p->inten;
   const float out_scale = ldexpf(1.f, p->amp_exp);
   if (!prec_is_tc(p->precision)) {
-    launch_fwd_simt(phi, p->amp, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr,
+    launch_field_f32(phi, p->amp, p->nx, p->ny, p->e32_aux, p->stream);
+    launch_fwd_simt(p->e32_aux, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr,
                     p->stream);
     launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, th, in, p->c, p->hist,
                  p->st, 2, p->weighting, out_scale, p->amp_energy, p->stream);
@@ -770,8 +778,8 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
     switch (which) {
       case 0:
         if (tc) launch_fwd_tc(p, p->tc, nullptr, s, p->K <= 4096);  // + fused focal step
-        else launch_fwd_simt(p->phi, p->amp, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part,
-                             nullptr, s);
+        else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr,
+                             s);
         break;
       case 1:
         if (tc && p->K <= 4096) break;  // fused into the forward kernel
@@ -785,7 +793,8 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
         break;
       default:
         if (tc) launch_bwd_tc(p, p->tc, nullptr, s);
-        else launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->phi, nullptr, s);
+        else launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
+                             nullptr, s);
         break;
     }
   };
@@ -813,6 +822,7 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   cudaMemcpyAsync(p->st, st_s, sizeof(OfaDevState), cudaMemcpyDeviceToDevice, s);
   if (tc) cudaMemcpyAsync(p->tc.e_hi, e_s[0], e_bytes, cudaMemcpyDeviceToDevice, s);
   if (e_s[1]) cudaMemcpyAsync(p->tc.e_lo, e_s[1], e_bytes, cudaMemcpyDeviceToDevice, s);
+  if (!tc) launch_field_f32(p->phi, p->amp, p->nx, p->ny, p->e32, s);  // field of the restored phi
   ofa_status st = sync_and_check(p);
   cleanup();
   if (st != OFA_OK) return st;

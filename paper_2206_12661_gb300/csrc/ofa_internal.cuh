@@ -86,6 +86,8 @@ struct ofa_plan {
   OfaDevState* st = nullptr;
   OfaDevState* st_host = nullptr;      // pinned mirror for readback
   float* scratch_phi = nullptr;        // for ofa_forward / ofa_adjoint on the tensor path
+  float2* e32 = nullptr;               // FP32 form: pupil field A exp(i phi) [ny][nx]
+  float2* e32_aux = nullptr;           // FP32 form: field of an external phase
   TcOperands tc;
   TcOperands tc_aux;                   // E planes of an external phase (forward/adjoint)
   bool aux_ready = false;
@@ -118,11 +120,13 @@ void launch_field_planes(const float* phi, const float* amp, int nx, int ny, int
                          int prec, void* hi, void* lo, cudaStream_t s);
 
 // ---------------------------------------------------------------- kernels (k_simt.cu)
-void launch_fwd_simt(const float* phi, const float* amp, const float2* fx, const float2* fy,
-                     int nx, int ny, int K, int kp, float2* part, const int* done, cudaStream_t s);
+void launch_field_f32(const float* phi, const float* amp, int nx, int ny, float2* e,
+                      cudaStream_t s);
+void launch_fwd_simt(const float2* e32, const float2* fx, const float2* fy, int nx, int ny, int K,
+                     int kp, float2* part, const int* done, cudaStream_t s);
 int simt_fwd_tiles(int ny);
 void launch_bwd_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,
-                     float* phi, const int* done, cudaStream_t s);
+                     const float* amp, float* phi, float2* e32, const int* done, cudaStream_t s);
 void launch_grad_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,
                       const float* phi, const float* amp, float amp_factor,
                       const OfaDevState* st, float* grad, cudaStream_t s);
