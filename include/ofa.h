@@ -81,6 +81,14 @@ typedef struct ofa_options {
                                 at creation and keep the fastest (default; results are
                                 cached per device, size and precision for the process),
                                 0 = a static cost model */
+  const double* focus_z;     /* [K] axial offsets z_k (m) of the foci from the focal plane
+                                (a 3D array), or NULL for z = 0.  Focus k's rows then carry
+                                the defocus phase of the pupil function, a Fresnel (paraxial)
+                                lens term: Fx[k][m] = exp(-i 2 pi (x_k u_m / (lambda f) +
+                                z_k u_m^2 / (2 lambda f^2))), Fy likewise with v_n; each
+                                |z_k| < f, and |x_k| + |z_k| u_max / f must stay inside the
+                                alias-free field (u_max = (nx - 1) pitch_x / 2; same in y),
+                                else OFA_ERR_OUT_OF_RANGE.  In mem_space; default NULL */
 } ofa_options;
 
 typedef struct ofa_stats {
@@ -252,6 +260,21 @@ ofa_status ofa_forward_noalloc(int nx, int ny, double pitch_x, double pitch_y,
                                const double* focus_xy, const float* phi,
                                const float* amplitude, float* theta, float* intensity,
                                void* cuda_stream);
+
+/*
+ * ofa_selftest_bounded_wait -- diagnostic of failure detection (the paper has no
+ * counterpart).  Every wait of the tensor-core kernels (on TMA data, a free stage,
+ * the accumulator) gives up after about one second, records the fact in the plan's
+ * device state and makes the next synchronising call return OFA_ERR_TIMEOUT instead
+ * of hanging.  This call runs one such wait on a barrier that nothing signals and
+ * returns what a plan would: OFA_ERR_TIMEOUT when the wait gave up as designed (the
+ * expected result; ofa_last_error(NULL) says so), OFA_OK if it did not give up,
+ * OFA_ERR_CUDA on a CUDA failure.  Takes about one second; synchronises the current
+ * device.  Plan creation honours OFA_FAULT_ALLOC=N in the environment: the N-th
+ * device allocation of that call fails as out of memory (OFA_ERR_OOM, everything
+ * already allocated is freed), for testing the error paths.
+ */
+ofa_status ofa_selftest_bounded_wait(void);
 
 /* Host-only helpers (no GPU needed). */
 

@@ -52,23 +52,34 @@ def pupil_coords(n: int, pitch: float) -> np.ndarray:
     return (np.arange(n, dtype=np.float64) - (n - 1) / 2.0) * float(pitch)
 
 
-def dft_rows(focal: np.ndarray, pupil: np.ndarray, lam_f: float) -> np.ndarray:
+def dft_rows(focal: np.ndarray, pupil: np.ndarray, lam_f: float, focus_z=None,
+             focal_length=None) -> np.ndarray:
     """Rows of the arbitrarily sampled DFT matrix of Eq. 2 at the foci.
 
     Omega[k, m] = exp(-i 2 pi focal_k * pupil_m / (lambda f)): the exponent of
     Eq. 1 with spatial frequency pupil_m / (lambda f), one row per focus.
+
+    3D foci (the axial position of a spot set by a defocus phase of the pupil
+    function, Sec. 4): with axial offsets z_k the pupil field seen by focus k
+    carries the paraxial (Fresnel) defocus exp(-i pi z_k (u^2 + v^2) / (lambda f^2)),
+    whose u and v factors fold into the two rows:
+    Omega[k, m] *= exp(-i pi z_k pupil_m^2 / (lambda f^2)).
     """
     focal = np.asarray(focal, dtype=np.float64)
     pupil = np.asarray(pupil, dtype=np.float64)
-    return np.exp(-1j * TWO_PI * np.outer(focal, pupil) / float(lam_f))
+    arg = TWO_PI * np.outer(focal, pupil) / float(lam_f)
+    if focus_z is not None:
+        lam_f2 = float(lam_f) * float(focal_length)
+        arg = arg + np.pi * np.outer(np.asarray(focus_z, np.float64), pupil ** 2) / lam_f2
+    return np.exp(-1j * arg)
 
 
-def plan_matrices(nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy):
-    """Fx [K][nx] and Fy [K][ny] for a centred pupil and foci (x_k, y_k)."""
+def plan_matrices(nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy, focus_z=None):
+    """Fx [K][nx] and Fy [K][ny] for a centred pupil and foci (x_k, y_k[, z_k])."""
     lam_f = float(wavelength) * float(focal_length)
     focus_xy = np.asarray(focus_xy, dtype=np.float64)
-    fx = dft_rows(focus_xy[:, 0], pupil_coords(nx, pitch_x), lam_f)
-    fy = dft_rows(focus_xy[:, 1], pupil_coords(ny, pitch_y), lam_f)
+    fx = dft_rows(focus_xy[:, 0], pupil_coords(nx, pitch_x), lam_f, focus_z, focal_length)
+    fy = dft_rows(focus_xy[:, 1], pupil_coords(ny, pitch_y), lam_f, focus_z, focal_length)
     return fx, fy
 
 

@@ -11,8 +11,13 @@
 
 namespace {
 
-__global__ void dft_rows_kernel(const double* __restrict__ focus_xy, int coord, int K, int n,
-                                double pitch, double lam_f, float2* __restrict__ out) {
+// Fx[k][m] = exp(-i 2 pi (x_k u_m / (lambda f) + z_k u_m^2 / (2 lambda f^2))): the
+// DFT row of Eq. 2 and, for a 3D focus (focus_z non-NULL), the separable Fresnel
+// defocus phase of the pupil function that moves the focus z_k off the focal plane.
+__global__ void dft_rows_kernel(const double* __restrict__ focus_xy,
+                                const double* __restrict__ focus_z, int coord, int K, int n,
+                                double pitch, double lam_f, double lam_f2,
+                                float2* __restrict__ out) {
   size_t total = (size_t)K * n;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -20,6 +25,7 @@ __global__ void dft_rows_kernel(const double* __restrict__ focus_xy, int coord, 
     int m = (int)(i % n);
     double u = ((double)m - 0.5 * (double)(n - 1)) * pitch;
     double turns = focus_xy[2 * (size_t)k + coord] * u / lam_f;
+    if (focus_z != nullptr) turns += focus_z[k] * u * u / (2.0 * lam_f2);
     double r = turns - rint(turns);                 // FP64 reduction to [-1/2, 1/2]
     float s, c;
     sincospif((float)(2.0 * r), &s, &c);
@@ -129,10 +135,10 @@ inline int grid_for(size_t n, int threads = 256) {
 
 }  // namespace
 
-void launch_dft_rows(const double* focus_xy, int coord, int K, int n, double pitch, double lam_f,
-                     float2* out, cudaStream_t s) {
-  dft_rows_kernel<<<grid_for((size_t)K * n), 256, 0, s>>>(focus_xy, coord, K, n, pitch, lam_f,
-                                                           out);
+void launch_dft_rows(const double* focus_xy, const double* focus_z, int coord, int K, int n,
+                     double pitch, double lam_f, double lam_f2, float2* out, cudaStream_t s) {
+  dft_rows_kernel<<<grid_for((size_t)K * n), 256, 0, s>>>(focus_xy, focus_z, coord, K, n, pitch,
+                                                           lam_f, lam_f2, out);
 }
 
 void launch_default_amplitude(float* amp, int nx, int ny, double px, double py, double wf,

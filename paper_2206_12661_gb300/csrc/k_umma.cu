@@ -853,6 +853,16 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
                                          g->kb_total, g->ep, nullptr, 1, 1, g->tail_count);
 }
 
+// Diagnostic: the bounded wait of the pipelines above, on a barrier nothing
+// arrives at (expected phase 0 of a barrier initialised with one arrival).
+__global__ void selftest_wait_kernel(OfaDevState* st) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  fence_mbar_init();
+  if (!mbar_wait(b, 0)) atomicOr(&st->err, OFA_ERRBIT_TIMEOUT);
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1025,6 +1035,10 @@ cudaError_t tc_prepare(int prec) {
 }
 
 bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err);
+
+void launch_selftest_wait(OfaDevState* st, cudaStream_t s) {
+  selftest_wait_kernel<<<1, 1, 0, s>>>(st);
+}
 
 namespace {
 struct TuneResult {

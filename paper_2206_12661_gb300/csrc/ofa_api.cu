@@ -9,6 +9,7 @@
 // The threshold test of Algorithm 1 runs on the device (focal kernel sets a
 // flag that makes the rest of a launch skip); the host checks it between
 // chunks only when a threshold is set.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -27,10 +28,17 @@ const char* kStatusNames[] = {"OFA_OK",          "OFA_ERR_INVALID_ARG", "OFA_ERR
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
+// Host-side fault injection for the error paths of plan creation: with
+// OFA_FAULT_ALLOC=N in the environment, the N-th device allocation of an
+// ofa_plan_create call fails as if the device were out of memory.
+thread_local int g_fault_alloc_countdown = 0;
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
+  if (g_fault_alloc_countdown > 0 && --g_fault_alloc_countdown == 0)
+    return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
   if (e == cudaSuccess) e = cudaMemset(*p, 0, count * sizeof(T));
   return e;
@@ -247,6 +255,7 @@ ofa_status ofa_options_default(ofa_options* o) {
   o->mem_space = OFA_MEM_HOST;
   o->weighting = 1;
   o->autotune = 1;
+  o->focus_z = nullptr;
   return OFA_OK;
 }
 
@@ -324,7 +333,7 @@ ofa_status ofa_destroy(ofa_plan* p) {
   cudaSetDevice(p->device);
   if (p->stream || p->own_stream) cudaStreamSynchronize(p->stream);
   destroy_graphs(p);
-  void* bufs[] = {p->focus_xy, p->t,     p->amp,   p->phi,   p->w,    p->fx,
+  void* bufs[] = {p->focus_xy, p->focus_z, p->t,     p->amp,   p->phi,   p->w,    p->fx,
                   p->fy,       p->fyT,   p->part,  p->theta, p->inten, p->c,
                   p->hist,     p->st,    p->scratch_phi, p->counters, p->e32, p->e32_aux};
   for (void* b : bufs) dfree(b);
@@ -368,20 +377,44 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   // Host copies of the small inputs for validation.
   std::vector<double> xy(2 * (size_t)n_foci);
   std::vector<float> tgt(n_foci);
+  std::vector<double> zz(opt.focus_z ? (size_t)n_foci : 0);
   if (opt.mem_space == OFA_MEM_DEVICE) {
     cudaError_t e = cudaMemcpy(xy.data(), focus_xy, xy.size() * sizeof(double),
                                cudaMemcpyDeviceToHost);
     if (e == cudaSuccess)
       e = cudaMemcpy(tgt.data(), target_intensity, tgt.size() * sizeof(float),
                      cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && opt.focus_z)
+      e = cudaMemcpy(zz.data(), opt.focus_z, zz.size() * sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "reading device inputs");
   } else {
     std::memcpy(xy.data(), focus_xy, xy.size() * sizeof(double));
     std::memcpy(tgt.data(), target_intensity, tgt.size() * sizeof(float));
+    if (opt.focus_z) std::memcpy(zz.data(), opt.focus_z, zz.size() * sizeof(double));
   }
   ofa_status vs = ofa_check_foci(n_foci, xy.data(), pitch_x, pitch_y, wavelength, focal_length,
                                  nullptr);
   if (vs != OFA_OK) return vs;
+  if (opt.focus_z) {
+    // the defocus phase shifts the local spatial frequency at the pupil edge by
+    // z u_max / (lambda f^2): the effective position |x| + |z| u_max / f must stay
+    // inside the alias-free field
+    const double hx = wavelength * focal_length / (2.0 * pitch_x);
+    const double hy = wavelength * focal_length / (2.0 * pitch_y);
+    const double ux = 0.5 * (nx - 1) * pitch_x, uy = 0.5 * (ny - 1) * pitch_y;
+    for (int k = 0; k < n_foci; ++k) {
+      const double z = zz[k];
+      if (!std::isfinite(z))
+        return ofa_fail(nullptr, OFA_ERR_INVALID_ARG,
+                        "focus " + std::to_string(k) + " has a non-finite axial offset");
+      if (std::fabs(z) >= focal_length ||
+          std::fabs(xy[2 * k]) + std::fabs(z) * ux / focal_length >= hx ||
+          std::fabs(xy[2 * k + 1]) + std::fabs(z) * uy / focal_length >= hy)
+        return ofa_fail(nullptr, OFA_ERR_OUT_OF_RANGE,
+                        "focus " + std::to_string(k) +
+                            ": the defocus phase of its axial offset is not sampled by the pupil");
+    }
+  }
   double tsum = 0.0;
   for (int k = 0; k < n_foci; ++k) {
     if (!std::isfinite(tgt[k]) || tgt[k] < 0.f)
@@ -418,9 +451,14 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
 
   auto fail = [&](ofa_status s) {
     g_thread_error = p->last_error;
+    g_fault_alloc_countdown = 0;
     ofa_destroy(p);
     return s;
   };
+  {
+    const char* f = getenv("OFA_FAULT_ALLOC");
+    g_fault_alloc_countdown = f ? std::max(0, atoi(f)) : 0;
+  }
 #define OFA_TRY(call, what)                                   \
   do {                                                        \
     cudaError_t e_ = (call);                                  \
@@ -439,6 +477,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   const bool tc = prec_is_tc(p->precision);
   const int n_part_max = tc ? (p->nyp / 128) * 8 : simt_fwd_tiles(ny);
   OFA_TRY(dalloc(&p->focus_xy, 2 * (size_t)n_foci), "alloc");
+  if (opt.focus_z) OFA_TRY(dalloc(&p->focus_z, (size_t)n_foci), "alloc");
   OFA_TRY(dalloc(&p->t, n_foci), "alloc");
   OFA_TRY(dalloc(&p->amp, npix), "alloc");
   OFA_TRY(dalloc(&p->phi, npix), "alloc");
@@ -469,6 +508,9 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   for (int k = 0; k < n_foci; ++k) tn[k] = (float)(tgt[k] / tsum);
   OFA_TRY(cudaMemcpy(p->focus_xy, xy.data(), xy.size() * sizeof(double), cudaMemcpyHostToDevice),
           "copy foci");
+  if (opt.focus_z)
+    OFA_TRY(cudaMemcpy(p->focus_z, zz.data(), zz.size() * sizeof(double), cudaMemcpyHostToDevice),
+            "copy axial offsets");
   OFA_TRY(cudaMemcpy(p->t, tn.data(), tn.size() * sizeof(float), cudaMemcpyHostToDevice),
           "copy targets");
   OFA_TRY(cudaMemcpy(p->w, ones.data(), ones.size() * sizeof(float), cudaMemcpyHostToDevice),
@@ -518,8 +560,11 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
 
   // Kernel (a): DFT rows with FP64 phase reduction.
   const double lam_f = wavelength * focal_length;
-  launch_dft_rows(p->focus_xy, 0, n_foci, nx, pitch_x, lam_f, p->fx, p->stream);
-  launch_dft_rows(p->focus_xy, 1, n_foci, ny, pitch_y, lam_f, p->fy, p->stream);
+  const double lam_f2 = lam_f * focal_length;
+  launch_dft_rows(p->focus_xy, p->focus_z, 0, n_foci, nx, pitch_x, lam_f, lam_f2, p->fx,
+                  p->stream);
+  launch_dft_rows(p->focus_xy, p->focus_z, 1, n_foci, ny, pitch_y, lam_f, lam_f2, p->fy,
+                  p->stream);
   if (tc) {
     launch_transpose_fy(p->fy, n_foci, ny, p->kp, p->nyp, p->fyT, p->stream);
     launch_pack_fx(p->fx, n_foci, nx, p->kp, p->nxp, 0, p->precision, p->tc.bx_hi, p->tc.bx_lo,
@@ -548,6 +593,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   launch_control(p->st, 0.0, 1, p->stream);
   OFA_TRY(cudaGetLastError(), "launching set-up kernels");
   OFA_TRY(cudaStreamSynchronize(p->stream), "plan set-up");
+  g_fault_alloc_countdown = 0;
 #undef OFA_TRY
   *out = p;
   return OFA_OK;
@@ -882,6 +928,23 @@ ofa_status ofa_batch_create(ofa_batch** out, ofa_plan* const* plans, int count, 
   }
   *out = b;
   return OFA_OK;
+}
+
+ofa_status ofa_selftest_bounded_wait(void) {
+  OfaDevState* st = nullptr;
+  cudaError_t e = cudaMalloc(&st, sizeof(OfaDevState));
+  if (e == cudaSuccess) e = cudaMemset(st, 0, sizeof(OfaDevState));
+  if (e == cudaSuccess) {
+    launch_selftest_wait(st, nullptr);
+    e = cudaGetLastError();
+  }
+  OfaDevState h{};
+  if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(OfaDevState), cudaMemcpyDeviceToHost);
+  if (st) cudaFree(st);
+  if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "bounded-wait self-test");
+  if (h.err & OFA_ERRBIT_TIMEOUT)
+    return ofa_fail(nullptr, OFA_ERR_TIMEOUT, "a bounded device wait gave up (self-test)");
+  return ofa_fail(nullptr, OFA_OK, "the self-test wait completed");
 }
 
 ofa_status ofa_batch_info(const ofa_batch* b, int* grouped, int* fwd_bn, int* inv_bn) {

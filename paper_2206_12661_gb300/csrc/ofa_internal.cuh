@@ -69,6 +69,7 @@ struct ofa_plan {
   double amp_energy = 0;               // sum of user A^2
 
   double* focus_xy = nullptr;          // [K][2]
+  double* focus_z = nullptr;           // [K] axial offsets, or NULL (2D)
   float* t = nullptr;                  // [K] normalised targets
   float* amp = nullptr;                // [ny][nx]
   float* phi = nullptr;                // [ny][nx]
@@ -105,8 +106,8 @@ ofa_status ofa_cuda_check(ofa_plan* p, cudaError_t e, const char* what);
 void ofa_set_thread_error(const std::string& msg);
 
 // ---------------------------------------------------------------- kernels (k_gen.cu)
-void launch_dft_rows(const double* focus_xy, int coord, int K, int n, double pitch,
-                     double lam_f, float2* out, cudaStream_t s);
+void launch_dft_rows(const double* focus_xy, const double* focus_z, int coord, int K, int n,
+                     double pitch, double lam_f, double lam_f2, float2* out, cudaStream_t s);
 void launch_default_amplitude(float* amp, int nx, int ny, double px, double py, double waist_frac,
                               cudaStream_t s);
 void launch_default_phase(float* phi, int nx, int ny, uint64_t seed, cudaStream_t s);
@@ -151,6 +152,9 @@ cudaError_t tc_prepare(int prec);
 // fastest in t (cached per device, size and precision for the process).
 bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err);
 bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err);
+// One thread waits, with the bounded wait of the tensor-core kernels, on an mbarrier
+// nothing arrives at; it sets OFA_ERRBIT_TIMEOUT in st->err when the wait gives up.
+void launch_selftest_wait(OfaDevState* st, cudaStream_t s);
 // fuse_focal: the last CTA runs the focal step of the loop (mode 0) on the final Theta.
 void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s,
                    bool fuse_focal);

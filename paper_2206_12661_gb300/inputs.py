@@ -39,6 +39,7 @@ class Workload:
     phi0: np.ndarray              # [ny][nx] float32, radians in [-pi, pi)
     n_iter: int
     meta: dict = field(default_factory=dict)
+    focus_z: np.ndarray | None = None   # [K] float64 axial offsets (m) of 3D foci, or None
 
     @property
     def n_foci(self) -> int:
@@ -186,6 +187,29 @@ def rect_workload(nx: int = 1920, ny: int = 1152, cols: int = 50, rows: int = 50
     return w
 
 
+def volume_workload(n: int = 512, cols: int = 7, rows: int = 7, layers: int = 3,
+                    z_span: float = 0.1, n_iter: int = 50, seed: int = 6,
+                    name: str | None = None) -> Workload:
+    """3D array: `layers` jittered cols x rows grids (pitch 3 spots), layer l at
+    axial offset z_l spread evenly over [-z_span/2, z_span/2], each layer's grid
+    shifted by half a pitch so layers do not overlap in x-y, targets 1."""
+    rng = np.random.default_rng(seed)
+    s = spot_size(n)
+    xy, zz = [], []
+    for l in range(layers):
+        g = jittered_grid(rng, cols, rows, 3 * s, 3 * s)
+        g += (l - (layers - 1) / 2.0) * 1.5 * s
+        xy.append(g)
+        z = 0.0 if layers == 1 else -z_span / 2 + l * z_span / (layers - 1)
+        zz.append(np.full(g.shape[0], z))
+    xy = np.concatenate(xy)
+    w = _make(name or f"volume{n}x{n}_{xy.shape[0]}foci", n, n, xy, np.ones(xy.shape[0]), rng,
+              n_iter, {"layout": "jittered grids in layers", "layers": layers,
+                       "z_span_m": z_span, "seed": seed})
+    w.focus_z = np.ascontiguousarray(np.concatenate(zz), dtype=np.float64)
+    return w
+
+
 def batch_workloads(count: int = 256, sizes=(512, 768, 1024), k_min: int = 16, k_max: int = 4096,
                     n_iter: int = 50, seed: int = 5) -> list[Workload]:
     """Uneven batch: N drawn from sizes, K log-uniform in [k_min, k_max], jittered grid foci."""
@@ -210,6 +234,8 @@ NAMED = {
                                                       name="pupil1024_poisson1000"),
     "pupil1920x1152_grid2500": lambda: rect_workload(1920, 1152, 50, 50, n_iter=50, seed=3,
                                                      name="pupil1920x1152_grid2500"),
+    "pupil512_volume147": lambda: volume_workload(512, 7, 7, 3, z_span=0.1, n_iter=50, seed=6,
+                                                  name="pupil512_volume147"),
     "pupil1024_grid400_adam": lambda: grid_workload(1024, 20, 20, n_iter=200, seed=4,
                                                     uniform_targets=False,
                                                     name="pupil1024_grid400_adam"),

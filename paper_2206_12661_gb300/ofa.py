@@ -42,7 +42,8 @@ OFA_MEM_DEVICE = 1
 class ofa_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("seed", C.c_uint64), ("cuda_stream", C.c_void_p),
                 ("amplitude", C.c_void_p), ("waist_frac", C.c_double), ("phi0", C.c_void_p),
-                ("mem_space", C.c_int), ("weighting", C.c_int), ("autotune", C.c_int)]
+                ("mem_space", C.c_int), ("weighting", C.c_int), ("autotune", C.c_int),
+                ("focus_z", C.c_void_p)]
 
 
 class ofa_stats(C.Structure):
@@ -74,6 +75,7 @@ SIGNATURES = [
     ("ofa_batch_iterate", _I, [_P, _I]),
     ("ofa_batch_destroy", _I, [_P]),
     ("ofa_batch_info", _I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    ("ofa_selftest_bounded_wait", _I, []),
     ("ofa_forward_noalloc", _I, [_I, _I, _D, _D, _D, _D, _I, _P, _P, _P, _P, _P, _P]),
     ("ofa_fft_equivalent_size", _I, [_I, _D, _D, _D, _D, C.POINTER(_I)]),
     ("ofa_max_foci_per_axis", _I, [_D, _D, _D, _D, C.POINTER(_I)]),
@@ -236,6 +238,12 @@ def ofa_batch_destroy(batch):
     _check(_lib.ofa_batch_destroy(batch))
 
 
+def ofa_selftest_bounded_wait() -> int:
+    """Run one bounded device wait that nothing ends; returns the raw status
+    (OFA_ERR_TIMEOUT is the expected, healthy outcome)."""
+    return int(_lib.ofa_selftest_bounded_wait())
+
+
 def ofa_batch_info(batch) -> dict:
     g, f, i = C.c_int(0), C.c_int(0), C.c_int(0)
     _check(_lib.ofa_batch_info(batch, C.byref(g), C.byref(f), C.byref(i)))
@@ -281,7 +289,8 @@ class Plan:
 
     def __init__(self, nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy, target,
                  precision="f16x3", amplitude=None, phi0=None, seed=0, weighting=True,
-                 stream=None, waist_frac=0.4, mem_space=OFA_MEM_HOST, autotune=True):
+                 stream=None, waist_frac=0.4, mem_space=OFA_MEM_HOST, autotune=True,
+                 focus_z=None):
         opt = ofa_options_default()
         opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opt.seed = int(seed)
@@ -297,9 +306,12 @@ class Plan:
                 amplitude = np.ascontiguousarray(amplitude, dtype=np.float32)
             if phi0 is not None:
                 phi0 = np.ascontiguousarray(phi0, dtype=np.float32)
-        self._keep = (focus_xy, target, amplitude, phi0)
+            if focus_z is not None:
+                focus_z = np.ascontiguousarray(focus_z, dtype=np.float64)
+        self._keep = (focus_xy, target, amplitude, phi0, focus_z)
         opt.amplitude = _ptr(amplitude)
         opt.phi0 = _ptr(phi0)
+        opt.focus_z = _ptr(focus_z)
         self.nx, self.ny, self.K = int(nx), int(ny), int(focus_xy.shape[0])
         self.handle = ofa_plan_create(nx, ny, pitch_x, pitch_y, wavelength, focal_length,
                                       focus_xy, target, opt)
@@ -307,6 +319,8 @@ class Plan:
 
     @classmethod
     def from_workload(cls, w, **kw):
+        if getattr(w, "focus_z", None) is not None:
+            kw.setdefault("focus_z", w.focus_z)
         return cls(w.nx, w.ny, w.pitch_x, w.pitch_y, w.wavelength, w.focal_length, w.focus_xy,
                    w.target, amplitude=w.amplitude, phi0=w.phi0, **kw)
 

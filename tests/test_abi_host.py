@@ -106,6 +106,24 @@ def test_plan_create_rejects_bad_input_before_touching_cuda(ofa):
     assert "precision" in ofa.ofa_last_error()
 
 
+def test_3d_axial_offsets_validated_before_touching_cuda(ofa):
+    xy = np.array([[1e-3, 0.0], [0.0, -1e-3]])
+    t = np.ones(2, np.float32)
+    o = ofa.ofa_options_default()
+    z = np.array([0.0, np.nan])
+    o.focus_z = z.ctypes.data
+    with pytest.raises(ofa.OfaError) as e:
+        ofa.ofa_plan_create(64, 64, 8e-6, 8e-6, 532e-9, 0.2, xy, t, o)
+    assert e.value.status == ofa.OFA_ERR_INVALID_ARG
+    # |z| >= f, and a defocus whose phase the pupil cannot sample
+    for bad in (np.array([0.0, 0.25]), np.array([0.19, 0.0])):
+        o.focus_z = bad.ctypes.data
+        n = 4096 if bad[0] else 64
+        with pytest.raises(ofa.OfaError) as e:
+            ofa.ofa_plan_create(n, n, 8e-6, 8e-6, 532e-9, 0.2, xy, t, o)
+        assert e.value.status == ofa.OFA_ERR_OUT_OF_RANGE, ofa.ofa_last_error()
+
+
 def test_null_safe_destroy(ofa):
     ofa.ofa_destroy(None)
     ofa.ofa_batch_destroy(None)

@@ -223,6 +223,38 @@ def test_full_run_1920x1152_forms(ofa, oracle_1920, prec):
     assert abs(st.uniformity - ref["uniformity"]) < u_tol
 
 
+@pytest.mark.parametrize("prec", ALL)
+@pytest.mark.parametrize("shape", [(96, 80, 13), (300, 260, 150)])
+def test_forward_3d_foci(ofa, dev, prec, shape):
+    """3D foci: the defocus phase folded into the DFT rows, against the oracle."""
+    nx, ny, K = shape
+    w = custom(nx, ny, K, seed=31)
+    w.focus_z = np.random.default_rng(32).uniform(-60e-3, 60e-3, K)
+    fx, fy = O.plan_matrices(w.nx, w.ny, w.pitch_x, w.pitch_y, w.wavelength, w.focal_length,
+                             w.focus_xy, focus_z=w.focus_z)
+    ref = O.forward(O.pupil_field(w.amplitude, w.phi0), fx, fy)
+    got, _ = gpu_forward(ofa, w, prec)
+    err, _ = amp_err(got, ref)
+    assert err < AMP_TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "fp32"])
+def test_full_run_volume(ofa, dev, prec):
+    """Three layers of 49 foci at z = -50, 0, +50 mm: final xi and U within 1e-3 of FP64."""
+    w = I.named("pupil512_volume147")
+    fx, fy = O.plan_matrices(w.nx, w.ny, w.pitch_x, w.pitch_y, w.wavelength, w.focal_length,
+                             w.focus_xy, focus_z=w.focus_z)
+    ref = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, w.n_iter)
+    plan = ofa.Plan.from_workload(w, precision=prec)
+    it, xi = plan.iterate(w.n_iter, want_stats=True)
+    st = plan.stats()
+    plan.close()
+    assert it == w.n_iter
+    assert abs(xi - ref["xi"]) < 1e-3, (xi, ref["xi"])
+    assert abs(st.uniformity - ref["uniformity"]) < 1e-3
+    assert ref["xi"] > 0.95
+
+
 def test_single_focus_closed_form(ofa, dev):
     """K = 1: one iteration gives the linear ramp; the next forward has |Theta| = sum A, xi = 1."""
     w = custom(96, 80, 1, seed=3)

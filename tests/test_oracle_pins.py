@@ -121,6 +121,61 @@ def test_single_focus_linear_ramp():
     assert abs(out["xi"] - 1.0) < 1e-12
 
 
+# ------------------------------------------------ 3D foci (defocus phase of the pupil function)
+def test_3d_single_focus_lens_phase():
+    """K = 1 at (x0, y0, z0): one cycle gives the ramp plus the Fresnel lens term
+    pi z0 (u^2 + v^2) / (lambda f^2); the next forward has |Theta| = sum A."""
+    rng = np.random.default_rng(21)
+    ny, nx = 14, 18
+    x0, y0, z0 = 0.9e-3, -1.1e-3, 7.5e-3
+    A = O.default_amplitude(nx, ny, P, P)
+    phi0 = rng.uniform(-np.pi, np.pi, (ny, nx))
+    fx, fy = O.plan_matrices(nx, ny, P, P, LAM, F, [[x0, y0]], focus_z=[z0])
+    theta0 = O.forward(O.pupil_field(A, phi0), fx, fy)
+    out = O.gsw(A, phi0, fx, fy, np.array([1.0]), n_iter=1)
+    u = (np.arange(nx) - (nx - 1) / 2) * P
+    v = (np.arange(ny) - (ny - 1) / 2) * P
+    lens = np.pi * z0 * (u[None, :] ** 2 + v[:, None] ** 2) / (LAM * F * F)
+    want = np.angle(theta0[0]) + 2 * np.pi * (x0 * u[None, :] + y0 * v[:, None]) / (LAM * F) + lens
+    assert np.max(np.abs(np.exp(1j * out["phi"]) - np.exp(1j * want))) < 1e-9
+    assert abs(np.abs(out["theta"][0]) - A.sum()) < 1e-12 * A.sum()
+    # on a 64^2 pupil the lens phase of z0 = 50 mm reaches 0.5 rad at the edge: the
+    # focus moves off the focal plane (|Theta(z=0)| < |Theta(z0)| = sum A)
+    n2, z1 = 64, 50e-3
+    A2 = O.default_amplitude(n2, n2, P, P)
+    fx, fy = O.plan_matrices(n2, n2, P, P, LAM, F, [[x0, y0]], focus_z=[z1])
+    phi = O.gsw(A2, np.zeros((n2, n2)), fx, fy, np.array([1.0]), n_iter=1)["phi"]
+    at = O.forward(O.pupil_field(A2, phi), fx, fy)
+    fx0, fy0 = O.plan_matrices(n2, n2, P, P, LAM, F, [[x0, y0]], focus_z=[0.0])
+    off = O.forward(O.pupil_field(A2, phi), fx0, fy0)
+    assert abs(np.abs(at[0]) - A2.sum()) < 1e-12 * A2.sum()
+    assert np.abs(off[0]) < 0.99 * A2.sum()
+
+
+def test_3d_forward_equals_brute_force_sum():
+    """Separable rows against the non-separated sum with the full 2D exponent."""
+    rng = np.random.default_rng(22)
+    ny, nx, K = 6, 9, 4
+    E = rand_field(rng, ny, nx)
+    xy = rng.uniform(-2e-3, 2e-3, (K, 2))
+    z = rng.uniform(-20e-3, 20e-3, K)
+    fx, fy = O.plan_matrices(nx, ny, P, P, LAM, F, xy, focus_z=z)
+    got = O.forward(E, fx, fy)
+    want = np.zeros(K, complex)
+    for k in range(K):
+        for n in range(ny):
+            for m in range(nx):
+                u, v = (m - (nx - 1) / 2) * P, (n - (ny - 1) / 2) * P
+                ph = 2 * math.pi * (xy[k, 0] * u + xy[k, 1] * v) / (LAM * F) + \
+                    math.pi * z[k] * (u * u + v * v) / (LAM * F * F)
+                want[k] += E[n, m] * cmath.exp(-1j * ph)
+    assert rel(got, want) < 1e-12
+    # z = 0 is the 2D operator exactly
+    fx0, fy0 = O.plan_matrices(nx, ny, P, P, LAM, F, xy, focus_z=np.zeros(K))
+    fx2, fy2 = O.plan_matrices(nx, ny, P, P, LAM, F, xy)
+    assert np.array_equal(fx0, fx2) and np.array_equal(fy0, fy2)
+
+
 # ------------------------------------------------ Parseval / Bessel
 def test_parseval_and_bessel():
     rng = np.random.default_rng(15)
