@@ -141,6 +141,23 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
  */
 ofa_status ofa_iterate(ofa_plan* plan, int n_iter, double threshold, int* iters_done, double* xi);
 
+/*
+ * ofa_iterate_measured -- one iteration in the camera-in-the-loop mode of the
+ * paper's experiments (Sec. 3): once the intensity accuracy has passed a threshold
+ * (0.95 there), the calculated focus intensities are replaced by captured ones in
+ * the weight update, w_j = w_{j-1} sqrt(I~ / I_meas) at unit sums; the focused field
+ * keeps the phase of the calculated Theta (a camera records intensities only).
+ *   measured     [K] float32 captured focus intensities >= 0, any common scale, in
+ *                mem_space (host values are checked: non-finite or negative ->
+ *                OFA_ERR_INVALID_ARG)
+ *   xi_measured  (nullable, host) intensity accuracy of the captured intensities
+ * Runs forward, update and inverse once (not graph-captured: each call follows a
+ * capture) and synchronises.  The caller decides when to switch to this mode and
+ * captures the OFA of the current phase (ofa_get_phase) between calls.
+ */
+ofa_status ofa_iterate_measured(ofa_plan* plan, const float* measured, int mem_space,
+                                double* xi_measured);
+
 /* Copy the current CGH phi [ny][nx] (radians in (-pi, pi]) to phi_out, which lives in
  * out_mem_space.  Synchronises the plan's stream for host output. */
 ofa_status ofa_get_phase(const ofa_plan* plan, float* phi_out, int out_mem_space);

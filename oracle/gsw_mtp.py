@@ -155,6 +155,20 @@ def focused_field(w: np.ndarray, target: np.ndarray, theta: np.ndarray) -> np.nd
     return np.asarray(w, np.float64) * np.sqrt(t) * np.exp(1j * psi)
 
 
+def camera_step(amplitude, phi, fx, fy, target, w, measured):
+    """One iteration of the camera-in-the-loop mode (Sec. 3, experiments): the loop of
+    Algorithm 1 with the calculated intensities replaced by captured ones in the
+    weight update; the focused field keeps the phase of the calculated Theta (a
+    camera records intensities only).  Returns (phi, w, xi of the measurement)."""
+    A = np.asarray(amplitude, np.float64)
+    theta = forward(pupil_field(A, phi), fx, fy)
+    meas = np.asarray(measured, np.float64)
+    xi = intensity_accuracy(target, meas)
+    w = generalized_weights(w, target, meas)
+    field = focused_field(w, target, theta)
+    return phase_projection(adjoint(field, fx, fy)), w, xi
+
+
 # ----------------------------------------------------------- the GSW loop
 def gsw(amplitude, phi0, fx, fy, target, n_iter, threshold=None, weighting=True, w0=None,
         record=False):

@@ -235,6 +235,28 @@ __global__ void __launch_bounds__(FT) focal_iter_kernel(
                          ofa_focal::BarBlock());
 }
 
+// The loop's focal step with captured intensities (camera in the loop).
+__global__ void __launch_bounds__(FT) focal_measured_kernel(
+    const float2* __restrict__ part, int n_part, int kp, int K, const float* __restrict__ t,
+    float* __restrict__ w, float2* __restrict__ theta, float2* __restrict__ c,
+    double* __restrict__ hist, OfaDevState* __restrict__ st, int weighting,
+    const float* __restrict__ meas) {
+  __shared__ float sh[4 * 33];
+  if (st->done) return;
+  for (int k = threadIdx.x; k < K; k += FT) {
+    float2 a = make_float2(0.f, 0.f);
+    for (int p = 0; p < n_part; ++p) {
+      const float2 v = part[(size_t)p * kp + k];
+      a.x += v.x;
+      a.y += v.y;
+    }
+    theta[k] = a;
+  }
+  __syncthreads();
+  ofa_focal::iterate<FT>(theta, K, kp, t, w, c, hist, st, weighting, sh, (int)threadIdx.x,
+                         ofa_focal::BarBlock(), meas);
+}
+
 // Mode 0 for K <= 4096: everything from registers (ofa_focal::iterate_regs).
 __global__ void __launch_bounds__(FT) focal_regs_kernel(
     const float2* __restrict__ part, int n_part, int kp, int K, const float* __restrict__ t,
@@ -390,6 +412,13 @@ void launch_focal(const float2* part, int n_part, int kp, int K, const float* t,
   }
   focal_kernel<<<1, FT, 0, s>>>(part, n_part, kp, K, t, w, theta, inten, c, hist, st, mode,
                                 weighting, out_scale, energy);
+}
+
+void launch_focal_measured(const float2* part, int n_part, int kp, int K, const float* t,
+                           float* w, float2* theta, float2* c, double* hist, OfaDevState* st,
+                           int weighting, const float* meas, cudaStream_t s) {
+  focal_measured_kernel<<<1, FT, 0, s>>>(part, n_part, kp, K, t, w, theta, c, hist, st,
+                                         weighting, meas);
 }
 
 void launch_control(OfaDevState* st, double threshold, int reset_done, cudaStream_t s) {

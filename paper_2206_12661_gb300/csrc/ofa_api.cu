@@ -335,7 +335,8 @@ ofa_status ofa_destroy(ofa_plan* p) {
   destroy_graphs(p);
   void* bufs[] = {p->focus_xy, p->focus_z, p->t,     p->amp,   p->phi,   p->w,    p->fx,
                   p->fy,       p->fyT,   p->part,  p->theta, p->inten, p->c,
-                  p->hist,     p->st,    p->scratch_phi, p->counters, p->e32, p->e32_aux};
+                  p->hist,     p->st,    p->scratch_phi, p->counters, p->e32, p->e32_aux,
+                  p->meas};
   for (void* b : bufs) dfree(b);
   if (p->st_host) cudaFreeHost(p->st_host);
   free_tc(p->tc);
@@ -490,6 +491,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   OFA_TRY(dalloc(&p->c, p->kp), "alloc");
   OFA_TRY(dalloc(&p->hist, OFA_HIST_CAP), "alloc");
   OFA_TRY(dalloc(&p->counters, p->kp / 64 + 1), "alloc");
+  OFA_TRY(dalloc(&p->meas, n_foci), "alloc");
   OFA_TRY(dalloc(&p->st, 1), "alloc");
   OFA_TRY(cudaMallocHost(reinterpret_cast<void**>(&p->st_host), sizeof(OfaDevState)),
           "pinned alloc");
@@ -649,6 +651,40 @@ ofa_status ofa_iterate(ofa_plan* p, int n_iter, double threshold, int* iters_don
     if (s != OFA_OK) return s;
     *xi = p->st_host->xi;
   }
+  return OFA_OK;
+}
+
+ofa_status ofa_iterate_measured(ofa_plan* p, const float* measured, int mem_space,
+                                double* xi_measured) {
+  if (!p || !measured) return ofa_fail(p, OFA_ERR_INVALID_ARG, "NULL argument");
+  if (mem_space != OFA_MEM_HOST && mem_space != OFA_MEM_DEVICE)
+    return ofa_fail(p, OFA_ERR_INVALID_ARG, "unknown memory space");
+  cudaSetDevice(p->device);
+  if (mem_space == OFA_MEM_HOST) {
+    for (int k = 0; k < p->K; ++k)
+      if (!std::isfinite(measured[k]) || measured[k] < 0.f)
+        return ofa_fail(p, OFA_ERR_INVALID_ARG, "measured intensities must be finite and >= 0");
+  }
+  cudaStream_t s = p->stream;
+  cudaError_t e = cudaMemcpyAsync(p->meas, measured, (size_t)p->K * sizeof(float),
+                                  kind_from(mem_space), s);
+  if (e != cudaSuccess) return ofa_cuda_check(p, e, "copying measured intensities");
+  launch_control(p->st, 0.0, 1, s);
+  // forward (partials only), focal step on the captured intensities, inverse
+  const int n_part = prec_is_tc(p->precision) ? fwd_n_part(p->nyp, p->tc) : simt_fwd_tiles(p->ny);
+  if (prec_is_tc(p->precision)) launch_fwd_tc(p, p->tc, nullptr, s, false);
+  else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, s);
+  launch_focal_measured(p->part, n_part, p->kp, p->K, p->t, p->w, p->theta, p->c, p->hist, p->st,
+                        p->weighting, p->meas, s);
+  if (prec_is_tc(p->precision)) {
+    launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
+    launch_bwd_tc(p, p->tc, nullptr, s);
+  } else {
+    launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->amp, p->phi, p->e32, nullptr, s);
+  }
+  ofa_status st = sync_and_check(p);
+  if (st != OFA_OK) return st;
+  if (xi_measured) *xi_measured = p->st_host->xi;
   return OFA_OK;
 }
 

@@ -112,17 +112,21 @@ __device__ __forceinline__ void block_sum2_max(float (&v)[2], float& mx, float* 
 
 // theta: the final Theta_k (K values, written by other threads or blocks of this
 // launch: read through L2); sh: >= 4 * 33 floats of shared memory.
+// meas (nullable): captured intensities that replace the calculated |Theta_k|^2 in
+// xi and the weight update (camera in the loop); the focused field keeps the
+// phase of the calculated Theta.
 template <int NT, class Bar>
 __device__ inline void iterate(const float2* theta, int K, int kp, const float* __restrict__ t,
                                float* __restrict__ w, float2* __restrict__ c,
                                double* __restrict__ hist, OfaDevState* __restrict__ st,
-                               int weighting, float* sh, int tid, Bar bar) {
+                               int weighting, float* sh, int tid, Bar bar,
+                               const float* __restrict__ meas = nullptr) {
   constexpr int nt = NT;
   const double thr = st->threshold;
   float r1[1] = {0.f};
   for (int k = tid; k < K; k += nt) {
     const float2 a = __ldcg(theta + k);
-    r1[0] += a.x * a.x + a.y * a.y;
+    r1[0] += meas ? meas[k] : a.x * a.x + a.y * a.y;
   }
   block_sum<NT>(r1, sh, tid, bar);
   const float S = r1[0];
@@ -138,7 +142,7 @@ __device__ inline void iterate(const float2* theta, int K, int kp, const float* 
   float mx = 0.f;
   for (int k = tid; k < K; k += nt) {
     const float2 a = __ldcg(theta + k);
-    const float ih = (a.x * a.x + a.y * a.y) * inv_s;
+    const float ih = (meas ? meas[k] : a.x * a.x + a.y * a.y) * inv_s;
     const float tk = t[k];
     const float d = tk - ih;
     r2[0] += d * d;
@@ -172,7 +176,8 @@ __device__ inline void iterate(const float2* theta, int K, int kp, const float* 
       const float tk = t[k];
       float wk = w[k];
       if (weighting) {
-        wk *= sqrtf(tk) * rsqrtf(fmaxf(rr * inv_s, 1e-30f));  // w_j = w_{j-1} sqrt(t / Ihat)
+        const float iu = meas ? meas[k] : rr;
+        wk *= sqrtf(tk) * rsqrtf(fmaxf(iu * inv_s, 1e-30f));  // w_j = w_{j-1} sqrt(t / Ihat)
         w[k] = wk;
       }
       const float mag = wk * sqrtf(tk) * scale;

@@ -89,6 +89,7 @@ struct ofa_plan {
   float* scratch_phi = nullptr;        // for ofa_forward / ofa_adjoint on the tensor path
   float2* e32 = nullptr;               // FP32 form: pupil field A exp(i phi) [ny][nx]
   float2* e32_aux = nullptr;           // FP32 form: field of an external phase
+  float* meas = nullptr;               // [K] captured intensities (camera in the loop)
   TcOperands tc;
   TcOperands tc_aux;                   // E planes of an external phase (forward/adjoint)
   bool aux_ready = false;
@@ -139,6 +140,9 @@ void launch_grad_simt(const float2* c, const float2* fx, const float2* fy, int n
 void launch_focal(const float2* part, int n_part, int kp, int K, const float* t, float* w,
                   float2* theta, float* inten, float2* c, double* hist, OfaDevState* st,
                   int mode, int weighting, float out_scale, double energy, cudaStream_t s);
+void launch_focal_measured(const float2* part, int n_part, int kp, int K, const float* t,
+                           float* w, float2* theta, float2* c, double* hist, OfaDevState* st,
+                           int weighting, const float* meas, cudaStream_t s);
 void launch_control(OfaDevState* st, double threshold, int reset_done, cudaStream_t s);
 void launch_set_j(OfaDevState* st, int j, int reset_hist, cudaStream_t s);
 void launch_grad_c(const float2* theta, const float* g, int K, int kp, float in_scale,

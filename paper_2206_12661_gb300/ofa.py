@@ -76,6 +76,7 @@ SIGNATURES = [
     ("ofa_batch_destroy", _I, [_P]),
     ("ofa_batch_info", _I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     ("ofa_selftest_bounded_wait", _I, []),
+    ("ofa_iterate_measured", _I, [_P, _P, _I, C.POINTER(_D)]),
     ("ofa_forward_noalloc", _I, [_I, _I, _D, _D, _D, _D, _I, _P, _P, _P, _P, _P, _P]),
     ("ofa_fft_equivalent_size", _I, [_I, _D, _D, _D, _D, C.POINTER(_I)]),
     ("ofa_max_foci_per_axis", _I, [_D, _D, _D, _D, C.POINTER(_I)]),
@@ -159,6 +160,15 @@ def ofa_iterate(plan, n_iter: int, threshold: float = 0.0, want_stats: bool = Fa
     xi = C.c_double()
     _check(_lib.ofa_iterate(plan, int(n_iter), float(threshold), C.byref(it), C.byref(xi)), plan)
     return it.value, xi.value
+
+
+def ofa_iterate_measured(plan, measured, mem_space: int = OFA_MEM_HOST) -> float:
+    """One camera-in-the-loop iteration; returns the captured intensities' xi."""
+    if mem_space == OFA_MEM_HOST:
+        measured = np.ascontiguousarray(measured, dtype=np.float32)
+    xi = C.c_double()
+    _check(_lib.ofa_iterate_measured(plan, _ptr(measured), int(mem_space), C.byref(xi)), plan)
+    return xi.value
 
 
 def ofa_get_phase(plan, out, mem_space: int):

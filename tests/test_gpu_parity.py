@@ -461,3 +461,51 @@ def test_batch_grouped_uneven_large(ofa, dev):
         assert abs(hb[0] - hq[0]) < 1e-6 and abs(hb[1] - hq[1]) < 2e-5, (w.name, hb, hq)
         q.close()
         p.close()
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "fp32"])
+def test_camera_step_matches_oracle(ofa, dev, prec):
+    """One camera-in-the-loop iteration from phi0 with a camera of per-focus gain g."""
+    w = I.named("pupil256_grid100_uniform")
+    fx, fy = oracle_mats(w)
+    A = w.amplitude.astype(np.float64)
+    g = np.random.default_rng(41).uniform(0.8, 1.2, w.n_foci)
+    I0 = np.abs(O.forward(O.pupil_field(A, w.phi0.astype(np.float64)), fx, fy)) ** 2
+    meas = g * I0
+    phi_ref, w_ref, xi_ref = O.camera_step(A, w.phi0.astype(np.float64), fx, fy, w.target,
+                                           np.ones(w.n_foci), meas)
+    plan = ofa.Plan.from_workload(w, precision=prec)
+    xi = ofa.ofa_iterate_measured(plan.handle, (1e-3 * meas).astype(np.float32))
+    phi, wt, j = plan.get_state()
+    plan.close()
+    assert j == 1 and abs(xi - xi_ref) < 1e-5, (xi, xi_ref)
+    assert np.allclose(wt / wt.mean(), w_ref / w_ref.mean(), rtol=1e-4)
+    # the phases agree where the field is not negligible: compare the next forward
+    th_gpu = O.forward(O.pupil_field(A, phi.astype(np.float64)), fx, fy)
+    th_ref = O.forward(O.pupil_field(A, phi_ref), fx, fy)
+    err, _ = amp_err(th_gpu, th_ref)
+    assert err < 1e-4, err
+
+
+def test_camera_in_the_loop_corrects_a_systematic_gain(ofa, dev):
+    """A camera that sees focus k with gain g_k (beam profile, aberration): after
+    the computed loop, captured-intensity iterations drive the captured OFA to the
+    targets, which the computed loop alone cannot do."""
+    w = I.named("pupil256_grid100_uniform")
+    fx, fy = oracle_mats(w)
+    A = w.amplitude.astype(np.float64)
+    g = np.random.default_rng(42).uniform(0.75, 1.25, w.n_foci)
+
+    def capture(plan):
+        phi = plan.phase().astype(np.float64)
+        return g * np.abs(O.forward(O.pupil_field(A, phi), fx, fy)) ** 2
+
+    plan = ofa.Plan.from_workload(w, precision="f16x3")
+    plan.iterate(30)
+    xi_before = O.intensity_accuracy(w.target, capture(plan))
+    xis = [ofa.ofa_iterate_measured(plan.handle, capture(plan).astype(np.float32))
+           for _ in range(20)]
+    xi_after = O.intensity_accuracy(w.target, capture(plan))
+    plan.close()
+    assert xi_before < 0.95, xi_before
+    assert xi_after > 0.99 and xi_after > xi_before + 0.03, (xi_before, xi_after, xis)

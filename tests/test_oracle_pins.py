@@ -176,6 +176,41 @@ def test_3d_forward_equals_brute_force_sum():
     assert np.array_equal(fx0, fx2) and np.array_equal(fy0, fy2)
 
 
+# ------------------------------------------------ camera-in-the-loop step
+def test_camera_step_with_a_perfect_camera_is_algorithm1():
+    rng = np.random.default_rng(23)
+    ny, nx, K = 20, 24, 6
+    A = O.default_amplitude(nx, ny, P, P)
+    xy = rng.uniform(-3e-3, 3e-3, (K, 2))
+    t = rng.uniform(0.5, 1.0, K)
+    fx, fy = O.plan_matrices(nx, ny, P, P, LAM, F, xy)
+    phi0 = rng.uniform(-np.pi, np.pi, (ny, nx))
+    w0 = rng.uniform(0.5, 2.0, K)
+    ref = O.gsw(A, phi0, fx, fy, t, n_iter=1, w0=w0)
+    I0 = np.abs(O.forward(O.pupil_field(A, phi0), fx, fy)) ** 2
+    phi, w, xi = O.camera_step(A, phi0, fx, fy, t, w0, 37.0 * I0)   # any camera scale
+    assert np.max(np.abs(np.exp(1j * phi) - np.exp(1j * ref["phi"]))) < 1e-12
+    assert np.allclose(w, ref["w"], rtol=1e-12) and abs(xi - ref["xi_hist"][0]) < 1e-12
+
+
+def test_camera_step_weights_see_the_camera_gain():
+    """A camera that reads focus k with gain g_k: the weights get an extra 1/sqrt(g_k)
+    up to the common normalisation factor."""
+    rng = np.random.default_rng(24)
+    ny, nx, K = 16, 16, 5
+    A = O.default_amplitude(nx, ny, P, P)
+    fx, fy = O.plan_matrices(nx, ny, P, P, LAM, F, rng.uniform(-3e-3, 3e-3, (K, 2)))
+    phi0 = rng.uniform(-np.pi, np.pi, (ny, nx))
+    t = np.ones(K)
+    g = rng.uniform(0.7, 1.3, K)
+    I0 = np.abs(O.forward(O.pupil_field(A, phi0), fx, fy)) ** 2
+    _, w_true, _ = O.camera_step(A, phi0, fx, fy, t, np.ones(K), I0)
+    _, w_cam, _ = O.camera_step(A, phi0, fx, fy, t, np.ones(K), g * I0)
+    ratio = (w_cam / w_true) * np.sqrt(g)
+    assert np.allclose(ratio, ratio[0], rtol=1e-12)
+    assert abs(ratio[0] - np.sqrt(np.sum(g * I0) / np.sum(I0))) < 1e-12
+
+
 # ------------------------------------------------ Parseval / Bessel
 def test_parseval_and_bessel():
     rng = np.random.default_rng(15)
