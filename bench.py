@@ -189,6 +189,37 @@ def bench_config(ofa, I, torch, stream, flush, name: str, precisions, reps: int 
     return out
 
 
+def bench_separable(ofa, I, torch, stream, flush, reps: int = 3) -> dict:
+    """Table 1 geometry (1000^2 pupil) with regular 9 x 9 and 45 x 47 grids: the
+    separable grid form (products through the distinct focus coordinates, FP32)
+    against the general tensor-core form (F16X3), iterations/s."""
+    out = {}
+    for name in ("table1_grid9x9", "table1_grid45x47"):
+        w = I.named(name)
+        rec = {"n_foci": w.n_foci}
+        for label, kw in (("separable_fp32", {"separable": 1, "precision": "fp32"}),
+                          ("general_f16x3", {"separable": 0, "precision": "f16x3"})):
+            with torch.cuda.stream(stream):
+                p = ofa.Plan.from_workload(w, stream=stream.cuda_stream, **kw)
+                p.iterate(w.n_iter)
+                ms = 0.0
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    p.iterate(w.n_iter)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms += e0.elapsed_time(e1)
+                rec[label] = {"iterations_per_s": reps * w.n_iter / (ms / 1000.0),
+                              "form": ofa.ofa_plan_form(p.handle), "xi": p.stats().xi}
+                p.close()
+        out[name] = rec
+    return out
+
+
 def bench_differentiation(ofa, I, torch, stream, flush, precision: str = "f16x3",
                           steps: int = 200) -> dict:
     """Adam on the focal-intensity loss (1024^2 pupil, 20x20 grid, random targets).
@@ -489,6 +520,7 @@ def main():
             bench_config(ofa, I, torch, stream, flush, "pupil1920x1152_grid2500", all_forms),
         ]
         result["batch"] = bench_batch(ofa, I, torch, stream, flush)
+        result["separable"] = bench_separable(ofa, I, torch, stream, flush)
 
     plan.close()
     if rank == 0 and not args.no_cpu_baseline:

@@ -89,6 +89,15 @@ typedef struct ofa_options {
                                 |z_k| < f, and |x_k| + |z_k| u_max / f must stay inside the
                                 alias-free field (u_max = (nx - 1) pitch_x / 2; same in y),
                                 else OFA_ERR_OUT_OF_RANGE.  In mem_space; default NULL */
+  int separable;             /* separable grid form: with foci on the grid of their U_x
+                                distinct x and U_y distinct y values (the paper's regular
+                                arrays), Theta on that grid is Fy_u E Fx_u^T (Eq. 2 through
+                                the distinct coordinates) and the inverse factors the same
+                                way, nx ny (U_x + U_y) complex products per iteration instead
+                                of 2 nx ny K; these run in FP32 on the CUDA cores whatever
+                                the precision.  -1 = when that is at most half the cost
+                                (default), 0 = never, 1 = always (OFA_ERR_UNSUPPORTED with
+                                focus_z) */
 } ofa_options;
 
 typedef struct ofa_stats {
@@ -221,6 +230,10 @@ ofa_status ofa_profile_kernels(ofa_plan* plan, int reps, double* ms_out);
  * (bytes of K), forward and inverse CTA group (1, or 2 for 2-SM MMA pairs of 256
  * accumulator rows).  The FP32 form reports zeros. */
 ofa_status ofa_plan_config(const ofa_plan* plan, int* config_out);
+
+/* Form of a plan: *separable = 1 with the U_x and U_y distinct focus coordinates it
+ * factors through (see ofa_options.separable), else 0 and zeros.  Outputs nullable. */
+ofa_status ofa_plan_form(const ofa_plan* plan, int* separable, int* ux, int* uy);
 
 /* Problem sizes of a plan (any output may be NULL). */
 ofa_status ofa_plan_info(const ofa_plan* plan, int* nx, int* ny, int* n_foci, int* precision);

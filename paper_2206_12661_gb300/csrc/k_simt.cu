@@ -65,6 +65,9 @@ __global__ void field_f32_kernel(const float* __restrict__ phi, const float* __r
   }
 }
 
+// STORE: instead of the per-focus dot, write the product itself transposed,
+// gt[k][n] = G[n][k] (the separable grid form's first product).
+template <bool STORE>
 __global__ void __launch_bounds__(256) fwd_simt_kernel(
     const float2* __restrict__ e32, const float2* __restrict__ fx, const float2* __restrict__ fy,
     int nx, int ny, int K, int kp, float2* __restrict__ part, const int* __restrict__ done) {
@@ -115,6 +118,19 @@ __global__ void __launch_bounds__(256) fwd_simt_kernel(
     b ^= 1;
   }
 
+  if (STORE) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + tx * 4 + j;
+      if (k >= K) continue;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int n = n0 + ty * 4 + i;
+        if (n < ny) part[(size_t)k * ny + n] = acc[i][j];
+      }
+    }
+    return;
+  }
   // Per-focus dot with the Fy rows, reduced over the tile's 64 rows in fixed order.
   float2* red = &Es[0][0][0];  // 16 x 64 float2
 #pragma unroll
@@ -245,6 +261,47 @@ __global__ void __launch_bounds__(256) bwd_simt_kernel(
   }
 }
 
+// Separable grid form, focal step of the forward: Theta_k = sum_n Fyu[iy_k][n] G[n][ix_k]
+// (one warp per focus, fixed-order shuffle tree), written as the single partial row.
+__global__ void sep_theta_kernel(const float2* __restrict__ gt, const float2* __restrict__ fyu,
+                                 const int2* __restrict__ ixy, int K, int ny,
+                                 float2* __restrict__ part) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= K) return;
+  const int2 q = ixy[warp];
+  const float2* g = gt + (size_t)q.x * ny;
+  const float2* f = fyu + (size_t)q.y * ny;
+  float2 a = make_float2(0.f, 0.f);
+  for (int n = lane; n < ny; n += 32) cmac(a, f[n], g[n]);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+    a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+  }
+  if (lane == 0) part[warp] = a;
+}
+
+// Separable grid form, first product of the inverse: for row iy of the grid,
+// T[iy][m] = sum over the foci of that row (in fixed order) of c_k conj(Fxu[ix_k][m]);
+// stored conjugated, as the inverse product conjugates its right operand.
+__global__ void sep_t_kernel(const float2* __restrict__ c, const float2* __restrict__ fxu,
+                             const int2* __restrict__ ixy, const int* __restrict__ row_ptr,
+                             const int* __restrict__ row_foci, int uy, int nx,
+                             float2* __restrict__ tconj) {
+  const size_t total = (size_t)uy * nx;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int iy = (int)(i / nx), m = (int)(i % nx);
+    float2 a = make_float2(0.f, 0.f);
+    for (int r = row_ptr[iy]; r < row_ptr[iy + 1]; ++r) {
+      const int k = row_foci[r];
+      const float2 f = fxu[(size_t)ixy[k].x * nx + m];
+      cmac(a, c[k], make_float2(f.x, -f.y));
+    }
+    tconj[i] = make_float2(a.x, -a.y);
+  }
+}
+
 }  // namespace
 
 constexpr int FWD_SPLIT = 1;  // contraction parts of the forward (grid z)
@@ -262,7 +319,26 @@ void launch_field_f32(const float* phi, const float* amp, int nx, int ny, float2
 void launch_fwd_simt(const float2* e32, const float2* fx, const float2* fy, int nx, int ny, int K,
                      int kp, float2* part, const int* done, cudaStream_t s) {
   dim3 grid((K + T64 - 1) / T64, (ny + T64 - 1) / T64, FWD_SPLIT);
-  fwd_simt_kernel<<<grid, 256, 0, s>>>(e32, fx, fy, nx, ny, K, kp, part, done);
+  fwd_simt_kernel<false><<<grid, 256, 0, s>>>(e32, fx, fy, nx, ny, K, kp, part, done);
+}
+
+void launch_sep_forward(const float2* e32, const float2* fxu, int nx, int ny, int ux,
+                        float2* gt, cudaStream_t s) {
+  dim3 grid((ux + T64 - 1) / T64, (ny + T64 - 1) / T64, 1);
+  fwd_simt_kernel<true><<<grid, 256, 0, s>>>(e32, fxu, nullptr, nx, ny, ux, ux, gt, nullptr);
+}
+
+void launch_sep_theta(const float2* gt, const float2* fyu, const int2* ixy, int K, int ny,
+                      float2* part, cudaStream_t s) {
+  sep_theta_kernel<<<(K + 7) / 8, 256, 0, s>>>(gt, fyu, ixy, K, ny, part);
+}
+
+void launch_sep_t(const float2* c, const float2* fxu, const int2* ixy, const int* row_ptr,
+                  const int* row_foci, int uy, int nx, float2* tconj, cudaStream_t s) {
+  const size_t total = (size_t)uy * nx;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  sep_t_kernel<<<(unsigned)blocks, 256, 0, s>>>(c, fxu, ixy, row_ptr, row_foci, uy, nx, tconj);
 }
 
 void launch_bwd_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,

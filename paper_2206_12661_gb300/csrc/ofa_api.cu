@@ -48,6 +48,10 @@ void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
+// The tensor-core products run unless the plan uses the separable grid form (whose
+// products are small and run on the CUDA cores in FP32).
+inline bool use_tc(const ofa_plan* p) { return prec_is_tc(p->precision) && !p->sep; }
+
 cudaMemcpyKind kind_from(int mem_space) {
   return mem_space == OFA_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 }
@@ -126,9 +130,23 @@ void destroy_graphs(ofa_plan* p) {
 int* done_ptr(ofa_plan* p) { return &p->st->done; }
 
 // One iteration of Algorithm 1 on stream s.
+// Separable grid form: the forward through the distinct x (G = E Fxu^T, then
+// Theta_k = Fyu[iy_k] . G[:, ix_k]) into the single partial row.
+void enqueue_sep_forward(ofa_plan* p, const float2* e32, cudaStream_t s) {
+  launch_sep_forward(e32, p->fxu, p->nx, p->ny, p->ux, p->gt, s);
+  launch_sep_theta(p->gt, p->fyu, p->ixy, p->K, p->ny, p->part, s);
+}
+
 void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
   const int* done = done_ptr(p);
-  if (!prec_is_tc(p->precision)) {
+  if (p->sep) {
+    enqueue_sep_forward(p, p->e32, s);
+    launch_focal(p->part, 1, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist, p->st,
+                 0, p->weighting, 1.f, p->amp_energy, s);
+    launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj, s);
+    launch_bwd_simt(p->ones, p->tconj, p->fyu, p->nx, p->ny, p->uy, p->amp, p->phi, p->e32, done,
+                    s);
+  } else if (!use_tc(p)) {
     launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, done, s);
     launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
                  p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
@@ -147,7 +165,11 @@ void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
 
 // Forward at the loop's current phase + statistics (mode 1) or output (mode 2).
 void enqueue_forward_current(ofa_plan* p, cudaStream_t s) {
-  if (!prec_is_tc(p->precision)) {
+  if (p->sep) {
+    enqueue_sep_forward(p, p->e32, s);
+    launch_focal(p->part, 1, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist, p->st,
+                 1, p->weighting, ldexpf(1.f, p->amp_exp), p->amp_energy, s);
+  } else if (!use_tc(p)) {
     launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, s);
     launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
                  p->c, p->hist, p->st, 1, p->weighting, ldexpf(1.f, p->amp_exp), p->amp_energy,
@@ -186,7 +208,7 @@ ofa_status sync_and_check(ofa_plan* p) {
 }
 
 ofa_status ensure_aux(ofa_plan* p) {
-  if (!prec_is_tc(p->precision) || p->aux_ready) return OFA_OK;
+  if (!use_tc(p) || p->aux_ready) return OFA_OK;
   TcOperands& a = p->tc_aux;
   a = p->tc;  // shares the static operands and their maps
   a.e_hi = a.e_lo = nullptr;
@@ -256,6 +278,7 @@ ofa_status ofa_options_default(ofa_options* o) {
   o->weighting = 1;
   o->autotune = 1;
   o->focus_z = nullptr;
+  o->separable = -1;
   return OFA_OK;
 }
 
@@ -309,11 +332,19 @@ ofa_status ofa_check_foci(int n_foci, const double* xy, double px, double py, do
 ofa_status ofa_plan_config(const ofa_plan* p, int* c) {
   if (!p || !c) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "NULL argument");
   for (int i = 0; i < 12; ++i) c[i] = 0;
-  if (!prec_is_tc(p->precision)) return OFA_OK;
+  if (!use_tc(p)) return OFA_OK;
   const TcOperands& t = p->tc;
   c[0] = t.fwd_bn; c[1] = t.fwd_split; c[2] = t.fwd_ccx; c[3] = t.fwd_ccy;
   c[4] = t.bwd_bn; c[5] = t.bwd_ccx; c[6] = t.bwd_ccy; c[7] = p->K <= 4096 ? 1 : 0;
   c[8] = t.fwd_rb; c[9] = t.bwd_rb; c[10] = t.fwd_cg; c[11] = t.bwd_cg;
+  return OFA_OK;
+}
+
+ofa_status ofa_plan_form(const ofa_plan* p, int* separable, int* ux, int* uy) {
+  if (!p) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "plan is NULL");
+  if (separable) *separable = p->sep ? 1 : 0;
+  if (ux) *ux = p->sep ? p->ux : 0;
+  if (uy) *uy = p->sep ? p->uy : 0;
   return OFA_OK;
 }
 
@@ -336,7 +367,8 @@ ofa_status ofa_destroy(ofa_plan* p) {
   void* bufs[] = {p->focus_xy, p->focus_z, p->t,     p->amp,   p->phi,   p->w,    p->fx,
                   p->fy,       p->fyT,   p->part,  p->theta, p->inten, p->c,
                   p->hist,     p->st,    p->scratch_phi, p->counters, p->e32, p->e32_aux,
-                  p->meas};
+                  p->meas,     p->fxu,   p->fyu,   p->gt,    p->tconj, p->ones, p->ixy,
+                  p->row_ptr,  p->row_foci};
   for (void* b : bufs) dfree(b);
   if (p->st_host) cudaFreeHost(p->st_host);
   free_tc(p->tc);
@@ -450,6 +482,31 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   p->nyp = round_up(ny, 128);
   p->kp = round_up(n_foci, 128);
 
+  // Separable grid form: with foci on the grid of their ux distinct x and uy distinct
+  // y coordinates, Eq. 2 factors through those values (Theta on the grid is
+  // Fyu E Fxu^T), costing nx ny (ux + uy) complex products instead of 2 nx ny K.
+  std::vector<double> xs, ys;
+  if (opt.separable != 0 && !opt.focus_z) {
+    for (int k = 0; k < n_foci; ++k) {
+      xs.push_back(xy[2 * k]);
+      ys.push_back(xy[2 * k + 1]);
+    }
+    std::sort(xs.begin(), xs.end());
+    xs.erase(std::unique(xs.begin(), xs.end()), xs.end());
+    std::sort(ys.begin(), ys.end());
+    ys.erase(std::unique(ys.begin(), ys.end()), ys.end());
+    const double c_sep = (double)nx * ny * ((double)xs.size() + (double)ys.size()) +
+                         (double)n_foci * (nx + ny);
+    const double c_gen = 2.0 * nx * ny * (double)n_foci;
+    p->sep = opt.separable == 1 || c_sep < 0.5 * c_gen;
+    p->ux = (int)xs.size();
+    p->uy = (int)ys.size();
+  }
+  if (opt.separable == 1 && !p->sep) {
+    delete p;
+    return ofa_fail(nullptr, OFA_ERR_UNSUPPORTED, "the separable form needs 2D foci");
+  }
+
   auto fail = [&](ofa_status s) {
     g_thread_error = p->last_error;
     g_fault_alloc_countdown = 0;
@@ -475,7 +532,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   OFA_TRY(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking),
           "creating capture stream");
 
-  const bool tc = prec_is_tc(p->precision);
+  const bool tc = use_tc(p);
   const int n_part_max = tc ? (p->nyp / 128) * 8 : simt_fwd_tiles(ny);
   OFA_TRY(dalloc(&p->focus_xy, 2 * (size_t)n_foci), "alloc");
   if (opt.focus_z) OFA_TRY(dalloc(&p->focus_z, (size_t)n_foci), "alloc");
@@ -492,6 +549,56 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   OFA_TRY(dalloc(&p->hist, OFA_HIST_CAP), "alloc");
   OFA_TRY(dalloc(&p->counters, p->kp / 64 + 1), "alloc");
   OFA_TRY(dalloc(&p->meas, n_foci), "alloc");
+  if (p->sep) {
+    OFA_TRY(dalloc(&p->fxu, (size_t)p->ux * nx), "alloc");
+    OFA_TRY(dalloc(&p->fyu, (size_t)p->uy * ny), "alloc");
+    OFA_TRY(dalloc(&p->gt, (size_t)p->ux * ny), "alloc");
+    OFA_TRY(dalloc(&p->tconj, (size_t)p->uy * nx), "alloc");
+    OFA_TRY(dalloc(&p->ones, (size_t)p->uy), "alloc");
+    OFA_TRY(dalloc(&p->ixy, (size_t)n_foci), "alloc");
+    OFA_TRY(dalloc(&p->row_ptr, (size_t)p->uy + 1), "alloc");
+    OFA_TRY(dalloc(&p->row_foci, (size_t)n_foci), "alloc");
+    std::vector<int2> ixy(n_foci);
+    std::vector<int> count(p->uy + 1, 0), order(n_foci);
+    for (int k = 0; k < n_foci; ++k) {
+      ixy[k].x = (int)(std::lower_bound(xs.begin(), xs.end(), xy[2 * k]) - xs.begin());
+      ixy[k].y = (int)(std::lower_bound(ys.begin(), ys.end(), xy[2 * k + 1]) - ys.begin());
+      count[ixy[k].y + 1]++;
+      order[k] = k;
+    }
+    for (int r = 0; r < p->uy; ++r) count[r + 1] += count[r];
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return ixy[a].y != ixy[b].y ? ixy[a].y < ixy[b].y : ixy[a].x < ixy[b].x;
+    });
+    std::vector<float2> ones(p->uy, make_float2(1.f, 0.f));
+    std::vector<double> ux2(2 * (size_t)p->ux, 0.0), uy2(2 * (size_t)p->uy, 0.0);
+    for (int i = 0; i < p->ux; ++i) ux2[2 * i] = xs[i];
+    for (int i = 0; i < p->uy; ++i) uy2[2 * i + 1] = ys[i];
+    double* dcoord = nullptr;
+    OFA_TRY(dalloc(&dcoord, ux2.size() + uy2.size()), "alloc");
+    cudaError_t ce = cudaMemcpy(dcoord, ux2.data(), ux2.size() * 8, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(dcoord + ux2.size(), uy2.data(), uy2.size() * 8, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(p->ixy, ixy.data(), ixy.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(p->row_ptr, count.data(), count.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(p->row_foci, order.data(), order.size() * sizeof(int),
+                      cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(p->ones, ones.data(), ones.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) {
+      const double lf = wavelength * focal_length;
+      launch_dft_rows(dcoord, nullptr, 0, p->ux, nx, pitch_x, lf, lf * focal_length, p->fxu,
+                      p->stream);
+      launch_dft_rows(dcoord + ux2.size(), nullptr, 1, p->uy, ny, pitch_y, lf, lf * focal_length,
+                      p->fyu, p->stream);
+      ce = cudaStreamSynchronize(p->stream);
+    }
+    dfree(dcoord);
+    OFA_TRY(ce, "separable grid set-up");
+  }
   OFA_TRY(dalloc(&p->st, 1), "alloc");
   OFA_TRY(cudaMallocHost(reinterpret_cast<void**>(&p->st_host), sizeof(OfaDevState)),
           "pinned alloc");
@@ -671,12 +778,17 @@ ofa_status ofa_iterate_measured(ofa_plan* p, const float* measured, int mem_spac
   if (e != cudaSuccess) return ofa_cuda_check(p, e, "copying measured intensities");
   launch_control(p->st, 0.0, 1, s);
   // forward (partials only), focal step on the captured intensities, inverse
-  const int n_part = prec_is_tc(p->precision) ? fwd_n_part(p->nyp, p->tc) : simt_fwd_tiles(p->ny);
-  if (prec_is_tc(p->precision)) launch_fwd_tc(p, p->tc, nullptr, s, false);
+  const int n_part = p->sep ? 1 : use_tc(p) ? fwd_n_part(p->nyp, p->tc) : simt_fwd_tiles(p->ny);
+  if (p->sep) enqueue_sep_forward(p, p->e32, s);
+  else if (use_tc(p)) launch_fwd_tc(p, p->tc, nullptr, s, false);
   else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, s);
   launch_focal_measured(p->part, n_part, p->kp, p->K, p->t, p->w, p->theta, p->c, p->hist, p->st,
                         p->weighting, p->meas, s);
-  if (prec_is_tc(p->precision)) {
+  if (p->sep) {
+    launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj, s);
+    launch_bwd_simt(p->ones, p->tconj, p->fyu, p->nx, p->ny, p->uy, p->amp, p->phi, p->e32,
+                    nullptr, s);
+  } else if (use_tc(p)) {
     launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
     launch_bwd_tc(p, p->tc, nullptr, s);
   } else {
@@ -767,7 +879,7 @@ ofa_status ofa_set_state(ofa_plan* p, const float* phi, const float* w, int j, i
   if (phi) e = cudaMemcpyAsync(p->phi, phi, (size_t)p->nx * p->ny * 4, kd, p->stream);
   if (e == cudaSuccess && w) e = cudaMemcpyAsync(p->w, w, (size_t)p->K * 4, kd, p->stream);
   if (e != cudaSuccess) return ofa_cuda_check(p, e, "copying state");
-  if (prec_is_tc(p->precision))
+  if (use_tc(p))
     launch_field_planes(p->phi, p->amp, p->nx, p->ny, p->nxp, p->precision, p->tc.e_hi,
                         p->tc.e_lo, p->stream);
   else
@@ -782,7 +894,12 @@ ofa_status ofa_forward(ofa_plan* p, const float* phi, float* theta, float* inten
   float2* th = theta ? reinterpret_cast<float2*>(theta) : p->theta;
   float* in = intensity ? intensity : p->inten;
   const float out_scale = ldexpf(1.f, p->amp_exp);
-  if (!prec_is_tc(p->precision)) {
+  if (p->sep) {
+    launch_field_f32(phi, p->amp, p->nx, p->ny, p->e32_aux, p->stream);
+    enqueue_sep_forward(p, p->e32_aux, p->stream);
+    launch_focal(p->part, 1, p->kp, p->K, p->t, p->w, th, in, p->c, p->hist, p->st, 2,
+                 p->weighting, out_scale, p->amp_energy, p->stream);
+  } else if (!use_tc(p)) {
     launch_field_f32(phi, p->amp, p->nx, p->ny, p->e32_aux, p->stream);
     launch_fwd_simt(p->e32_aux, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr,
                     p->stream);
@@ -808,7 +925,12 @@ ofa_status ofa_adjoint(ofa_plan* p, const float* phi, const float* theta,
   launch_grad_c(reinterpret_cast<const float2*>(theta), grad_intensity, p->K, p->kp, 1.f, p->c,
                 p->st, p->stream);
   const float amp_factor = ldexpf(1.f, p->amp_exp);
-  if (!prec_is_tc(p->precision)) {
+  if (p->sep) {
+    launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj,
+                 p->stream);
+    launch_grad_simt(p->ones, p->tconj, p->fyu, p->nx, p->ny, p->uy, phi, p->amp, amp_factor,
+                     p->st, grad_phi, p->stream);
+  } else if (!use_tc(p)) {
     launch_grad_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, phi, p->amp, amp_factor, p->st,
                      grad_phi, p->stream);
   } else {
@@ -822,7 +944,7 @@ ofa_status ofa_adjoint(ofa_plan* p, const float* phi, const float* theta,
 ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   if (!p || reps < 1 || !ms_out) return ofa_fail(p, OFA_ERR_INVALID_ARG, "bad argument");
   cudaSetDevice(p->device);
-  const bool tc = prec_is_tc(p->precision);
+  const bool tc = use_tc(p);
   const size_t npix = (size_t)p->nx * p->ny;
   // Save the loop state (the focal kernel updates w, j and the history; the
   // inverse rewrites phi and the field planes).
@@ -855,11 +977,12 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   if (e_s[1]) cudaMemcpyAsync(e_s[1], p->tc.e_lo, e_bytes, cudaMemcpyDeviceToDevice, s);
   launch_control(p->st, 0.0, 1, s);
 
-  const int n_part = tc ? fwd_n_part(p->nyp, p->tc) : simt_fwd_tiles(p->ny);
+  const int n_part = p->sep ? 1 : tc ? fwd_n_part(p->nyp, p->tc) : simt_fwd_tiles(p->ny);
   auto run = [&](int which) {
     switch (which) {
       case 0:
-        if (tc) launch_fwd_tc(p, p->tc, nullptr, s, p->K <= 4096);  // + fused focal step
+        if (p->sep) enqueue_sep_forward(p, p->e32, s);
+        else if (tc) launch_fwd_tc(p, p->tc, nullptr, s, p->K <= 4096);  // + fused focal step
         else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr,
                              s);
         break;
@@ -870,11 +993,15 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
                      p->st, 0, p->weighting, 1.f, p->amp_energy, s);
         break;
       case 2:
-        if (tc) launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi,
-                               p->tc.p_lo, s);
+        if (p->sep) launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx,
+                                 p->tconj, s);
+        else if (tc) launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision,
+                                    p->tc.p_hi, p->tc.p_lo, s);
         break;
       default:
-        if (tc) launch_bwd_tc(p, p->tc, nullptr, s);
+        if (p->sep) launch_bwd_simt(p->ones, p->tconj, p->fyu, p->nx, p->ny, p->uy, p->amp,
+                                    p->phi, p->e32, nullptr, s);
+        else if (tc) launch_bwd_tc(p, p->tc, nullptr, s);
         else launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
                              nullptr, s);
         break;
@@ -884,7 +1011,7 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
   for (int which = 0; which < 4; ++which) {
-    if ((which == 2 && !tc) || (which == 1 && tc && p->K <= 4096)) {
+    if ((which == 2 && !tc && !p->sep) || (which == 1 && tc && p->K <= 4096)) {
       ms_out[which] = 0.0;
       continue;
     }
@@ -946,7 +1073,7 @@ ofa_status ofa_batch_create(ofa_batch** out, ofa_plan* const* plans, int count, 
   // and its focal step fits the forward kernel's last CTA; otherwise plan after plan.
   bool grouped = true;
   for (ofa_plan* p : b->plans)
-    grouped = grouped && prec_is_tc(p->precision) && p->precision == plans[0]->precision &&
+    grouped = grouped && use_tc(p) && p->precision == plans[0]->precision &&
               p->K <= 4096;
   if (grouped) {
     if (cudaDeviceSynchronize() != cudaSuccess) {

@@ -90,6 +90,17 @@ struct ofa_plan {
   float2* e32 = nullptr;               // FP32 form: pupil field A exp(i phi) [ny][nx]
   float2* e32_aux = nullptr;           // FP32 form: field of an external phase
   float* meas = nullptr;               // [K] captured intensities (camera in the loop)
+  // separable grid form (sep): products through the ux distinct x and uy distinct y
+  bool sep = false;
+  int ux = 0, uy = 0;
+  float2* fxu = nullptr;               // [ux][nx] DFT rows of the distinct x
+  float2* fyu = nullptr;               // [uy][ny] DFT rows of the distinct y
+  float2* gt = nullptr;                // [ux][ny] first forward product, transposed
+  float2* tconj = nullptr;             // [uy][nx] first inverse product, conjugated
+  float2* ones = nullptr;              // [uy] unit weights of the second inverse product
+  int2* ixy = nullptr;                 // [K] (ix, iy) of each focus
+  int* row_ptr = nullptr;              // [uy + 1] foci of each grid row ...
+  int* row_foci = nullptr;             // [K] ... in increasing ix order
   TcOperands tc;
   TcOperands tc_aux;                   // E planes of an external phase (forward/adjoint)
   bool aux_ready = false;
@@ -129,6 +140,15 @@ void launch_fwd_simt(const float2* e32, const float2* fx, const float2* fy, int 
 int simt_fwd_tiles(int ny);
 void launch_bwd_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,
                      const float* amp, float* phi, float2* e32, const int* done, cudaStream_t s);
+// Separable grid form (foci on a grid of ux distinct x and uy distinct y values):
+// gt[ix][n] = sum_m E[n][m] Fxu[ix][m]; Theta_k = sum_n Fyu[iy_k][n] gt[ix_k][n];
+// tconj[iy][m] = conj(sum_{k in row iy} c_k conj(Fxu[ix_k][m])).
+void launch_sep_forward(const float2* e32, const float2* fxu, int nx, int ny, int ux,
+                        float2* gt, cudaStream_t s);
+void launch_sep_theta(const float2* gt, const float2* fyu, const int2* ixy, int K, int ny,
+                      float2* part, cudaStream_t s);
+void launch_sep_t(const float2* c, const float2* fxu, const int2* ixy, const int* row_ptr,
+                  const int* row_foci, int uy, int nx, float2* tconj, cudaStream_t s);
 void launch_grad_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,
                       const float* phi, const float* amp, float amp_factor,
                       const OfaDevState* st, float* grad, cudaStream_t s);

@@ -210,6 +210,29 @@ def volume_workload(n: int = 512, cols: int = 7, rows: int = 7, layers: int = 3,
     return w
 
 
+def table1_workload(cols: int = 9, rows: int = 9, n_iter: int = 40, seed: int = 7,
+                    uniform_targets: bool = False, name: str | None = None) -> Workload:
+    """Table 1 geometry: 1000 x 1000 SLM pixels at 12.5 um, 785 nm, f = 250 mm, a regular
+    cols x rows grid with the 20-camera-pixel gap (3.45 um pixels) of the Fig. 2
+    discussion; targets U[0.5, 1] (the paper's 'various intensities') or 1."""
+    rng = np.random.default_rng(seed)
+    n, pitch, lam, f = 1000, 12.5e-6, 785e-9, 0.25
+    gap = 20 * 3.45e-6
+    gx = (np.arange(cols) - (cols - 1) / 2.0) * gap
+    gy = (np.arange(rows) - (rows - 1) / 2.0) * gap
+    xx, yy = np.meshgrid(gx, gy)
+    foci = np.stack([xx.ravel(), yy.ravel()], 1)
+    k = foci.shape[0]
+    t = np.ones(k) if uniform_targets else rng.uniform(0.5, 1.0, k)
+    return Workload(name=name or f"table1_grid{cols}x{rows}", nx=n, ny=n, pitch_x=pitch,
+                    pitch_y=pitch, wavelength=lam, focal_length=f,
+                    focus_xy=np.ascontiguousarray(foci, dtype=np.float64),
+                    target=np.ascontiguousarray(t, dtype=np.float32),
+                    amplitude=gaussian_amplitude(n, n, pitch, pitch),
+                    phi0=uniform_phase(rng, n, n), n_iter=n_iter,
+                    meta={"layout": "regular grid", "gap_m": gap, "seed": seed})
+
+
 def batch_workloads(count: int = 256, sizes=(512, 768, 1024), k_min: int = 16, k_max: int = 4096,
                     n_iter: int = 50, seed: int = 5) -> list[Workload]:
     """Uneven batch: N drawn from sizes, K log-uniform in [k_min, k_max], jittered grid foci."""
@@ -236,6 +259,9 @@ NAMED = {
                                                      name="pupil1920x1152_grid2500"),
     "pupil512_volume147": lambda: volume_workload(512, 7, 7, 3, z_span=0.1, n_iter=50, seed=6,
                                                   name="pupil512_volume147"),
+    "table1_grid9x9": lambda: table1_workload(9, 9, n_iter=40, seed=7, name="table1_grid9x9"),
+    "table1_grid45x47": lambda: table1_workload(45, 47, n_iter=40, seed=8,
+                                                name="table1_grid45x47"),
     "pupil1024_grid400_adam": lambda: grid_workload(1024, 20, 20, n_iter=200, seed=4,
                                                     uniform_targets=False,
                                                     name="pupil1024_grid400_adam"),

@@ -43,7 +43,7 @@ class ofa_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("seed", C.c_uint64), ("cuda_stream", C.c_void_p),
                 ("amplitude", C.c_void_p), ("waist_frac", C.c_double), ("phi0", C.c_void_p),
                 ("mem_space", C.c_int), ("weighting", C.c_int), ("autotune", C.c_int),
-                ("focus_z", C.c_void_p)]
+                ("focus_z", C.c_void_p), ("separable", C.c_int)]
 
 
 class ofa_stats(C.Structure):
@@ -77,6 +77,7 @@ SIGNATURES = [
     ("ofa_batch_info", _I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     ("ofa_selftest_bounded_wait", _I, []),
     ("ofa_iterate_measured", _I, [_P, _P, _I, C.POINTER(_D)]),
+    ("ofa_plan_form", _I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     ("ofa_forward_noalloc", _I, [_I, _I, _D, _D, _D, _D, _I, _P, _P, _P, _P, _P, _P]),
     ("ofa_fft_equivalent_size", _I, [_I, _D, _D, _D, _D, C.POINTER(_I)]),
     ("ofa_max_foci_per_axis", _I, [_D, _D, _D, _D, C.POINTER(_I)]),
@@ -227,6 +228,12 @@ def ofa_plan_config(plan) -> dict:
     return dict(zip(keys, (int(x) for x in c)))
 
 
+def ofa_plan_form(plan) -> dict:
+    a, b, c = C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(_lib.ofa_plan_form(plan, C.byref(a), C.byref(b), C.byref(c)), plan)
+    return {"separable": bool(a.value), "ux": b.value, "uy": c.value}
+
+
 def ofa_plan_info(plan):
     a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     _check(_lib.ofa_plan_info(plan, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), plan)
@@ -300,13 +307,14 @@ class Plan:
     def __init__(self, nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy, target,
                  precision="f16x3", amplitude=None, phi0=None, seed=0, weighting=True,
                  stream=None, waist_frac=0.4, mem_space=OFA_MEM_HOST, autotune=True,
-                 focus_z=None):
+                 focus_z=None, separable=-1):
         opt = ofa_options_default()
         opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opt.seed = int(seed)
         opt.cuda_stream = stream
         opt.weighting = 1 if weighting else 0
         opt.autotune = 1 if autotune else 0
+        opt.separable = int(separable)
         opt.waist_frac = float(waist_frac)
         opt.mem_space = int(mem_space)
         if mem_space == OFA_MEM_HOST:

@@ -43,6 +43,7 @@ def test_options_default(ofa):
     assert o.waist_frac == 0.4
     assert o.weighting == 1
     assert o.autotune == 1
+    assert o.separable == -1 and not o.focus_z
     assert not o.amplitude and not o.phi0 and not o.cuda_stream
 
 

@@ -509,3 +509,76 @@ def test_camera_in_the_loop_corrects_a_systematic_gain(ofa, dev):
     plan.close()
     assert xi_before < 0.95, xi_before
     assert xi_after > 0.99 and xi_after > xi_before + 0.03, (xi_before, xi_after, xis)
+
+
+def test_separable_form_table1_9x9_matches_oracle(ofa, dev):
+    """The paper's Table 1 replay: 9 x 9 grid, 1000^2 pupil.  The plan factors through
+    the 9 distinct x and y; its xi history follows the FP64 oracle's general loop and
+    reaches 0.99 (the paper: iteration 16, here within 40)."""
+    w = I.named("table1_grid9x9")
+    fx, fy = oracle_mats(w)
+    ref = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, w.n_iter)
+    plan = ofa.Plan.from_workload(w, precision="f16x3")
+    form = ofa.ofa_plan_form(plan.handle)
+    it, xi = plan.iterate(w.n_iter, want_stats=True)
+    st = plan.stats()
+    hist = plan.xi_history()
+    plan.close()
+    assert form == {"separable": True, "ux": 9, "uy": 9}
+    # FP32 rounding is amplified while xi climbs steeply (iterations 3-6 here): the
+    # first iterations agree to 1e-6, the whole history to 2e-3, the end to 1e-3
+    assert np.max(np.abs(hist[:3] - ref["xi_hist"][:3])) < 1e-6
+    assert np.max(np.abs(hist - ref["xi_hist"])) < 2e-3
+    assert abs(xi - ref["xi"]) < 1e-3 and abs(st.uniformity - ref["uniformity"]) < 1e-3
+    assert hist.max() >= 0.99 and int(np.argmax(hist >= 0.99)) < 40
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "fp32"])
+def test_separable_equals_general_form(ofa, dev, prec):
+    w = I.named("table1_grid9x9")
+    hs = []
+    for sep in (1, 0):
+        plan = ofa.Plan.from_workload(w, precision=prec, separable=sep)
+        assert ofa.ofa_plan_form(plan.handle)["separable"] == bool(sep)
+        plan.iterate(12)
+        hs.append(plan.xi_history())
+        plan.close()
+    # same operator, different rounding (FP32 grid products vs the general form),
+    # amplified while xi climbs steeply (iterations 3-6)
+    assert np.max(np.abs(hs[0][:3] - hs[1][:3])) < 1e-5, hs
+    assert np.max(np.abs(hs[0] - hs[1])) < 5e-3, hs
+
+
+def test_separable_45x47_forward_and_gradient(ofa, dev):
+    """2115 foci on a 45 x 47 grid: amplitudes of the separable forward and the
+    adjoint gradient against the oracle's general operator."""
+    w = I.named("table1_grid45x47")
+    fx, fy = oracle_mats(w)
+    A = w.amplitude.astype(np.float64)
+    phi = w.phi0.astype(np.float64)
+    theta = O.forward(O.pupil_field(A, phi), fx, fy)
+    plan = ofa.Plan.from_workload(w, precision="f16x3",
+                                  stream=torch.cuda.current_stream().cuda_stream)
+    assert ofa.ofa_plan_form(plan.handle) == {"separable": True, "ux": 45, "uy": 47}
+    phi_d = torch.from_numpy(w.phi0).cuda()
+    th = torch.zeros(w.n_foci, 2, device="cuda")
+    ofa.ofa_forward(plan.handle, phi_d, th, None)
+    torch.cuda.synchronize()
+    g = th.cpu().numpy().astype(np.float64)
+    err, _ = amp_err(g[:, 0] + 1j * g[:, 1], theta)
+    assert err < 1e-5, err
+    gI = O.intensity_loss_grad_I(w.target, np.abs(theta) ** 2)
+    ref = O.phase_gradient(A, phi, fx, fy, gI)
+    grad = torch.zeros(w.ny, w.nx, device="cuda")
+    ofa.ofa_adjoint(plan.handle, phi_d, th, torch.from_numpy(gI.astype(np.float32)).cuda(), grad)
+    torch.cuda.synchronize()
+    plan.close()
+    rel = np.linalg.norm(grad.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert rel < 1e-4, rel
+
+
+def test_separable_refused_for_3d(ofa, dev):
+    w = I.named("table1_grid9x9")
+    with pytest.raises(ofa.OfaError) as e:
+        ofa.Plan.from_workload(w, separable=1, focus_z=np.zeros(w.n_foci))
+    assert e.value.status == ofa.OFA_ERR_UNSUPPORTED
