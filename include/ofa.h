@@ -95,9 +95,9 @@ typedef struct ofa_options {
                                 the distinct coordinates) and the inverse factors the same
                                 way, nx ny (U_x + U_y) complex products per iteration instead
                                 of 2 nx ny K; these run in FP32 on the CUDA cores whatever
-                                the precision.  -1 = when that is at most half the cost
-                                (default), 0 = never, 1 = always (OFA_ERR_UNSUPPORTED with
-                                focus_z) */
+                                the precision.  -1 = when the work shrinks by more than
+                                20x for the tensor-core forms, 2x for FP32 (default),
+                                0 = never, 1 = always (OFA_ERR_UNSUPPORTED with focus_z) */
 } ofa_options;
 
 typedef struct ofa_stats {

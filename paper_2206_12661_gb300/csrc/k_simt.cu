@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(256) fwd_simt_kernel(
   }
 
   if (STORE) {
+    float2* g = part + (size_t)blockIdx.z * K * ny;   // slice of this contraction part
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int k = k0 + tx * 4 + j;
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(256) fwd_simt_kernel(
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int n = n0 + ty * 4 + i;
-        if (n < ny) part[(size_t)k * ny + n] = acc[i][j];
+        if (n < ny) g[(size_t)k * ny + n] = acc[i][j];
       }
     }
     return;
@@ -263,43 +264,79 @@ __global__ void __launch_bounds__(256) bwd_simt_kernel(
 
 // Separable grid form, focal step of the forward: Theta_k = sum_n Fyu[iy_k][n] G[n][ix_k]
 // (one warp per focus, fixed-order shuffle tree), written as the single partial row.
-__global__ void sep_theta_kernel(const float2* __restrict__ gt, const float2* __restrict__ fyu,
-                                 const int2* __restrict__ ixy, int K, int ny,
-                                 float2* __restrict__ part) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= K) return;
-  const int2 q = ixy[warp];
+// The first product's contraction slices [parts][ux][ny] summed in order into slice 0.
+__global__ void sep_reduce_kernel(float2* __restrict__ gt, size_t slice, int parts) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < slice;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float2 a = gt[i];
+    for (int z = 1; z < parts; ++z) {
+      const float2 v = gt[z * slice + i];
+      a.x += v.x;
+      a.y += v.y;
+    }
+    gt[i] = a;
+  }
+}
+
+// One 256-thread block per focus; fixed-order shuffle and shared-memory tree.
+__global__ void __launch_bounds__(256) sep_theta_kernel(const float2* __restrict__ gt,
+                                                        const float2* __restrict__ fyu,
+                                                        const int2* __restrict__ ixy, int ny,
+                                                        float2* __restrict__ part) {
+  __shared__ float2 red[8];
+  const int k = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int2 q = ixy[k];
   const float2* g = gt + (size_t)q.x * ny;
   const float2* f = fyu + (size_t)q.y * ny;
   float2 a = make_float2(0.f, 0.f);
-  for (int n = lane; n < ny; n += 32) cmac(a, f[n], g[n]);
+  for (int n = threadIdx.x; n < ny; n += 256) cmac(a, f[n], g[n]);
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
     a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
   }
-  if (lane == 0) part[warp] = a;
+  if (lane == 0) red[warp] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float2 t = red[0];
+    for (int w = 1; w < 8; ++w) {
+      t.x += red[w].x;
+      t.y += red[w].y;
+    }
+    part[k] = t;
+  }
 }
 
 // Separable grid form, first product of the inverse: for row iy of the grid,
 // T[iy][m] = sum over the foci of that row (in fixed order) of c_k conj(Fxu[ix_k][m]);
-// stored conjugated, as the inverse product conjugates its right operand.
-__global__ void sep_t_kernel(const float2* __restrict__ c, const float2* __restrict__ fxu,
-                             const int2* __restrict__ ixy, const int* __restrict__ row_ptr,
-                             const int* __restrict__ row_foci, int uy, int nx,
-                             float2* __restrict__ tconj) {
-  const size_t total = (size_t)uy * nx;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const int iy = (int)(i / nx), m = (int)(i % nx);
-    float2 a = make_float2(0.f, 0.f);
-    for (int r = row_ptr[iy]; r < row_ptr[iy + 1]; ++r) {
-      const int k = row_foci[r];
-      const float2 f = fxu[(size_t)ixy[k].x * nx + m];
-      cmac(a, c[k], make_float2(f.x, -f.y));
+// stored conjugated, as the inverse product conjugates its right operand.  Block
+// (column chunk, iy); the row's (c_k, ix_k) are staged in shared memory.
+constexpr int SEP_T_ROW = 256;   // foci of a row staged per pass
+__global__ void __launch_bounds__(256) sep_t_kernel(
+    const float2* __restrict__ c, const float2* __restrict__ fxu, const int2* __restrict__ ixy,
+    const int* __restrict__ row_ptr, const int* __restrict__ row_foci, int nx,
+    float2* __restrict__ tconj) {
+  __shared__ float2 cs[SEP_T_ROW];
+  __shared__ int xs[SEP_T_ROW];
+  const int iy = blockIdx.y, m = blockIdx.x * 256 + threadIdx.x;
+  const int r0 = row_ptr[iy], r1 = row_ptr[iy + 1];
+  float2 a = make_float2(0.f, 0.f);
+  for (int rb = r0; rb < r1; rb += SEP_T_ROW) {
+    const int nr = min(SEP_T_ROW, r1 - rb);
+    __syncthreads();
+    if ((int)threadIdx.x < nr) {
+      const int k = row_foci[rb + threadIdx.x];
+      cs[threadIdx.x] = c[k];
+      xs[threadIdx.x] = ixy[k].x;
     }
-    tconj[i] = make_float2(a.x, -a.y);
+    __syncthreads();
+    if (m < nx)
+      for (int r = 0; r < nr; ++r) {
+        const float2 f = fxu[(size_t)xs[r] * nx + m];
+        cmac(a, cs[r], make_float2(f.x, -f.y));
+      }
   }
+  if (m < nx) tconj[(size_t)iy * nx + m] = make_float2(a.x, -a.y);
 }
 
 }  // namespace
@@ -322,23 +359,36 @@ void launch_fwd_simt(const float2* e32, const float2* fx, const float2* fy, int 
   fwd_simt_kernel<false><<<grid, 256, 0, s>>>(e32, fx, fy, nx, ny, K, kp, part, done);
 }
 
-void launch_sep_forward(const float2* e32, const float2* fxu, int nx, int ny, int ux,
+int sep_parts(int nx, int ny, int ux, int sms) {
+  const int tiles = ((ux + T64 - 1) / T64) * ((ny + T64 - 1) / T64);
+  const int steps = (nx + TS - 1) / TS;
+  int parts = (2 * sms + tiles - 1) / tiles;   // about two blocks per SM
+  if (parts > steps) parts = steps;
+  if (parts > 32) parts = 32;
+  return parts < 1 ? 1 : parts;
+}
+
+void launch_sep_forward(const float2* e32, const float2* fxu, int nx, int ny, int ux, int parts,
                         float2* gt, cudaStream_t s) {
-  dim3 grid((ux + T64 - 1) / T64, (ny + T64 - 1) / T64, 1);
+  dim3 grid((ux + T64 - 1) / T64, (ny + T64 - 1) / T64, parts);
   fwd_simt_kernel<true><<<grid, 256, 0, s>>>(e32, fxu, nullptr, nx, ny, ux, ux, gt, nullptr);
 }
 
-void launch_sep_theta(const float2* gt, const float2* fyu, const int2* ixy, int K, int ny,
-                      float2* part, cudaStream_t s) {
-  sep_theta_kernel<<<(K + 7) / 8, 256, 0, s>>>(gt, fyu, ixy, K, ny, part);
+void launch_sep_theta(float2* gt, const float2* fyu, const int2* ixy, int K, int ny, int ux,
+                      int parts, float2* part, cudaStream_t s) {
+  if (parts > 1) {
+    const size_t slice = (size_t)ux * ny;
+    size_t blocks = (slice + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    sep_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(gt, slice, parts);
+  }
+  sep_theta_kernel<<<K, 256, 0, s>>>(gt, fyu, ixy, ny, part);
 }
 
 void launch_sep_t(const float2* c, const float2* fxu, const int2* ixy, const int* row_ptr,
                   const int* row_foci, int uy, int nx, float2* tconj, cudaStream_t s) {
-  const size_t total = (size_t)uy * nx;
-  size_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  sep_t_kernel<<<(unsigned)blocks, 256, 0, s>>>(c, fxu, ixy, row_ptr, row_foci, uy, nx, tconj);
+  dim3 grid((nx + 255) / 256, uy);
+  sep_t_kernel<<<grid, 256, 0, s>>>(c, fxu, ixy, row_ptr, row_foci, nx, tconj);
 }
 
 void launch_bwd_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,

@@ -92,7 +92,7 @@ struct ofa_plan {
   float* meas = nullptr;               // [K] captured intensities (camera in the loop)
   // separable grid form (sep): products through the ux distinct x and uy distinct y
   bool sep = false;
-  int ux = 0, uy = 0;
+  int ux = 0, uy = 0, sep_parts = 1;
   float2* fxu = nullptr;               // [ux][nx] DFT rows of the distinct x
   float2* fyu = nullptr;               // [uy][ny] DFT rows of the distinct y
   float2* gt = nullptr;                // [ux][ny] first forward product, transposed
@@ -143,10 +143,13 @@ void launch_bwd_simt(const float2* c, const float2* fx, const float2* fy, int nx
 // Separable grid form (foci on a grid of ux distinct x and uy distinct y values):
 // gt[ix][n] = sum_m E[n][m] Fxu[ix][m]; Theta_k = sum_n Fyu[iy_k][n] gt[ix_k][n];
 // tconj[iy][m] = conj(sum_{k in row iy} c_k conj(Fxu[ix_k][m])).
-void launch_sep_forward(const float2* e32, const float2* fxu, int nx, int ny, int ux,
+// The first forward product is split over `parts` contraction slices (enough blocks
+// to fill the SMs when ux is small); gt holds [parts][ux][ny].
+int sep_parts(int nx, int ny, int ux, int sms);
+void launch_sep_forward(const float2* e32, const float2* fxu, int nx, int ny, int ux, int parts,
                         float2* gt, cudaStream_t s);
-void launch_sep_theta(const float2* gt, const float2* fyu, const int2* ixy, int K, int ny,
-                      float2* part, cudaStream_t s);
+void launch_sep_theta(float2* gt, const float2* fyu, const int2* ixy, int K, int ny, int ux,
+                      int parts, float2* part, cudaStream_t s);
 void launch_sep_t(const float2* c, const float2* fxu, const int2* ixy, const int* row_ptr,
                   const int* row_foci, int uy, int nx, float2* tconj, cudaStream_t s);
 void launch_grad_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,

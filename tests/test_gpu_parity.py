@@ -518,7 +518,7 @@ def test_separable_form_table1_9x9_matches_oracle(ofa, dev):
     w = I.named("table1_grid9x9")
     fx, fy = oracle_mats(w)
     ref = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, w.n_iter)
-    plan = ofa.Plan.from_workload(w, precision="f16x3")
+    plan = ofa.Plan.from_workload(w, precision="f16x3", separable=1)
     form = ofa.ofa_plan_form(plan.handle)
     it, xi = plan.iterate(w.n_iter, want_stats=True)
     st = plan.stats()
@@ -526,8 +526,8 @@ def test_separable_form_table1_9x9_matches_oracle(ofa, dev):
     plan.close()
     assert form == {"separable": True, "ux": 9, "uy": 9}
     # FP32 rounding is amplified while xi climbs steeply (iterations 3-6 here): the
-    # first iterations agree to 1e-6, the whole history to 2e-3, the end to 1e-3
-    assert np.max(np.abs(hist[:3] - ref["xi_hist"][:3])) < 1e-6
+    # first iterations agree to 1e-5, the whole history to 2e-3, the end to 1e-3
+    assert np.max(np.abs(hist[:3] - ref["xi_hist"][:3])) < 1e-5
     assert np.max(np.abs(hist - ref["xi_hist"])) < 2e-3
     assert abs(xi - ref["xi"]) < 1e-3 and abs(st.uniformity - ref["uniformity"]) < 1e-3
     assert hist.max() >= 0.99 and int(np.argmax(hist >= 0.99)) < 40
@@ -559,6 +559,7 @@ def test_separable_45x47_forward_and_gradient(ofa, dev):
     theta = O.forward(O.pupil_field(A, phi), fx, fy)
     plan = ofa.Plan.from_workload(w, precision="f16x3",
                                   stream=torch.cuda.current_stream().cuda_stream)
+    # auto: the 45 x 47 grid needs 0.04 of the general form's work
     assert ofa.ofa_plan_form(plan.handle) == {"separable": True, "ux": 45, "uy": 47}
     phi_d = torch.from_numpy(w.phi0).cuda()
     th = torch.zeros(w.n_foci, 2, device="cuda")
