@@ -837,7 +837,7 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
 // Many problems in one launch: block b computes tile tiles[b] = (problem, m_tile,
 // n_tile) of problem items[problem], whose tensor maps and epilogue arguments sit
 // in device memory (written once before the first launch and never modified).
-struct alignas(64) GroupItem {
+struct GroupItem {  // aligned as its tensor maps are
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
   EpiArgs ep;
   int kb_total;

@@ -33,14 +33,48 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 // ofa_plan_create call fails as if the device were out of memory.
 thread_local int g_fault_alloc_countdown = 0;
 
+// While a plan is being created its buffers are only reserved (slot, bytes) and
+// then carved out of one zero-filled device allocation (arena_commit): one
+// cudaMalloc and one memset instead of one pair per buffer.
+struct ArenaReq {
+  void** slot;
+  size_t bytes;
+};
+thread_local std::vector<ArenaReq>* g_arena = nullptr;
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
   if (g_fault_alloc_countdown > 0 && --g_fault_alloc_countdown == 0)
     return cudaErrorMemoryAllocation;
+  if (g_arena) {
+    g_arena->push_back({reinterpret_cast<void**>(p), count * sizeof(T)});
+    return cudaSuccess;
+  }
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
   if (e == cudaSuccess) e = cudaMemset(*p, 0, count * sizeof(T));
+  return e;
+}
+
+cudaError_t arena_commit(ofa_plan* p, const std::vector<ArenaReq>& reqs) {
+  std::vector<size_t> off(reqs.size());
+  size_t total = 0;
+  for (size_t i = 0; i < reqs.size(); ++i) {
+    total = (total + 255) & ~(size_t)255;
+    off[i] = total;
+    total += reqs[i].bytes;
+  }
+  void* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, total ? total : 256);
+  if (e != cudaSuccess) return e;
+  p->arena = base;
+  for (size_t i = 0; i < reqs.size(); ++i) {
+    *reqs[i].slot = static_cast<uint8_t*>(base) + off[i];
+    p->arena_slots.push_back(reqs[i].slot);
+  }
+  e = cudaMemsetAsync(base, 0, total, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   return e;
 }
 
@@ -106,11 +140,10 @@ ofa_status alloc_tc(ofa_plan* p, TcOperands& t, bool with_static) {
   const size_t e_n = (size_t)p->nyp * 2 * p->nxp;
   const size_t bx_n = (size_t)2 * p->kp * 2 * p->nxp;
   const size_t pp_n = (size_t)p->nyp * 2 * p->kp;
+  // reserve or allocate straight into the operand's own slot (an arena commit
+  // writes the final address there later)
   auto A = [&](void** ptr, size_t n) -> bool {
-    uint8_t* q = nullptr;
-    if (dalloc(&q, n * eb) != cudaSuccess) return false;
-    *ptr = q;
-    return true;
+    return dalloc(reinterpret_cast<uint8_t**>(ptr), n * eb) == cudaSuccess;
   };
   bool ok = A(&t.e_hi, e_n) && (t.npass == 1 || A(&t.e_lo, e_n));
   if (with_static) {
@@ -364,6 +397,11 @@ ofa_status ofa_destroy(ofa_plan* p) {
   cudaSetDevice(p->device);
   if (p->stream || p->own_stream) cudaStreamSynchronize(p->stream);
   destroy_graphs(p);
+  if (p->arena) {
+    cudaFree(p->arena);
+    for (void** slot : p->arena_slots) *slot = nullptr;
+    p->arena = nullptr;
+  }
   void* bufs[] = {p->focus_xy, p->focus_z, p->t,     p->amp,   p->phi,   p->w,    p->fx,
                   p->fy,       p->fyT,   p->part,  p->theta, p->inten, p->c,
                   p->hist,     p->st,    p->scratch_phi, p->counters, p->e32, p->e32_aux,
@@ -514,6 +552,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   auto fail = [&](ofa_status s) {
     g_thread_error = p->last_error;
     g_fault_alloc_countdown = 0;
+    g_arena = nullptr;
     ofa_destroy(p);
     return s;
   };
@@ -538,31 +577,58 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
 
   const bool tc = use_tc(p);
   const int n_part_max = tc ? (p->nyp / 128) * 8 : simt_fwd_tiles(ny);
-  OFA_TRY(dalloc(&p->focus_xy, 2 * (size_t)n_foci), "alloc");
-  if (opt.focus_z) OFA_TRY(dalloc(&p->focus_z, (size_t)n_foci), "alloc");
-  OFA_TRY(dalloc(&p->t, n_foci), "alloc");
-  OFA_TRY(dalloc(&p->amp, npix), "alloc");
-  OFA_TRY(dalloc(&p->phi, npix), "alloc");
-  OFA_TRY(dalloc(&p->w, n_foci), "alloc");
-  OFA_TRY(dalloc(&p->fx, (size_t)n_foci * nx), "alloc");
-  OFA_TRY(dalloc(&p->fy, (size_t)n_foci * ny), "alloc");
-  OFA_TRY(dalloc(&p->part, (size_t)n_part_max * p->kp), "alloc");
-  OFA_TRY(dalloc(&p->theta, n_foci), "alloc");
-  OFA_TRY(dalloc(&p->inten, n_foci), "alloc");
-  OFA_TRY(dalloc(&p->c, p->kp), "alloc");
-  OFA_TRY(dalloc(&p->hist, OFA_HIST_CAP), "alloc");
-  OFA_TRY(dalloc(&p->counters, p->kp / 64 + 1), "alloc");
-  OFA_TRY(dalloc(&p->meas, n_foci), "alloc");
+  // Reserve every device buffer, then carve them out of one allocation.
+  std::vector<ArenaReq> reqs;
+  g_arena = &reqs;
+  auto reserve_all = [&]() -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    auto R = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    R(dalloc(&p->focus_xy, 2 * (size_t)n_foci));
+    if (opt.focus_z) R(dalloc(&p->focus_z, (size_t)n_foci));
+    R(dalloc(&p->t, n_foci));
+    R(dalloc(&p->amp, npix));
+    R(dalloc(&p->phi, npix));
+    R(dalloc(&p->w, n_foci));
+    R(dalloc(&p->fx, (size_t)n_foci * nx));
+    R(dalloc(&p->fy, (size_t)n_foci * ny));
+    R(dalloc(&p->part, (size_t)n_part_max * p->kp));
+    R(dalloc(&p->theta, n_foci));
+    R(dalloc(&p->inten, n_foci));
+    R(dalloc(&p->c, p->kp));
+    R(dalloc(&p->hist, OFA_HIST_CAP));
+    R(dalloc(&p->counters, p->kp / 64 + 1));
+    R(dalloc(&p->meas, n_foci));
+    if (p->sep) {
+      R(dalloc(&p->fxu, (size_t)p->ux * nx));
+      R(dalloc(&p->fyu, (size_t)p->uy * ny));
+      p->sep_parts = sep_parts(nx, ny, p->ux, prop.multiProcessorCount);
+      R(dalloc(&p->gt, (size_t)p->sep_parts * p->ux * ny));
+      R(dalloc(&p->tconj, (size_t)p->uy * nx));
+      R(dalloc(&p->ones, (size_t)p->uy));
+      R(dalloc(&p->ixy, (size_t)n_foci));
+      R(dalloc(&p->row_ptr, (size_t)p->uy + 1));
+      R(dalloc(&p->row_foci, (size_t)n_foci));
+      R(dalloc(&p->sep_coord, 2 * ((size_t)p->ux + p->uy)));
+    }
+    R(dalloc(&p->st, 1));
+    if (!tc) {
+      R(dalloc(&p->e32, npix));
+      R(dalloc(&p->e32_aux, npix));
+    } else {
+      R(dalloc(&p->fyT, (size_t)p->nyp * p->kp));
+      if (e == cudaSuccess && alloc_tc(p, p->tc, true) != OFA_OK) e = cudaErrorMemoryAllocation;
+    }
+    return e;
+  };
+  {
+    cudaError_t re = reserve_all();
+    g_arena = nullptr;
+    OFA_TRY(re, "alloc");
+  }
+  OFA_TRY(arena_commit(p, reqs), "alloc");
+  OFA_TRY(cudaMallocHost(reinterpret_cast<void**>(&p->st_host), sizeof(OfaDevState)),
+          "pinned alloc");
   if (p->sep) {
-    OFA_TRY(dalloc(&p->fxu, (size_t)p->ux * nx), "alloc");
-    OFA_TRY(dalloc(&p->fyu, (size_t)p->uy * ny), "alloc");
-    p->sep_parts = sep_parts(nx, ny, p->ux, prop.multiProcessorCount);
-    OFA_TRY(dalloc(&p->gt, (size_t)p->sep_parts * p->ux * ny), "alloc");
-    OFA_TRY(dalloc(&p->tconj, (size_t)p->uy * nx), "alloc");
-    OFA_TRY(dalloc(&p->ones, (size_t)p->uy), "alloc");
-    OFA_TRY(dalloc(&p->ixy, (size_t)n_foci), "alloc");
-    OFA_TRY(dalloc(&p->row_ptr, (size_t)p->uy + 1), "alloc");
-    OFA_TRY(dalloc(&p->row_foci, (size_t)n_foci), "alloc");
     std::vector<int2> ixy(n_foci);
     std::vector<int> count(p->uy + 1, 0), order(n_foci);
     for (int k = 0; k < n_foci; ++k) {
@@ -579,8 +645,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     std::vector<double> ux2(2 * (size_t)p->ux, 0.0), uy2(2 * (size_t)p->uy, 0.0);
     for (int i = 0; i < p->ux; ++i) ux2[2 * i] = xs[i];
     for (int i = 0; i < p->uy; ++i) uy2[2 * i + 1] = ys[i];
-    double* dcoord = nullptr;
-    OFA_TRY(dalloc(&dcoord, ux2.size() + uy2.size()), "alloc");
+    double* dcoord = p->sep_coord;
     cudaError_t ce = cudaMemcpy(dcoord, ux2.data(), ux2.size() * 8, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess)
       ce = cudaMemcpy(dcoord + ux2.size(), uy2.data(), uy2.size() * 8, cudaMemcpyHostToDevice);
@@ -601,20 +666,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
                       p->fyu, p->stream);
       ce = cudaStreamSynchronize(p->stream);
     }
-    dfree(dcoord);
     OFA_TRY(ce, "separable grid set-up");
-  }
-  OFA_TRY(dalloc(&p->st, 1), "alloc");
-  OFA_TRY(cudaMallocHost(reinterpret_cast<void**>(&p->st_host), sizeof(OfaDevState)),
-          "pinned alloc");
-  if (!tc) {
-    OFA_TRY(dalloc(&p->e32, npix), "alloc");
-    OFA_TRY(dalloc(&p->e32_aux, npix), "alloc");
-  }
-  if (tc) {
-    OFA_TRY(dalloc(&p->fyT, (size_t)p->nyp * p->kp), "alloc");
-    if (alloc_tc(p, p->tc, true) != OFA_OK)
-      return fail(ofa_fail(p, OFA_ERR_OOM, "allocating tensor-core operands"));
   }
 
   // Small inputs.
@@ -638,14 +690,19 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   } else {
     launch_default_amplitude(p->amp, nx, ny, pitch_x, pitch_y, opt.waist_frac, p->stream);
   }
-  std::vector<float> ah(npix);
-  OFA_TRY(cudaMemcpyAsync(ah.data(), p->amp, npix * sizeof(float), cudaMemcpyDeviceToHost,
-                          p->stream),
-          "read amplitude");
-  OFA_TRY(cudaStreamSynchronize(p->stream), "sync");
+  std::vector<float> ah;
+  const float* av = opt.amplitude;
+  if (!opt.amplitude || opt.mem_space == OFA_MEM_DEVICE) {
+    ah.resize(npix);
+    OFA_TRY(cudaMemcpyAsync(ah.data(), p->amp, npix * sizeof(float), cudaMemcpyDeviceToHost,
+                            p->stream),
+            "read amplitude");
+    OFA_TRY(cudaStreamSynchronize(p->stream), "sync");
+    av = ah.data();
+  }
   double amax = 0.0, energy = 0.0;
   for (size_t i = 0; i < npix; ++i) {
-    const double a = ah[i];
+    const double a = av[i];
     if (!std::isfinite(a) || a < 0.0) {
       p->last_error = "amplitude must be finite and >= 0";
       return fail(OFA_ERR_INVALID_ARG);

@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/ofa.h"
 
@@ -108,6 +109,10 @@ struct ofa_plan {
   cudaGraphExec_t chunk_exec = nullptr;
   cudaGraphExec_t one_exec = nullptr;
   int chunk_iters = 16;
+
+  void* arena = nullptr;               // one allocation holding the buffers above
+  std::vector<void**> arena_slots;     // the pointers carved out of it
+  double* sep_coord = nullptr;         // separable form: distinct coordinates (set-up)
 
   std::string last_error;
 };
