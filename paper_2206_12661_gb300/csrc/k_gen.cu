@@ -70,9 +70,9 @@ __global__ void scale_kernel(float* x, size_t n, float f) {
     x[i] *= f;
 }
 
-// fyT[n][k] = fy[k][n] (zero outside K x ny), [nyp][kp]
+// fyT[n][k] = fy[k][n] (conjugated when conj; zero outside K x ny), [nyp][kp]
 __global__ void transpose_fy_kernel(const float2* __restrict__ fy, int K, int ny, int kp,
-                                    int nyp, float2* __restrict__ fyT) {
+                                    int nyp, int conj, float2* __restrict__ fyT) {
   __shared__ float2 tile[32][33];
   int k0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -82,7 +82,8 @@ __global__ void transpose_fy_kernel(const float2* __restrict__ fy, int K, int ny
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     int n = n0 + r, k = k0 + threadIdx.x;
-    if (n < nyp && k < kp) fyT[(size_t)n * kp + k] = tile[threadIdx.x][r];
+    const float2 v = tile[threadIdx.x][r];
+    if (n < nyp && k < kp) fyT[(size_t)n * kp + k] = make_float2(v.x, conj ? -v.y : v.y);
   }
 }
 
@@ -155,9 +156,9 @@ void launch_scale(float* x, size_t n, float f, cudaStream_t s) {
 }
 
 void launch_transpose_fy(const float2* fy, int K, int ny, int kp, int nyp, float2* fyT,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool conj) {
   dim3 grid((kp + 31) / 32, (nyp + 31) / 32);
-  transpose_fy_kernel<<<grid, dim3(32, 8), 0, s>>>(fy, K, ny, kp, nyp, fyT);
+  transpose_fy_kernel<<<grid, dim3(32, 8), 0, s>>>(fy, K, ny, kp, nyp, conj ? 1 : 0, fyT);
 }
 
 void launch_pack_fx(const float2* fx, int K, int nx, int kp, int nxp, int inverse, int prec,

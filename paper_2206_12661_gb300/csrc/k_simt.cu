@@ -11,9 +11,26 @@
 // projection phi = arg(E') and the next field A exp(i phi) (or, for the
 // gradient, 2 Im(conj(E) E')).
 //
-// Both are 64 x 64 complex tiles, 256 threads, 4 x 4 complex accumulators per
-// thread, 16-deep steps through double-buffered shared memory (one barrier per
-// step) with the next step's global loads in flight during the current one.
+// Both products are 64 x 64 complex tiles computed by 128 threads (four warps of
+// 32 x 32), each thread holding 8 x 4 complex outputs, by one loop (tile_product)
+// over operands stored row-major with the contraction contiguous: E and Fx for
+// the forward; conj(Fy)^T c and conj(Fx)^T for the inverse (conj(Fx)^T and Fy^T
+// are formed once per plan, conj(Fy)^T c once per iteration).  Stages of 16 contraction
+// steps are copied global -> shared by cp.async (two buffers, one barrier per
+// stage).  The shape is set by shared-memory bandwidth, the limit of these
+// products on sm_103a: a 16-byte shared load costs a warp 4 SM cycles, or 2 when
+// it reads at most four distinct addresses, so every lane of a quarter warp
+// reads the same row operand and the per-thread tile is 8 rows by 4 columns, 16
+// shared-load cycles for 32 FMA cycles per contraction step.  Both products
+// split their contraction over up to four blocks per tile (more resident warps
+// per SM and an even spread of blocks over the SMs) and sum the parts in fixed
+// order, so results do not depend on timing: in the forward the last block of a
+// tile to arrive sums the per-focus partial dots; in the inverse the parts of a
+// tile form a thread-block cluster and reduce through distributed shared memory.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "ofa_internal.cuh"
 #include "ofa_math.cuh"
 
@@ -21,6 +38,14 @@ namespace {
 
 constexpr int T64 = 64;
 constexpr int TS = 16;
+constexpr int SIMT_THREADS = 128;
+constexpr int SP = TS + 2;   // padded row pitch (complex) of the forward's staged tiles
+
+// Pairs of contraction steps unrolled in the inner loop.
+#ifndef OFA_SIMT_UNROLL
+#define OFA_SIMT_UNROLL 1
+#endif
+constexpr int UNROLL = OFA_SIMT_UNROLL;
 
 __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, acc.x);
@@ -29,27 +54,19 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(a.y, b.x, acc.y);
 }
 
-// 16 steps of the 4 x 4 complex outer products of one shared-memory stage:
-// rows a[.][ty*4 ..], columns b[.][tx*4 ..].
-// UNROLL: steps unrolled (the forward runs best with 4, the inverse with 16).
-template <int UNROLL>
-__device__ __forceinline__ void mma_stage(const float2 (*a)[T64], const float2 (*b)[T64], int ty,
-                                          int tx, float2 (&acc)[4][4]) {
-#pragma unroll UNROLL
-  for (int mm = 0; mm < TS; ++mm) {
-    const float4 a01 = *reinterpret_cast<const float4*>(&a[mm][ty * 4]);
-    const float4 a23 = *reinterpret_cast<const float4*>(&a[mm][ty * 4 + 2]);
-    const float4 b01 = *reinterpret_cast<const float4*>(&b[mm][tx * 4]);
-    const float4 b23 = *reinterpret_cast<const float4*>(&b[mm][tx * 4 + 2]);
-    const float2 e[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
-                         make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
-    const float2 f[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
-                         make_float2(b23.x, b23.y), make_float2(b23.z, b23.w)};
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) cmac(acc[i][j], e[i], f[j]);
-  }
+// 8-byte global -> shared asynchronous copy; zero-fills the destination when !ok
+// (src is then not read).
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src, bool ok) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+               "r"(ok ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 // E = A exp(i phi), complex planes [ny][nx] (accurate sincosf: the FP32 form keeps
@@ -65,201 +82,252 @@ __global__ void field_f32_kernel(const float* __restrict__ phi, const float* __r
   }
 }
 
-// STORE: instead of the per-focus dot, write the product itself transposed,
-// gt[k][n] = G[n][k] (the separable grid form's first product).
-template <bool STORE>
-__global__ void __launch_bounds__(256) fwd_simt_kernel(
-    const float2* __restrict__ e32, const float2* __restrict__ fx, const float2* __restrict__ fy,
-    int nx, int ny, int K, int kp, float2* __restrict__ part, const int* __restrict__ done) {
-  if (done != nullptr && *done) return;
-  __shared__ __align__(16) float2 Es[2][TS][T64];
-  __shared__ __align__(16) float2 Fs[2][TS][T64];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int n0 = blockIdx.y * T64, k0 = blockIdx.x * T64;
-  const int lr = tid >> 2, lc = (tid & 3) * 4;
-  // this block's share of the contraction: whole TS-deep steps [m_begin, m_end)
-  const int steps = (nx + TS - 1) / TS;
-  const int m_begin = (int)(blockIdx.z * steps / gridDim.z) * TS;
-  const int m_end = min(nx, (int)((blockIdx.z + 1) * steps / gridDim.z) * TS);
+// Shared staging of one 64 x 64 tile product: two buffers of 64 rows x 16
+// contraction steps for each operand, padded pitch.
+struct TileSmem {
+  float2 a[2][T64][SP];
+  float2 b[2][T64][SP];
+};
 
-  float2 acc[4][4];
+// acc[i][j] += sum_t A[r0 + r_i][t] B[c0 + c_j][t] over t in [t_begin, t_end).
+// A and B are row-major with the contraction contiguous
+// (leading dimensions lda, ldb; rows >= a_rows / b_rows read as zero) and are
+// staged in that layout, so that one 16-byte load gives a row's two consecutive
+// contraction steps.  Thread (warp w, lane l): rows r_i = (w>>1)*32 + (l>>3) + 4i,
+// i < 8 (one row per quarter warp: the same address across its lanes), columns
+// c_j = (w&1)*32 + (l&7) + 8j, j < 4 (eight consecutive padded rows per quarter:
+// distinct banks).  t_begin is a multiple of 16; t_end is one too or the end of
+// the contraction.
+__device__ __forceinline__ void tile_product(TileSmem& sm, const float2* __restrict__ A, int lda,
+                                             int a_rows, const float2* __restrict__ B, int ldb,
+                                             int b_rows, int r0, int c0, int t_begin, int t_end,
+                                             float2 (&acc)[8][4]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lr = lane >> 3, lc = lane & 7, wr = warp >> 1, wc = warp & 1;
+  // element q of a stage: row (tid + 128 q) / 16, step (tid + 128 q) % 16
+  auto issue = [&](int b, int t0) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + SIMT_THREADS * q, r = e >> 4, tt = e & 15, t = t0 + tt;
+      const bool okA = r0 + r < a_rows && t < t_end, okB = c0 + r < b_rows && t < t_end;
+      cp_async8(&sm.a[b][r][tt], okA ? A + (size_t)(r0 + r) * lda + t : A, okA);
+      cp_async8(&sm.b[b][r][tt], okB ? B + (size_t)(c0 + r) * ldb + t : B, okB);
+    }
+    cp_async_commit();
+  };
 
-  float2 ev[4], fv[4];
-  auto gload = [&](int m0) {
-    const int n = n0 + lr, k = k0 + lr;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int m = m0 + lc + q;
-      ev[q] = (n < ny && m < nx) ? e32[(size_t)n * nx + m] : make_float2(0.f, 0.f);
-      fv[q] = (k < K && m < nx) ? fx[(size_t)k * nx + m] : make_float2(0.f, 0.f);
-    }
-  };
-  auto sstore = [&](int b) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      Es[b][lc + q][lr] = ev[q];
-      Fs[b][lc + q][lr] = fv[q];
-    }
-  };
-  gload(m_begin);
-  sstore(0);
-  __syncthreads();
+  if (t_begin < t_end) issue(0, t_begin);
   int b = 0;
-  for (int m0 = m_begin; m0 < m_end; m0 += TS) {
-    const bool more = m0 + TS < m_end;
-    if (more) gload(m0 + TS);
-    mma_stage<4>(Es[b], Fs[b], ty, tx, acc);
-    if (more) sstore(b ^ 1);  // its readers finished before the previous barrier
-    __syncthreads();
+  for (int t0 = t_begin; t0 < t_end; t0 += TS) {
+    cp_async_wait_all();
+    __syncthreads();  // stage b complete; every thread is done with stage b ^ 1
+    if (t0 + TS < t_end) issue(b ^ 1, t0 + TS);
+#pragma unroll UNROLL
+    for (int tt = 0; tt < TS; tt += 2) {
+      float4 fq[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        fq[j] = *reinterpret_cast<const float4*>(&sm.b[b][wc * 32 + lc + 8 * j][tt]);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float4 aq = *reinterpret_cast<const float4*>(&sm.a[b][wr * 32 + lr + 4 * i][tt]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          cmac(acc[i][j], make_float2(aq.x, aq.y), make_float2(fq[j].x, fq[j].y));
+          cmac(acc[i][j], make_float2(aq.z, aq.w), make_float2(fq[j].z, fq[j].w));
+        }
+      }
+    }
     b ^= 1;
-  }
-
-  if (STORE) {
-    float2* g = part + (size_t)blockIdx.z * K * ny;   // slice of this contraction part
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int k = k0 + tx * 4 + j;
-      if (k >= K) continue;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int n = n0 + ty * 4 + i;
-        if (n < ny) g[(size_t)k * ny + n] = acc[i][j];
-      }
-    }
-    return;
-  }
-  // Per-focus dot with the Fy rows, reduced over the tile's 64 rows in fixed order.
-  float2* red = &Es[0][0][0];  // 16 x 64 float2
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int k = k0 + tx * 4 + j;
-    float2 s = make_float2(0.f, 0.f);
-    if (k < K) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int n = n0 + ty * 4 + i;
-        if (n < ny) cmac(s, fy[(size_t)k * ny + n], acc[i][j]);
-      }
-    }
-    red[ty * T64 + tx * 4 + j] = s;
-  }
-  __syncthreads();
-  if (tid < T64) {
-    float2 a = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      const float2 v = red[t * T64 + tid];
-      a.x += v.x;
-      a.y += v.y;
-    }
-    const int k = k0 + tid;
-    if (k < kp) part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * kp + k] = a;
   }
 }
 
+// Contraction part z of gridDim.z: whole 16-deep steps [begin, end) of len.
+__device__ __forceinline__ int2 part_range(int len) {
+  const int steps = (len + TS - 1) / TS;
+  return make_int2((int)(blockIdx.z * steps / gridDim.z) * TS,
+                   min(len, (int)((blockIdx.z + 1) * steps / gridDim.z) * TS));
+}
+
+// Forward tile: rows n (E rows), columns k (foci), contraction m.
+// STORE: instead of the per-focus dot, write the product itself transposed,
+// gt[k][n] = G[n][k] (the separable grid form's first product).
+template <bool STORE>
+__global__ void __launch_bounds__(SIMT_THREADS, 4) fwd_simt_kernel(
+    const float2* __restrict__ e32, const float2* __restrict__ fx, const float2* __restrict__ fy,
+    int nx, int ny, int K, int kp, float2* __restrict__ part, const int* __restrict__ done,
+    float2* __restrict__ fws, unsigned* __restrict__ cnt) {
+  if (done != nullptr && *done) return;
+  __shared__ __align__(16) TileSmem sm;
+  __shared__ float2 red[2][T64];
+  __shared__ int last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lr = lane >> 3, lc = lane & 7, wr = warp >> 1, wc = warp & 1;
+  const int n0 = blockIdx.y * T64, k0 = blockIdx.x * T64;
+
+  float2 acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  const int2 range = part_range(nx);
+  tile_product(sm, e32, nx, ny, fx, nx, K, n0, k0, range.x, range.y, acc);
+
+  if constexpr (STORE) {
+    float2* g = part + (size_t)blockIdx.z * K * ny;   // slice of this contraction part
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + wc * 32 + lc + 8 * j;
+      if (k >= K) continue;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int n = n0 + wr * 32 + lr + 4 * i;
+        if (n < ny) g[(size_t)k * ny + n] = acc[i][j];
+      }
+    }
+  } else {
+    // Per-focus dot with the Fy rows over the tile's 64 rows, reduced in fixed order:
+    // the thread's 8 rows, the four quarter warps (shuffles), the two row warps.
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + wc * 32 + lc + 8 * j;
+      float2 s = make_float2(0.f, 0.f);
+      if (k < K) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int n = n0 + wr * 32 + lr + 4 * i;
+          if (n < ny) cmac(s, fy[(size_t)k * ny + n], acc[i][j]);
+        }
+      }
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 8);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 8);
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 16);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 16);
+      if (lr == 0) red[wr][wc * 32 + lc + 8 * j] = s;
+    }
+    __syncthreads();
+    const int k = k0 + tid;
+    float2 mine = make_float2(0.f, 0.f);
+    if (tid < T64) mine = make_float2(red[0][tid].x + red[1][tid].x, red[0][tid].y + red[1][tid].y);
+    if (gridDim.z == 1) {
+      if (tid < T64 && k < kp) part[(size_t)blockIdx.y * kp + k] = mine;
+      return;
+    }
+    // contraction parts: the last block of this tile sums them in order z = 0, 1, ...
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    float2* ws = fws + (size_t)tile * gridDim.z * T64;
+    if (tid < T64) ws[blockIdx.z * T64 + tid] = mine;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(&cnt[tile], 1u) == gridDim.z - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (tid < T64) {
+      float2 a = make_float2(0.f, 0.f);
+      for (int z = 0; z < (int)gridDim.z; ++z) {
+        const float2 v = z == (int)blockIdx.z ? mine : __ldcg(&ws[z * T64 + tid]);
+        a.x += v.x;
+        a.y += v.y;
+      }
+      if (k < kp) part[(size_t)blockIdx.y * kp + k] = a;
+    }
+    if (tid == 0) cnt[tile] = 0;
+  }
+}
+
+// pT[n][k] = conj(FyT[n][k]) c_k: the inverse's left operand, rows n, contraction
+// k < K, row pitch ldk (the padding columns are zero).
+__global__ void scale_conj_kernel(const float2* __restrict__ fyT, const float2* __restrict__ c,
+                                  int K, int ldk, int ny, float2* __restrict__ pT,
+                                  const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  const size_t n = (size_t)ldk * ny;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % ldk);
+    const float2 a = fyT[i], ck = k < K ? c[k] : make_float2(0.f, 0.f);
+    pT[i] = make_float2(a.x * ck.x + a.y * ck.y, a.x * ck.y - a.y * ck.x);
+  }
+}
+
+// Inverse tile: rows n, columns m, contraction k over this block's part of it:
+// E'[n][m] = sum_k pT[n][k] fxT[m][k], fxT = conj(Fx)^T (both with row pitch ldk).
+// With the contraction split (gridDim.z > 1) the z parts of a tile run as one
+// thread-block cluster: each keeps its partial tile in its shared memory, and
+// after a cluster barrier part z sums outputs [32z/Z, 32(z+1)/Z) of every thread
+// over the parts in order 0, 1, ... (distributed shared memory) and finishes them.
 // EPI 0: phi = arg(E') (atan2(0,0) = 0) and the next field A exp(i phi), formed
 // exactly as field_f32_kernel forms it from a stored phi.
 // EPI 1: grad = f 2 A (cos phi Im B - sin phi Re B).
 template <int EPI>
-__global__ void __launch_bounds__(256) bwd_simt_kernel(
-    const float2* __restrict__ c, const float2* __restrict__ fx, const float2* __restrict__ fy,
-    int nx, int ny, int K, float* __restrict__ out, float2* __restrict__ e_out,
-    const float* __restrict__ phi_in, const float* __restrict__ amp, float amp_factor,
-    const OfaDevState* __restrict__ st, const int* __restrict__ done) {
+__global__ void __launch_bounds__(SIMT_THREADS, 4) bwd_simt_kernel(
+    const float2* __restrict__ pT, const float2* __restrict__ fxT, int nx, int ny, int K, int ldk,
+    float* __restrict__ out, float2* __restrict__ e_out, const float* __restrict__ phi_in,
+    const float* __restrict__ amp, float amp_factor, const OfaDevState* __restrict__ st,
+    const int* __restrict__ done) {
   if (done != nullptr && *done) return;
-  __shared__ __align__(16) float2 Ps[2][TS][T64];
-  __shared__ __align__(16) float2 Qs[2][TS][T64];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  __shared__ __align__(16) TileSmem sm;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lr = lane >> 3, lc = lane & 7, wr = warp >> 1, wc = warp & 1;
   const int n0 = blockIdx.y * T64, m0 = blockIdx.x * T64;
-  const int lk = tid >> 4, lc = (tid & 15) * 4;
 
-  float2 acc[4][4];
+  float2 acc[8][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  const int2 range = part_range(K);
+  tile_product(sm, pT, ldk, ny, fxT, ldk, nx, n0, m0, range.x, range.y, acc);
 
-  float2 pv[4], qv[4];
-  auto gload = [&](int k0) {
-    const int k = k0 + lk;
-    const float2 ck = k < K ? c[k] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int n = n0 + lc + q, m = m0 + lc + q;
-      const float2 a = (k < K && n < ny) ? fy[(size_t)k * ny + n] : make_float2(0.f, 0.f);
-      const float2 b = (k < K && m < nx) ? fx[(size_t)k * nx + m] : make_float2(0.f, 0.f);
-      // conj(Fy[k,n]) c_k
-      pv[q] = make_float2(a.x * ck.x + a.y * ck.y, a.x * ck.y - a.y * ck.x);
-      qv[q] = make_float2(b.x, -b.y);  // conj(Fx[k,m])
-    }
-  };
-  auto sstore = [&](int b) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      Ps[b][lk][lc + q] = pv[q];
-      Qs[b][lk][lc + q] = qv[q];
-    }
-  };
-  gload(0);
-  sstore(0);
-  __syncthreads();
-  int b = 0;
-  for (int k0 = 0; k0 < K; k0 += TS) {
-    const bool more = k0 + TS < K;
-    if (more) gload(k0 + TS);
-    mma_stage<16>(Ps[b], Qs[b], ty, tx, acc);
-    if (more) sstore(b ^ 1);
-    __syncthreads();
-    b ^= 1;
-  }
-
-  float factor = 0.f;
-  if (EPI == 1) factor = 2.f * amp_factor / st->c_scale;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int n = n0 + ty * 4 + i;
-    if (n >= ny) continue;
-    float v[4];
-    float2 ev[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int m = m0 + tx * 4 + j;
-      if (EPI == 0) {
-        v[j] = ofa_arg(acc[i][j].y, acc[i][j].x);
-        float s, cs;
-        sincosf(v[j], &s, &cs);
-        const float a = m < nx ? amp[(size_t)n * nx + m] : 0.f;
-        ev[j] = make_float2(a * cs, a * s);
-      } else if (m < nx) {
-        float s, cs;
-        sincosf(phi_in[(size_t)n * nx + m], &s, &cs);
-        v[j] = factor * amp[(size_t)n * nx + m] * (cs * acc[i][j].y - s * acc[i][j].x);
-      } else {
-        v[j] = 0.f;
-      }
-    }
-    const int m = m0 + tx * 4;
-    float* dst = out + (size_t)n * nx + m;
-    if ((nx & 3) == 0 && m + 3 < nx) {
-      *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
-      if (EPI == 0) {
-        float4* ed = reinterpret_cast<float4*>(e_out + (size_t)n * nx + m);
-        ed[0] = make_float4(ev[0].x, ev[0].y, ev[1].x, ev[1].y);
-        ed[1] = make_float4(ev[2].x, ev[2].y, ev[3].x, ev[3].y);
-      }
+  const float factor = EPI == 1 ? 2.f * amp_factor / st->c_scale : 0.f;
+  // output (i, j) of this thread: row n0 + (w>>1)*32 + (l>>3) + 4i, column
+  // m0 + (w&1)*32 + (l&7) + 8j
+  auto finish = [&](int i, int j, float2 z) {
+    const int n = n0 + wr * 32 + lr + 4 * i, m = m0 + wc * 32 + lc + 8 * j;
+    if (n >= ny || m >= nx) return;
+    const size_t o = (size_t)n * nx + m;
+    if (EPI == 0) {
+      const float ph = ofa_arg(z.y, z.x);
+      float sn, cs;
+      sincosf(ph, &sn, &cs);
+      const float a = amp[o];
+      out[o] = ph;
+      e_out[o] = make_float2(a * cs, a * sn);
     } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (m + j < nx) {
-          dst[j] = v[j];
-          if (EPI == 0) e_out[(size_t)n * nx + m + j] = ev[j];
-        }
+      float sn, cs;
+      sincosf(phi_in[o], &sn, &cs);
+      out[o] = factor * amp[o] * (cs * z.y - sn * z.x);
     }
+  };
+
+  if (gridDim.z == 1) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) finish(i, j, acc[i][j]);
+    return;
   }
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  float2* part = &sm.a[0][0][0];   // 32 x 128 partial outputs (fits in the stages)
+  __syncthreads();                 // every warp is done with the stages
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) part[(i * 4 + j) * SIMT_THREADS + tid] = acc[i][j];
+  cluster.sync();
+  const int Z = (int)gridDim.z, z = (int)blockIdx.z;
+  for (int idx = z * 32 / Z; idx < (z + 1) * 32 / Z; ++idx) {
+    float2 v = make_float2(0.f, 0.f);
+    for (int r = 0; r < Z; ++r) {
+      const float2 t = cluster.map_shared_rank(part, r)[idx * SIMT_THREADS + tid];
+      v.x += t.x;
+      v.y += t.y;
+    }
+    finish(idx >> 2, idx & 3, v);
+  }
+  cluster.sync();   // the other parts still read this block's shared memory
 }
 
 // Separable grid form, focal step of the forward: Theta_k = sum_n Fyu[iy_k][n] G[n][ix_k]
@@ -341,9 +409,40 @@ __global__ void __launch_bounds__(256) sep_t_kernel(
 
 }  // namespace
 
-constexpr int FWD_SPLIT = 1;  // contraction parts of the forward (grid z)
+// Contraction parts (grid z) of the two products, at most: more, shorter blocks
+// fill the SMs with resident warps and even out the blocks per SM.  A part keeps
+// at least four 16-deep stages.
+#ifndef OFA_SIMT_FWD_SPLIT
+#define OFA_SIMT_FWD_SPLIT 4
+#endif
+#ifndef OFA_SIMT_BWD_SPLIT
+#define OFA_SIMT_BWD_SPLIT 4
+#endif
+constexpr int FWD_SPLIT = OFA_SIMT_FWD_SPLIT;
+constexpr int BWD_SPLIT = OFA_SIMT_BWD_SPLIT;
 
-int simt_fwd_tiles(int ny) { return FWD_SPLIT * ((ny + T64 - 1) / T64); }
+int split_parts(int len, int max_parts) {
+  const int stages = (len + TS - 1) / TS;
+  return std::max(1, std::min(max_parts, stages / 4));
+}
+
+int tiles_of(int n) { return (n + T64 - 1) / T64; }
+
+int simt_fwd_tiles(int ny) { return tiles_of(ny); }
+
+int simt_ldk(int K) { return (K + TS - 1) / TS * TS; }
+
+SimtSizes simt_sizes(int nx, int ny, int K, int rows) {
+  SimtSizes z;
+  z.fwd_tiles = tiles_of(K) * tiles_of(ny);
+  const size_t ldk = simt_ldk(std::max(rows, K));
+  z.p32 = ldk * ny;
+  z.fxT = ldk * nx;
+  z.fyT = ldk * ny;
+  z.fws = (size_t)z.fwd_tiles * FWD_SPLIT * T64;
+  z.cnt = (size_t)z.fwd_tiles;
+  return z;
+}
 
 void launch_field_f32(const float* phi, const float* amp, int nx, int ny, float2* e,
                       cudaStream_t s) {
@@ -354,9 +453,10 @@ void launch_field_f32(const float* phi, const float* amp, int nx, int ny, float2
 }
 
 void launch_fwd_simt(const float2* e32, const float2* fx, const float2* fy, int nx, int ny, int K,
-                     int kp, float2* part, const int* done, cudaStream_t s) {
-  dim3 grid((K + T64 - 1) / T64, (ny + T64 - 1) / T64, FWD_SPLIT);
-  fwd_simt_kernel<false><<<grid, 256, 0, s>>>(e32, fx, fy, nx, ny, K, kp, part, done);
+                     int kp, float2* part, const int* done, const SimtWork& w, cudaStream_t s) {
+  dim3 grid(tiles_of(K), tiles_of(ny), split_parts(nx, FWD_SPLIT));
+  fwd_simt_kernel<false><<<grid, SIMT_THREADS, 0, s>>>(e32, fx, fy, nx, ny, K, kp, part, done,
+                                                       w.fws, w.cnt);
 }
 
 int sep_parts(int nx, int ny, int ux, int sms) {
@@ -371,7 +471,8 @@ int sep_parts(int nx, int ny, int ux, int sms) {
 void launch_sep_forward(const float2* e32, const float2* fxu, int nx, int ny, int ux, int parts,
                         float2* gt, cudaStream_t s) {
   dim3 grid((ux + T64 - 1) / T64, (ny + T64 - 1) / T64, parts);
-  fwd_simt_kernel<true><<<grid, 256, 0, s>>>(e32, fxu, nullptr, nx, ny, ux, ux, gt, nullptr);
+  fwd_simt_kernel<true><<<grid, SIMT_THREADS, 0, s>>>(e32, fxu, nullptr, nx, ny, ux, ux, gt, nullptr,
+                                                      nullptr, nullptr);
 }
 
 void launch_sep_theta(float2* gt, const float2* fyu, const int2* ixy, int K, int ny, int ux,
@@ -391,17 +492,47 @@ void launch_sep_t(const float2* c, const float2* fxu, const int2* ixy, const int
   sep_t_kernel<<<grid, 256, 0, s>>>(c, fxu, ixy, row_ptr, row_foci, nx, tconj);
 }
 
-void launch_bwd_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,
-                     const float* amp, float* phi, float2* e32, const int* done, cudaStream_t s) {
-  dim3 grid((nx + T64 - 1) / T64, (ny + T64 - 1) / T64);
-  bwd_simt_kernel<0><<<grid, 256, 0, s>>>(c, fx, fy, nx, ny, K, phi, e32, nullptr, amp, 0.f,
-                                          nullptr, done);
+void launch_scale_conj(const float2* c, const float2* fyT, int ny, int K, float2* pT,
+                       const int* done, cudaStream_t s) {
+  const int ldk = simt_ldk(K);
+  const size_t n = (size_t)ldk * ny;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  scale_conj_kernel<<<(unsigned)blocks, 256, 0, s>>>(fyT, c, K, ldk, ny, pT, done);
 }
 
-void launch_grad_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,
-                      const float* phi, const float* amp, float amp_factor,
-                      const OfaDevState* st, float* grad, cudaStream_t s) {
-  dim3 grid((nx + T64 - 1) / T64, (ny + T64 - 1) / T64);
-  bwd_simt_kernel<1><<<grid, 256, 0, s>>>(c, fx, fy, nx, ny, K, grad, nullptr, phi, amp,
-                                          amp_factor, st, nullptr);
+// The inverse product; its contraction parts (grid z) form one cluster per tile.
+template <int EPI>
+void launch_bwd_kernel(const float2* pT, const float2* fxT, int nx, int ny, int K, float* out,
+                       float2* e_out, const float* phi_in, const float* amp, float amp_factor,
+                       const OfaDevState* st, const int* done, cudaStream_t s) {
+  const int z = split_parts(K, BWD_SPLIT);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tiles_of(nx), tiles_of(ny), z);
+  cfg.blockDim = dim3(SIMT_THREADS);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = z;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, bwd_simt_kernel<EPI>, pT, fxT, nx, ny, K, simt_ldk(K), out, e_out,
+                     phi_in, amp, amp_factor, st, done);
+}
+
+void launch_bwd_simt(const float2* c, const float2* fxT, const float2* fyT, int nx, int ny, int K,
+                     const float* amp, float* phi, float2* e32, const int* done,
+                     const SimtWork& w, cudaStream_t s) {
+  launch_scale_conj(c, fyT, ny, K, w.p32, done, s);
+  launch_bwd_kernel<0>(w.p32, fxT, nx, ny, K, phi, e32, nullptr, amp, 0.f, nullptr, done, s);
+}
+
+void launch_grad_simt(const float2* c, const float2* fxT, const float2* fyT, int nx, int ny,
+                      int K, const float* phi, const float* amp, float amp_factor,
+                      const OfaDevState* st, float* grad, const SimtWork& w, cudaStream_t s) {
+  launch_scale_conj(c, fyT, ny, K, w.p32, nullptr, s);
+  launch_bwd_kernel<1>(w.p32, fxT, nx, ny, K, grad, nullptr, phi, amp, amp_factor, st, nullptr,
+                       s);
 }

@@ -165,6 +165,13 @@ int* done_ptr(ofa_plan* p) { return &p->st->done; }
 // One iteration of Algorithm 1 on stream s.
 // Separable grid form: the forward through the distinct x (G = E Fxu^T, then
 // Theta_k = Fyu[iy_k] . G[:, ix_k]) into the single partial row.
+// FP32 inverse operands of the separable form: the conjugate of the first inverse
+// product, transposed, [nx][ldk] (Fyu^T is formed once per plan).
+const float2* sep_fxT(ofa_plan* p, cudaStream_t s) {
+  launch_transpose_fy(p->tconj, p->uy, p->nx, simt_ldk(p->uy), p->nx, p->simt.fxT, s, true);
+  return p->simt.fxT;
+}
+
 void enqueue_sep_forward(ofa_plan* p, const float2* e32, cudaStream_t s) {
   launch_sep_forward(e32, p->fxu, p->nx, p->ny, p->ux, p->sep_parts, p->gt, s);
   launch_sep_theta(p->gt, p->fyu, p->ixy, p->K, p->ny, p->ux, p->sep_parts, p->part, s);
@@ -177,13 +184,13 @@ void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
     launch_focal(p->part, 1, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist, p->st,
                  0, p->weighting, 1.f, p->amp_energy, s);
     launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj, s);
-    launch_bwd_simt(p->ones, p->tconj, p->fyu, p->nx, p->ny, p->uy, p->amp, p->phi, p->e32, done,
+    launch_bwd_simt(p->ones, sep_fxT(p, s), p->simt.fyT, p->nx, p->ny, p->uy, p->amp, p->phi, p->e32, done, p->simt,
                     s);
   } else if (!use_tc(p)) {
-    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, done, s);
+    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, done, p->simt, s);
     launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
                  p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
-    launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->amp, p->phi, p->e32, done, s);
+    launch_bwd_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32, done, p->simt, s);
   } else {
     // up to 4096 foci the focal step runs in the forward kernel's last CTA
     const bool fuse = p->K <= 4096;
@@ -203,7 +210,7 @@ void enqueue_forward_current(ofa_plan* p, cudaStream_t s) {
     launch_focal(p->part, 1, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist, p->st,
                  1, p->weighting, ldexpf(1.f, p->amp_exp), p->amp_energy, s);
   } else if (!use_tc(p)) {
-    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, s);
+    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, p->simt, s);
     launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
                  p->c, p->hist, p->st, 1, p->weighting, ldexpf(1.f, p->amp_exp), p->amp_energy,
                  s);
@@ -614,6 +621,12 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     if (!tc) {
       R(dalloc(&p->e32, npix));
       R(dalloc(&p->e32_aux, npix));
+      const SimtSizes z = simt_sizes(nx, ny, n_foci, p->sep ? p->uy : n_foci);
+      R(dalloc(&p->simt.p32, z.p32));
+      R(dalloc(&p->simt.fxT, z.fxT));
+      R(dalloc(&p->simt.fyT, z.fyT));
+      R(dalloc(&p->simt.fws, z.fws));
+      R(dalloc(&p->simt.cnt, z.cnt));
     } else {
       R(dalloc(&p->fyT, (size_t)p->nyp * p->kp));
       if (e == cudaSuccess && alloc_tc(p, p->tc, true) != OFA_OK) e = cudaErrorMemoryAllocation;
@@ -759,7 +772,16 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
       return fail(OFA_ERR_CUDA);
     }
   }
-  if (!tc) launch_field_f32(p->phi, p->amp, nx, ny, p->e32, p->stream);
+  if (!tc) {
+    // FP32 inverse operands, contraction contiguous: conj(Fx)^T, Fy^T (separable: Fyu^T)
+    if (p->sep) {
+      launch_transpose_fy(p->fyu, p->uy, ny, simt_ldk(p->uy), ny, p->simt.fyT, p->stream);
+    } else {
+      launch_transpose_fy(p->fx, n_foci, nx, simt_ldk(n_foci), nx, p->simt.fxT, p->stream, true);
+      launch_transpose_fy(p->fy, n_foci, ny, simt_ldk(n_foci), ny, p->simt.fyT, p->stream);
+    }
+    launch_field_f32(p->phi, p->amp, nx, ny, p->e32, p->stream);
+  }
   launch_set_j(p->st, 0, 1, p->stream);
   launch_control(p->st, 0.0, 1, p->stream);
   OFA_TRY(cudaGetLastError(), "launching set-up kernels");
@@ -843,18 +865,18 @@ ofa_status ofa_iterate_measured(ofa_plan* p, const float* measured, int mem_spac
   const int n_part = p->sep ? 1 : use_tc(p) ? fwd_n_part(p->nyp, p->tc) : simt_fwd_tiles(p->ny);
   if (p->sep) enqueue_sep_forward(p, p->e32, s);
   else if (use_tc(p)) launch_fwd_tc(p, p->tc, nullptr, s, false);
-  else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, s);
+  else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, p->simt, s);
   launch_focal_measured(p->part, n_part, p->kp, p->K, p->t, p->w, p->theta, p->c, p->hist, p->st,
                         p->weighting, p->meas, s);
   if (p->sep) {
     launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj, s);
-    launch_bwd_simt(p->ones, p->tconj, p->fyu, p->nx, p->ny, p->uy, p->amp, p->phi, p->e32,
-                    nullptr, s);
+    launch_bwd_simt(p->ones, sep_fxT(p, s), p->simt.fyT, p->nx, p->ny, p->uy, p->amp, p->phi, p->e32,
+                    nullptr, p->simt, s);
   } else if (use_tc(p)) {
     launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
     launch_bwd_tc(p, p->tc, nullptr, s);
   } else {
-    launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->amp, p->phi, p->e32, nullptr, s);
+    launch_bwd_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32, nullptr, p->simt, s);
   }
   ofa_status st = sync_and_check(p);
   if (st != OFA_OK) return st;
@@ -963,7 +985,7 @@ ofa_status ofa_forward(ofa_plan* p, const float* phi, float* theta, float* inten
                  p->weighting, out_scale, p->amp_energy, p->stream);
   } else if (!use_tc(p)) {
     launch_field_f32(phi, p->amp, p->nx, p->ny, p->e32_aux, p->stream);
-    launch_fwd_simt(p->e32_aux, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr,
+    launch_fwd_simt(p->e32_aux, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, p->simt,
                     p->stream);
     launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, th, in, p->c, p->hist,
                  p->st, 2, p->weighting, out_scale, p->amp_energy, p->stream);
@@ -990,11 +1012,11 @@ ofa_status ofa_adjoint(ofa_plan* p, const float* phi, const float* theta,
   if (p->sep) {
     launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj,
                  p->stream);
-    launch_grad_simt(p->ones, p->tconj, p->fyu, p->nx, p->ny, p->uy, phi, p->amp, amp_factor,
-                     p->st, grad_phi, p->stream);
+    launch_grad_simt(p->ones, sep_fxT(p, p->stream), p->simt.fyT, p->nx, p->ny, p->uy, phi, p->amp, amp_factor,
+                     p->st, grad_phi, p->simt, p->stream);
   } else if (!use_tc(p)) {
-    launch_grad_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, phi, p->amp, amp_factor, p->st,
-                     grad_phi, p->stream);
+    launch_grad_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, phi, p->amp, amp_factor, p->st,
+                     grad_phi, p->simt, p->stream);
   } else {
     launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo,
                    p->stream);
@@ -1045,7 +1067,7 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
       case 0:
         if (p->sep) enqueue_sep_forward(p, p->e32, s);
         else if (tc) launch_fwd_tc(p, p->tc, nullptr, s, p->K <= 4096);  // + fused focal step
-        else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr,
+        else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, p->simt,
                              s);
         break;
       case 1:
@@ -1061,11 +1083,11 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
                                     p->tc.p_hi, p->tc.p_lo, s);
         break;
       default:
-        if (p->sep) launch_bwd_simt(p->ones, p->tconj, p->fyu, p->nx, p->ny, p->uy, p->amp,
-                                    p->phi, p->e32, nullptr, s);
+        if (p->sep) launch_bwd_simt(p->ones, sep_fxT(p, s), p->simt.fyT, p->nx, p->ny, p->uy, p->amp,
+                                    p->phi, p->e32, nullptr, p->simt, s);
         else if (tc) launch_bwd_tc(p, p->tc, nullptr, s);
-        else launch_bwd_simt(p->c, p->fx, p->fy, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
-                             nullptr, s);
+        else launch_bwd_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
+                             nullptr, p->simt, s);
         break;
     }
   };

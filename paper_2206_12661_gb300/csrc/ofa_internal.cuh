@@ -58,6 +58,18 @@ struct TcOperands {
   int fwd_ccx = 1, fwd_ccy = 1, bwd_ccx = 1, bwd_ccy = 1;  // thread-block cluster shapes
 };
 
+// FP32 form scratch: the inverse's transposed operands and the forward's
+// contraction-split workspace (each part writes its per-focus partial dots; the
+// last part to arrive at a tile, by arrival counter, sums them in fixed order).
+struct SimtWork {
+  // pitch simt_ldk(contraction length), zero padded:
+  float2* p32 = nullptr;      // [ny][ldk] conj(Fy[k,n]) c_k
+  float2* fxT = nullptr;      // [nx][ldk] conj(Fx)^T (separable: conj of the first inverse product^T)
+  float2* fyT = nullptr;      // [ny][ldk] Fy^T (separable form: Fyu^T)
+  float2* fws = nullptr;      // forward: [fwd_tiles][parts][64] partial per-focus dots
+  unsigned* cnt = nullptr;    // forward: [fwd_tiles] arrival counters
+};
+
 struct ofa_plan {
   int device = 0;
   cudaStream_t stream = nullptr;       // stream the plan's work is enqueued on
@@ -90,6 +102,7 @@ struct ofa_plan {
   float* scratch_phi = nullptr;        // for ofa_forward / ofa_adjoint on the tensor path
   float2* e32 = nullptr;               // FP32 form: pupil field A exp(i phi) [ny][nx]
   float2* e32_aux = nullptr;           // FP32 form: field of an external phase
+  SimtWork simt;                       // FP32 form: inverse operand and split workspaces
   float* meas = nullptr;               // [K] captured intensities (camera in the loop)
   // separable grid form (sep): products through the ux distinct x and uy distinct y
   bool sep = false;
@@ -129,8 +142,9 @@ void launch_default_amplitude(float* amp, int nx, int ny, double px, double py, 
                               cudaStream_t s);
 void launch_default_phase(float* phi, int nx, int ny, uint64_t seed, cudaStream_t s);
 void launch_scale(float* x, size_t n, float f, cudaStream_t s);
+// dst [nyp][kp] = src [K][ny] transposed (conjugated when conj), zero padded
 void launch_transpose_fy(const float2* fy, int K, int ny, int kp, int nyp, float2* fyT,
-                         cudaStream_t s);
+                         cudaStream_t s, bool conj = false);
 // Build the real block forms of Fx (forward, conj=0) or conj(Fx) (inverse, conj=1).
 void launch_pack_fx(const float2* fx, int K, int nx, int kp, int nxp, int inverse,
                     int prec, void* hi, void* lo, cudaStream_t s);
@@ -140,11 +154,22 @@ void launch_field_planes(const float* phi, const float* amp, int nx, int ny, int
 // ---------------------------------------------------------------- kernels (k_simt.cu)
 void launch_field_f32(const float* phi, const float* amp, int nx, int ny, float2* e,
                       cudaStream_t s);
+// Element counts of the SimtWork buffers for a plan (rows = the longest inverse
+// contraction the plan runs, K or the separable form's uy).
+struct SimtSizes {
+  size_t p32, fxT, fyT, fws, cnt;
+  int fwd_tiles;
+};
+SimtSizes simt_sizes(int nx, int ny, int K, int rows);
+int simt_ldk(int K);   // row pitch of the transposed FP32 inverse operands
+
 void launch_fwd_simt(const float2* e32, const float2* fx, const float2* fy, int nx, int ny, int K,
-                     int kp, float2* part, const int* done, cudaStream_t s);
-int simt_fwd_tiles(int ny);
-void launch_bwd_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,
-                     const float* amp, float* phi, float2* e32, const int* done, cudaStream_t s);
+                     int kp, float2* part, const int* done, const SimtWork& w, cudaStream_t s);
+int simt_fwd_tiles(int ny);   // partial Theta rows the forward writes
+// Inverse product from the transposed operands fxT = conj(Fx)^T [nx][ldk], fyT = Fy^T [ny][ldk].
+void launch_bwd_simt(const float2* c, const float2* fxT, const float2* fyT, int nx, int ny, int K,
+                     const float* amp, float* phi, float2* e32, const int* done,
+                     const SimtWork& w, cudaStream_t s);
 // Separable grid form (foci on a grid of ux distinct x and uy distinct y values):
 // gt[ix][n] = sum_m E[n][m] Fxu[ix][m]; Theta_k = sum_n Fyu[iy_k][n] gt[ix_k][n];
 // tconj[iy][m] = conj(sum_{k in row iy} c_k conj(Fxu[ix_k][m])).
@@ -157,9 +182,9 @@ void launch_sep_theta(float2* gt, const float2* fyu, const int2* ixy, int K, int
                       int parts, float2* part, cudaStream_t s);
 void launch_sep_t(const float2* c, const float2* fxu, const int2* ixy, const int* row_ptr,
                   const int* row_foci, int uy, int nx, float2* tconj, cudaStream_t s);
-void launch_grad_simt(const float2* c, const float2* fx, const float2* fy, int nx, int ny, int K,
+void launch_grad_simt(const float2* c, const float2* fxT, const float2* fyT, int nx, int ny, int K,
                       const float* phi, const float* amp, float amp_factor,
-                      const OfaDevState* st, float* grad, cudaStream_t s);
+                      const OfaDevState* st, float* grad, const SimtWork& w, cudaStream_t s);
 
 // ---------------------------------------------------------------- kernels (k_focal.cu)
 // mode 0: loop iteration (record xi, threshold test, weight update, c)
