@@ -464,9 +464,10 @@ def main():
                          "parallelism": f"replicas x{world}",
                          "kernels": kernel_config},
               "roofline": roofline, "clocks": clocks}
-    # fp32: forward, focal, inverse; tensor-core forms: forward (+ fused focal step up
-    # to 4096 foci, else a separate focal kernel), inverse operand build, inverse
-    kernels_per_iter = 3 if (args.precision == "fp32" or w.n_foci <= 4096) else 4
+    # fp32: forward, focal, inverse operand build, inverse; tensor-core forms: forward
+    # (+ fused focal step up to 4096 foci, else a separate focal kernel), inverse
+    # operand build, inverse
+    kernels_per_iter = 4 if (args.precision == "fp32" or w.n_foci > 4096) else 3
     result["gpu_launches"] = args.steps * (n_iter * kernels_per_iter + 1)
 
     if rank == 0 and not args.no_e2e:

@@ -216,8 +216,10 @@ ofa_status ofa_adjoint(ofa_plan* plan, const float* phi, const float* theta,
  *   ms_out[0] forward product (+ per-focus dot; in the tensor-core forms also the
  *   focal statistics and weight update, which run in its last CTA), ms_out[1] focal
  *   statistics and weight update as a separate kernel (0 for the tensor-core forms),
- *   ms_out[2] inverse left-operand build (0 for OFA_PREC_FP32), ms_out[3] inverse
- *   product (+ phase projection).
+ *   ms_out[2] inverse left-operand build (P = conj(Fy)^T diag(c): the split operand
+ *   planes of the tensor-core forms, the FP32 conj(Fy)^T c of OFA_PREC_FP32; the
+ *   separable form's first inverse product), ms_out[3] inverse product (+ phase
+ *   projection).
  * The loop state (phi, w, j, xi history) is saved before and restored after, so
  * the call does not change the result of later iterations.  Synchronises.
  */

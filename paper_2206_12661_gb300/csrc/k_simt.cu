@@ -237,18 +237,16 @@ __global__ void __launch_bounds__(SIMT_THREADS, 4) fwd_simt_kernel(
 }
 
 // pT[n][k] = conj(FyT[n][k]) c_k: the inverse's left operand, rows n, contraction
-// k < K, row pitch ldk (the padding columns are zero).
+// k < K, row pitch ldk (the padding columns are zero).  Block (column chunk, row n).
 __global__ void scale_conj_kernel(const float2* __restrict__ fyT, const float2* __restrict__ c,
-                                  int K, int ldk, int ny, float2* __restrict__ pT,
+                                  int K, int ldk, float2* __restrict__ pT,
                                   const int* __restrict__ done) {
   if (done != nullptr && *done) return;
-  const size_t n = (size_t)ldk * ny;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(i % ldk);
-    const float2 a = fyT[i], ck = k < K ? c[k] : make_float2(0.f, 0.f);
-    pT[i] = make_float2(a.x * ck.x + a.y * ck.y, a.x * ck.y - a.y * ck.x);
-  }
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ldk) return;
+  const size_t i = (size_t)blockIdx.y * ldk + k;
+  const float2 a = fyT[i], ck = k < K ? c[k] : make_float2(0.f, 0.f);
+  pT[i] = make_float2(a.x * ck.x + a.y * ck.y, a.x * ck.y - a.y * ck.x);
 }
 
 // Inverse tile: rows n, columns m, contraction k over this block's part of it:
@@ -495,10 +493,8 @@ void launch_sep_t(const float2* c, const float2* fxu, const int2* ixy, const int
 void launch_scale_conj(const float2* c, const float2* fyT, int ny, int K, float2* pT,
                        const int* done, cudaStream_t s) {
   const int ldk = simt_ldk(K);
-  const size_t n = (size_t)ldk * ny;
-  size_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  scale_conj_kernel<<<(unsigned)blocks, 256, 0, s>>>(fyT, c, K, ldk, ny, pT, done);
+  dim3 grid((ldk + 255) / 256, ny);
+  scale_conj_kernel<<<grid, 256, 0, s>>>(fyT, c, K, ldk, pT, done);
 }
 
 // The inverse product; its contraction parts (grid z) form one cluster per tile.
@@ -522,11 +518,17 @@ void launch_bwd_kernel(const float2* pT, const float2* fxT, int nx, int ny, int 
                      phi_in, amp, amp_factor, st, done);
 }
 
+void launch_bwd_simt_product(const float2* fxT, int nx, int ny, int K, const float* amp,
+                             float* phi, float2* e32, const int* done, const SimtWork& w,
+                             cudaStream_t s) {
+  launch_bwd_kernel<0>(w.p32, fxT, nx, ny, K, phi, e32, nullptr, amp, 0.f, nullptr, done, s);
+}
+
 void launch_bwd_simt(const float2* c, const float2* fxT, const float2* fyT, int nx, int ny, int K,
                      const float* amp, float* phi, float2* e32, const int* done,
                      const SimtWork& w, cudaStream_t s) {
   launch_scale_conj(c, fyT, ny, K, w.p32, done, s);
-  launch_bwd_kernel<0>(w.p32, fxT, nx, ny, K, phi, e32, nullptr, amp, 0.f, nullptr, done, s);
+  launch_bwd_simt_product(fxT, nx, ny, K, amp, phi, e32, done, w, s);
 }
 
 void launch_grad_simt(const float2* c, const float2* fxT, const float2* fyT, int nx, int ny,

@@ -1081,13 +1081,14 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
                                  p->tconj, s);
         else if (tc) launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision,
                                     p->tc.p_hi, p->tc.p_lo, s);
+        else launch_scale_conj(p->c, p->simt.fyT, p->ny, p->K, p->simt.p32, nullptr, s);
         break;
       default:
         if (p->sep) launch_bwd_simt(p->ones, sep_fxT(p, s), p->simt.fyT, p->nx, p->ny, p->uy, p->amp,
                                     p->phi, p->e32, nullptr, p->simt, s);
         else if (tc) launch_bwd_tc(p, p->tc, nullptr, s);
-        else launch_bwd_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
-                             nullptr, p->simt, s);
+        else launch_bwd_simt_product(p->simt.fxT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
+                                     nullptr, p->simt, s);
         break;
     }
   };
@@ -1095,7 +1096,7 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
   for (int which = 0; which < 4; ++which) {
-    if ((which == 2 && !tc && !p->sep) || (which == 1 && tc && p->K <= 4096)) {
+    if (which == 1 && tc && p->K <= 4096) {
       ms_out[which] = 0.0;
       continue;
     }

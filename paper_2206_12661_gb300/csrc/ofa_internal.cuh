@@ -166,7 +166,15 @@ int simt_ldk(int K);   // row pitch of the transposed FP32 inverse operands
 void launch_fwd_simt(const float2* e32, const float2* fx, const float2* fy, int nx, int ny, int K,
                      int kp, float2* part, const int* done, const SimtWork& w, cudaStream_t s);
 int simt_fwd_tiles(int ny);   // partial Theta rows the forward writes
-// Inverse product from the transposed operands fxT = conj(Fx)^T [nx][ldk], fyT = Fy^T [ny][ldk].
+// The inverse's left operand w.p32 = conj(fyT) c (the FP32 counterpart of build_p).
+void launch_scale_conj(const float2* c, const float2* fyT, int ny, int K, float2* pT,
+                       const int* done, cudaStream_t s);
+// The inverse product alone, from w.p32 and fxT.
+void launch_bwd_simt_product(const float2* fxT, int nx, int ny, int K, const float* amp,
+                             float* phi, float2* e32, const int* done, const SimtWork& w,
+                             cudaStream_t s);
+// Inverse product from the transposed operands fxT = conj(Fx)^T [nx][ldk], fyT = Fy^T [ny][ldk]
+// (launch_scale_conj, then launch_bwd_simt_product).
 void launch_bwd_simt(const float2* c, const float2* fxT, const float2* fyT, int nx, int ny, int K,
                      const float* amp, float* phi, float2* e32, const int* done,
                      const SimtWork& w, cudaStream_t s);
