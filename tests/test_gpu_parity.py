@@ -150,6 +150,46 @@ def test_one_step_from_same_iterate(ofa, dev, prec):
     assert phi_g.min() >= -np.pi and phi_g.max() <= np.pi
 
 
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_one_step_split_contraction_ragged(ofa, dev, prec):
+    """One iteration from the oracle's iterate on a ragged 333 x 250 pupil with 300 foci.
+
+    The FP32 products split both contractions here (333 -> 4 parts over m, 300 -> 4
+    parts over k: last-arrival reduction in the forward, cluster reduction in the
+    inverse) and every tile is ragged, odd nx taking the scalar stores."""
+    w = custom(333, 250, 300, seed=21, targets="random")
+    fx, fy = oracle_mats(w)
+    run = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, 4)
+    phi_j = run["phi"].astype(np.float32)
+    w_j = run["w"].astype(np.float32)
+    theta, w_new, back = one_step_reference(w, phi_j.astype(np.float64), w_j.astype(np.float64),
+                                            fx, fy)
+    plan = ofa.Plan.from_workload(w, precision=prec)
+    plan.set_state(phi_j, w_j, 4)
+    plan.iterate(1)
+    phi_g, w_g, j = plan.get_state()
+    plan.close()
+    assert j == 5
+    wrel = np.linalg.norm(w_g - w_new) / np.linalg.norm(w_new)
+    assert wrel < 20 * AMP_TOL[prec], wrel
+    mag = np.abs(back)
+    d = np.abs(np.exp(1j * phi_g) - np.exp(1j * np.angle(back)))
+    werr = math.sqrt(np.sum((mag * d) ** 2) / np.sum(mag ** 2))
+    assert werr < 20 * AMP_TOL[prec], werr
+
+
+def test_deterministic_split_contraction(ofa, dev):
+    """FP32 with both contractions split: repeated runs agree bit for bit."""
+    w = custom(333, 250, 300, seed=22)
+    outs = []
+    for _ in range(2):
+        p = ofa.Plan.from_workload(w, precision="fp32")
+        p.iterate(6)
+        outs.append(p.phase())
+        p.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
 @pytest.mark.parametrize("prec", ALL)
 def test_full_run_grid100(ofa, dev, prec):
     w = I.named("pupil256_grid100_uniform")
