@@ -171,8 +171,17 @@ ofa_status ofa_iterate_measured(ofa_plan* plan, const float* measured, int mem_s
  * out_mem_space.  Synchronises the plan's stream for host output. */
 ofa_status ofa_get_phase(const ofa_plan* plan, float* phi_out, int out_mem_space);
 
-/* Release every resource of the plan.  NULL-safe. */
+/* Release every resource of the plan.  NULL-safe.  The plan's device buffers live
+ * in one allocation; the library keeps the last one released on each device (the
+ * larger, if it already holds one), and the pinned state mirror, for the next plan
+ * of similar size to reuse, so a create/destroy loop allocates once.  ofa_trim
+ * frees what is kept. */
 ofa_status ofa_destroy(ofa_plan* plan);
+
+/* Free the device and pinned host memory that destroyed plans left for reuse on the
+ * current device (at most one plan arena and one state mirror).  Plans still alive
+ * are not affected.  OFA_OK, or OFA_ERR_CUDA if a free fails. */
+ofa_status ofa_trim(void);
 
 /* Statistics of one forward at the current phase (runs that forward; host output). */
 ofa_status ofa_get_stats(ofa_plan* plan, ofa_stats* stats);

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -57,6 +58,109 @@ cudaError_t dalloc(T** p, size_t count) {
   return e;
 }
 
+// Per-device reuse of what plan creation and destruction cost most on the host:
+// the device attributes, the kernels' shared-memory opt-in (once per precision),
+// one plan arena and one pinned state mirror.  A process that creates and
+// destroys plans in a loop then calls cudaMalloc / cudaMallocHost once; ofa_trim
+// releases the cached memory.
+struct DeviceCache {
+  bool attrs = false;
+  int cc = 0, sms = 0;
+  unsigned prepared = 0;   // bit per precision: kernel attributes set
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  OfaDevState* st_host = nullptr;
+};
+constexpr int OFA_MAX_DEVICES = 64;
+std::mutex g_cache_mu;
+DeviceCache g_cache[OFA_MAX_DEVICES];
+
+cudaError_t device_attrs(int dev, int* cc, int* sms) {
+  if (dev >= 0 && dev < OFA_MAX_DEVICES) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (g_cache[dev].attrs) {
+      *cc = g_cache[dev].cc;
+      *sms = g_cache[dev].sms;
+      return cudaSuccess;
+    }
+  }
+  int major = 0, minor = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  *cc = major * 10 + minor;
+  if (dev >= 0 && dev < OFA_MAX_DEVICES) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_cache[dev].attrs = true;
+    g_cache[dev].cc = *cc;
+    g_cache[dev].sms = *sms;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t prepare_precision(int dev, int prec) {
+  const bool cacheable = dev >= 0 && dev < OFA_MAX_DEVICES && prec >= 0 && prec < 32;
+  if (cacheable) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (g_cache[dev].prepared & (1u << prec)) return cudaSuccess;
+  }
+  cudaError_t e = tc_prepare(prec);
+  if (e == cudaSuccess && cacheable) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_cache[dev].prepared |= 1u << prec;
+  }
+  return e;
+}
+
+// A cached arena of at least `bytes` (and not more than four times that), or null.
+void* take_cached_arena(int dev, size_t bytes, size_t* got) {
+  if (dev < 0 || dev >= OFA_MAX_DEVICES) return nullptr;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  DeviceCache& c = g_cache[dev];
+  if (!c.arena || c.arena_bytes < bytes || c.arena_bytes / 4 > bytes) return nullptr;
+  void* a = c.arena;
+  *got = c.arena_bytes;
+  c.arena = nullptr;
+  c.arena_bytes = 0;
+  return a;
+}
+
+// Keep a destroyed plan's arena for the next plan (the larger of it and the one
+// already kept); free the other.  The plan's stream has been synchronised.
+void give_back_arena(int dev, void* arena, size_t bytes) {
+  void* drop = arena;
+  if (dev >= 0 && dev < OFA_MAX_DEVICES) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    DeviceCache& c = g_cache[dev];
+    if (!c.arena || c.arena_bytes < bytes) {
+      drop = c.arena;
+      c.arena = arena;
+      c.arena_bytes = bytes;
+    }
+  }
+  if (drop) cudaFree(drop);
+}
+
+OfaDevState* take_cached_st_host(int dev) {
+  if (dev < 0 || dev >= OFA_MAX_DEVICES) return nullptr;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  OfaDevState* h = g_cache[dev].st_host;
+  g_cache[dev].st_host = nullptr;
+  return h;
+}
+
+void give_back_st_host(int dev, OfaDevState* h) {
+  if (dev >= 0 && dev < OFA_MAX_DEVICES) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (!g_cache[dev].st_host) {
+      g_cache[dev].st_host = h;
+      return;
+    }
+  }
+  cudaFreeHost(h);
+}
+
 cudaError_t arena_commit(ofa_plan* p, const std::vector<ArenaReq>& reqs) {
   std::vector<size_t> off(reqs.size());
   size_t total = 0;
@@ -65,10 +169,17 @@ cudaError_t arena_commit(ofa_plan* p, const std::vector<ArenaReq>& reqs) {
     off[i] = total;
     total += reqs[i].bytes;
   }
-  void* base = nullptr;
-  cudaError_t e = cudaMalloc(&base, total ? total : 256);
-  if (e != cudaSuccess) return e;
+  if (total == 0) total = 256;
+  size_t bytes = 0;
+  void* base = take_cached_arena(p->device, total, &bytes);
+  if (!base) {
+    cudaError_t e = cudaMalloc(&base, total);
+    if (e != cudaSuccess) return e;
+    bytes = total;
+  }
   p->arena = base;
+  p->arena_bytes = bytes;
+  cudaError_t e = cudaSuccess;
   for (size_t i = 0; i < reqs.size(); ++i) {
     *reqs[i].slot = static_cast<uint8_t*>(base) + off[i];
     p->arena_slots.push_back(reqs[i].slot);
@@ -402,10 +513,11 @@ ofa_status ofa_destroy(ofa_plan* p) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
-  if (p->stream || p->own_stream) cudaStreamSynchronize(p->stream);
+  // the plan's work must be finished before its arena is handed to another plan
+  cudaStreamSynchronize(p->stream);
   destroy_graphs(p);
   if (p->arena) {
-    cudaFree(p->arena);
+    give_back_arena(p->device, p->arena, p->arena_bytes);
     for (void** slot : p->arena_slots) *slot = nullptr;
     p->arena = nullptr;
   }
@@ -415,7 +527,7 @@ ofa_status ofa_destroy(ofa_plan* p) {
                   p->meas,     p->fxu,   p->fyu,   p->gt,    p->tconj, p->ones, p->ixy,
                   p->row_ptr,  p->row_foci};
   for (void* b : bufs) dfree(b);
-  if (p->st_host) cudaFreeHost(p->st_host);
+  if (p->st_host) give_back_st_host(p->device, p->st_host);
   free_tc(p->tc);
   if (p->aux_ready) {
     dfree(p->tc_aux.e_hi);
@@ -504,13 +616,13 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "cudaGetDevice");
-  cudaDeviceProp prop;
-  e = cudaGetDeviceProperties(&prop, dev);
-  if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "cudaGetDeviceProperties");
-  if (prop.major * 10 + prop.minor != 103)
+  int cc = 0, sm_count = 0;
+  e = device_attrs(dev, &cc, &sm_count);
+  if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "cudaDeviceGetAttribute");
+  if (cc != 103)
     return ofa_fail(nullptr, OFA_ERR_UNSUPPORTED,
                     "this library is built for sm_103a (GB300) only; device is sm_" +
-                        std::to_string(prop.major * 10 + prop.minor));
+                        std::to_string(cc));
 
   ofa_plan* p = new ofa_plan();
   p->device = dev;
@@ -608,7 +720,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     if (p->sep) {
       R(dalloc(&p->fxu, (size_t)p->ux * nx));
       R(dalloc(&p->fyu, (size_t)p->uy * ny));
-      p->sep_parts = sep_parts(nx, ny, p->ux, prop.multiProcessorCount);
+      p->sep_parts = sep_parts(nx, ny, p->ux, sm_count);
       R(dalloc(&p->gt, (size_t)p->sep_parts * p->ux * ny));
       R(dalloc(&p->tconj, (size_t)p->uy * nx));
       R(dalloc(&p->ones, (size_t)p->uy));
@@ -639,8 +751,10 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     OFA_TRY(re, "alloc");
   }
   OFA_TRY(arena_commit(p, reqs), "alloc");
-  OFA_TRY(cudaMallocHost(reinterpret_cast<void**>(&p->st_host), sizeof(OfaDevState)),
-          "pinned alloc");
+  p->st_host = take_cached_st_host(dev);
+  if (!p->st_host)
+    OFA_TRY(cudaMallocHost(reinterpret_cast<void**>(&p->st_host), sizeof(OfaDevState)),
+            "pinned alloc");
   if (p->sep) {
     std::vector<int2> ixy(n_foci);
     std::vector<int> count(p->uy + 1, 0), order(n_foci);
@@ -757,8 +871,8 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
                    p->stream);
     launch_field_planes(p->phi, p->amp, nx, ny, p->nxp, p->precision, p->tc.e_hi, p->tc.e_lo,
                         p->stream);
-    OFA_TRY(tc_prepare(p->precision), "setting kernel shared-memory attributes");
-    choose_tiles(p, p->tc, prop.multiProcessorCount);
+    OFA_TRY(prepare_precision(dev, p->precision), "setting kernel shared-memory attributes");
+    choose_tiles(p, p->tc, sm_count);
     std::string err;
     if (opt.autotune) {
       OFA_TRY(cudaStreamSynchronize(p->stream), "plan set-up");
@@ -1175,6 +1289,29 @@ ofa_status ofa_batch_create(ofa_batch** out, ofa_plan* const* plans, int count, 
     cudaStreamSynchronize(b->cap_stream);
   }
   *out = b;
+  return OFA_OK;
+}
+
+ofa_status ofa_trim(void) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "cudaGetDevice");
+  void* arena = nullptr;
+  OfaDevState* h = nullptr;
+  if (dev >= 0 && dev < OFA_MAX_DEVICES) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    arena = g_cache[dev].arena;
+    h = g_cache[dev].st_host;
+    g_cache[dev].arena = nullptr;
+    g_cache[dev].arena_bytes = 0;
+    g_cache[dev].st_host = nullptr;
+  }
+  if (arena) e = cudaFree(arena);
+  if (h) {
+    const cudaError_t e2 = cudaFreeHost(h);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "releasing cached memory");
   return OFA_OK;
 }
 

@@ -124,6 +124,7 @@ struct ofa_plan {
   int chunk_iters = 16;
 
   void* arena = nullptr;               // one allocation holding the buffers above
+  size_t arena_bytes = 0;
   std::vector<void**> arena_slots;     // the pointers carved out of it
   double* sep_coord = nullptr;         // separable form: distinct coordinates (set-up)
 

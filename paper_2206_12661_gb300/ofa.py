@@ -76,6 +76,7 @@ SIGNATURES = [
     ("ofa_batch_destroy", _I, [_P]),
     ("ofa_batch_info", _I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     ("ofa_selftest_bounded_wait", _I, []),
+    ("ofa_trim", _I, []),
     ("ofa_iterate_measured", _I, [_P, _P, _I, C.POINTER(_D)]),
     ("ofa_plan_form", _I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     ("ofa_forward_noalloc", _I, [_I, _I, _D, _D, _D, _D, _I, _P, _P, _P, _P, _P, _P]),
@@ -253,6 +254,11 @@ def ofa_batch_iterate(batch, n_iter: int):
 
 def ofa_batch_destroy(batch):
     _check(_lib.ofa_batch_destroy(batch))
+
+
+def ofa_trim():
+    """Free the memory that destroyed plans left for reuse on the current device."""
+    _check(_lib.ofa_trim())
 
 
 def ofa_selftest_bounded_wait() -> int:
