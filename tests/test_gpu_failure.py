@@ -64,3 +64,31 @@ def test_allocation_failure_is_reported_and_cleaned_up(ofa, dev, n, prec):
     phase = p.phase()
     p.close()
     assert np.isfinite(phase).all()
+
+
+def test_destroyed_plan_memory_is_kept_for_reuse_and_trim_releases_it(ofa, dev):
+    """ofa_destroy keeps the plan's arena for the next plan; ofa_trim frees it."""
+    w = I.named("pupil1024_poisson1000")
+    ofa.ofa_trim()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    p = ofa.Plan.from_workload(w, precision="f16x3")
+    p.iterate(2)
+    phase_a = p.phase()
+    p.close()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 > (32 << 20), (free0, free1)    # the arena (~75 MB) is kept
+    # a second plan of the same shape reuses it: no further device memory, same result
+    q = ofa.Plan.from_workload(w, precision="f16x3")
+    torch.cuda.synchronize()
+    free2, _ = torch.cuda.mem_get_info()
+    q.iterate(2)
+    phase_b = q.phase()
+    q.close()
+    assert abs(free2 - free1) < (8 << 20), (free1, free2)
+    assert np.array_equal(phase_a, phase_b)
+    ofa.ofa_trim()
+    torch.cuda.synchronize()
+    free3, _ = torch.cuda.mem_get_info()
+    assert abs(free3 - free0) < (8 << 20), (free0, free3)
