@@ -237,16 +237,29 @@ __global__ void __launch_bounds__(SIMT_THREADS, 4) fwd_simt_kernel(
 }
 
 // pT[n][k] = conj(FyT[n][k]) c_k: the inverse's left operand, rows n, contraction
-// k < K, row pitch ldk (the padding columns are zero).  Block (column chunk, row n).
+// k < K, row pitch ldk (a multiple of 16; the padding columns are zero).  Each
+// thread handles four consecutive k of one row (two 16-byte loads and stores).
 __global__ void scale_conj_kernel(const float2* __restrict__ fyT, const float2* __restrict__ c,
-                                  int K, int ldk, float2* __restrict__ pT,
+                                  int K, int ldk, int ny, float2* __restrict__ pT,
                                   const int* __restrict__ done) {
   if (done != nullptr && *done) return;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= ldk) return;
-  const size_t i = (size_t)blockIdx.y * ldk + k;
-  const float2 a = fyT[i], ck = k < K ? c[k] : make_float2(0.f, 0.f);
-  pT[i] = make_float2(a.x * ck.x + a.y * ck.y, a.x * ck.y - a.y * ck.x);
+  const int q = ldk / 4;   // quads per row
+  const size_t n_quads = (size_t)q * ny;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n_quads;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int k0 = (int)(i % q) * 4;
+    const float4* src = reinterpret_cast<const float4*>(fyT) + 2 * i;
+    float4* dst = reinterpret_cast<float4*>(pT) + 2 * i;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float4 a = src[h];
+      const int k = k0 + 2 * h;
+      const float2 c0 = k < K ? c[k] : make_float2(0.f, 0.f);
+      const float2 c1 = k + 1 < K ? c[k + 1] : make_float2(0.f, 0.f);
+      dst[h] = make_float4(a.x * c0.x + a.y * c0.y, a.x * c0.y - a.y * c0.x,
+                           a.z * c1.x + a.w * c1.y, a.z * c1.y - a.w * c1.x);
+    }
+  }
 }
 
 // Inverse tile: rows n, columns m, contraction k over this block's part of it:
@@ -493,8 +506,10 @@ void launch_sep_t(const float2* c, const float2* fxu, const int2* ixy, const int
 void launch_scale_conj(const float2* c, const float2* fyT, int ny, int K, float2* pT,
                        const int* done, cudaStream_t s) {
   const int ldk = simt_ldk(K);
-  dim3 grid((ldk + 255) / 256, ny);
-  scale_conj_kernel<<<grid, 256, 0, s>>>(fyT, c, K, ldk, pT, done);
+  const size_t quads = (size_t)(ldk / 4) * ny;
+  size_t blocks = (quads + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  scale_conj_kernel<<<(unsigned)blocks, 256, 0, s>>>(fyT, c, K, ldk, ny, pT, done);
 }
 
 // The inverse product; its contraction parts (grid z) form one cluster per tile.
