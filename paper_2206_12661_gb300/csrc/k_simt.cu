@@ -482,8 +482,8 @@ int sep_parts(int nx, int ny, int ux, int sms) {
 void launch_sep_forward(const float2* e32, const float2* fxu, int nx, int ny, int ux, int parts,
                         float2* gt, cudaStream_t s) {
   dim3 grid((ux + T64 - 1) / T64, (ny + T64 - 1) / T64, parts);
-  fwd_simt_kernel<true><<<grid, SIMT_THREADS, 0, s>>>(e32, fxu, nullptr, nx, ny, ux, ux, gt, nullptr,
-                                                      nullptr, nullptr);
+  fwd_simt_kernel<true><<<grid, SIMT_THREADS, 0, s>>>(e32, fxu, nullptr, nx, ny, ux, ux, gt,
+                                                      nullptr, nullptr, nullptr);
 }
 
 void launch_sep_theta(float2* gt, const float2* fyu, const int2* ixy, int K, int ny, int ux,

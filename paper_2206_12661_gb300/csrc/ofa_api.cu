@@ -276,11 +276,17 @@ int* done_ptr(ofa_plan* p) { return &p->st->done; }
 // One iteration of Algorithm 1 on stream s.
 // Separable grid form: the forward through the distinct x (G = E Fxu^T, then
 // Theta_k = Fyu[iy_k] . G[:, ix_k]) into the single partial row.
-// FP32 inverse operands of the separable form: the conjugate of the first inverse
-// product, transposed, [nx][ldk] (Fyu^T is formed once per plan).
-const float2* sep_fxT(ofa_plan* p, cudaStream_t s) {
+// FP32 inverse operand of the separable form: the conjugate of the first inverse
+// product, transposed, into p->simt.fxT [nx][ldk] (Fyu^T is formed once per plan).
+void sep_transpose_t(ofa_plan* p, cudaStream_t s) {
   launch_transpose_fy(p->tconj, p->uy, p->nx, simt_ldk(p->uy), p->nx, p->simt.fxT, s, true);
-  return p->simt.fxT;
+}
+
+// Separable form, second inverse product fused with the phase projection.
+void enqueue_sep_inverse(ofa_plan* p, const int* done, cudaStream_t s) {
+  sep_transpose_t(p, s);
+  launch_bwd_simt(p->ones, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->uy, p->amp, p->phi, p->e32,
+                  done, p->simt, s);
 }
 
 void enqueue_sep_forward(ofa_plan* p, const float2* e32, cudaStream_t s) {
@@ -295,13 +301,13 @@ void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
     launch_focal(p->part, 1, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist, p->st,
                  0, p->weighting, 1.f, p->amp_energy, s);
     launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj, s);
-    launch_bwd_simt(p->ones, sep_fxT(p, s), p->simt.fyT, p->nx, p->ny, p->uy, p->amp, p->phi, p->e32, done, p->simt,
-                    s);
+    enqueue_sep_inverse(p, done, s);
   } else if (!use_tc(p)) {
     launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, done, p->simt, s);
     launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
                  p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
-    launch_bwd_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32, done, p->simt, s);
+    launch_bwd_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
+                    done, p->simt, s);
   } else {
     // up to 4096 foci the focal step runs in the forward kernel's last CTA
     const bool fuse = p->K <= 4096;
@@ -321,7 +327,8 @@ void enqueue_forward_current(ofa_plan* p, cudaStream_t s) {
     launch_focal(p->part, 1, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist, p->st,
                  1, p->weighting, ldexpf(1.f, p->amp_exp), p->amp_energy, s);
   } else if (!use_tc(p)) {
-    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, p->simt, s);
+    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, p->simt,
+                    s);
     launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
                  p->c, p->hist, p->st, 1, p->weighting, ldexpf(1.f, p->amp_exp), p->amp_energy,
                  s);
@@ -979,18 +986,20 @@ ofa_status ofa_iterate_measured(ofa_plan* p, const float* measured, int mem_spac
   const int n_part = p->sep ? 1 : use_tc(p) ? fwd_n_part(p->nyp, p->tc) : simt_fwd_tiles(p->ny);
   if (p->sep) enqueue_sep_forward(p, p->e32, s);
   else if (use_tc(p)) launch_fwd_tc(p, p->tc, nullptr, s, false);
-  else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, p->simt, s);
+  else
+    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, p->simt,
+                    s);
   launch_focal_measured(p->part, n_part, p->kp, p->K, p->t, p->w, p->theta, p->c, p->hist, p->st,
                         p->weighting, p->meas, s);
   if (p->sep) {
     launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj, s);
-    launch_bwd_simt(p->ones, sep_fxT(p, s), p->simt.fyT, p->nx, p->ny, p->uy, p->amp, p->phi, p->e32,
-                    nullptr, p->simt, s);
+    enqueue_sep_inverse(p, nullptr, s);
   } else if (use_tc(p)) {
     launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
     launch_bwd_tc(p, p->tc, nullptr, s);
   } else {
-    launch_bwd_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32, nullptr, p->simt, s);
+    launch_bwd_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
+                    nullptr, p->simt, s);
   }
   ofa_status st = sync_and_check(p);
   if (st != OFA_OK) return st;
@@ -1126,11 +1135,12 @@ ofa_status ofa_adjoint(ofa_plan* p, const float* phi, const float* theta,
   if (p->sep) {
     launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj,
                  p->stream);
-    launch_grad_simt(p->ones, sep_fxT(p, p->stream), p->simt.fyT, p->nx, p->ny, p->uy, phi, p->amp, amp_factor,
-                     p->st, grad_phi, p->simt, p->stream);
+    sep_transpose_t(p, p->stream);
+    launch_grad_simt(p->ones, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->uy, phi, p->amp,
+                     amp_factor, p->st, grad_phi, p->simt, p->stream);
   } else if (!use_tc(p)) {
-    launch_grad_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, phi, p->amp, amp_factor, p->st,
-                     grad_phi, p->simt, p->stream);
+    launch_grad_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, phi, p->amp,
+                     amp_factor, p->st, grad_phi, p->simt, p->stream);
   } else {
     launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo,
                    p->stream);
@@ -1181,8 +1191,8 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
       case 0:
         if (p->sep) enqueue_sep_forward(p, p->e32, s);
         else if (tc) launch_fwd_tc(p, p->tc, nullptr, s, p->K <= 4096);  // + fused focal step
-        else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, p->simt,
-                             s);
+        else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr,
+                             p->simt, s);
         break;
       case 1:
         if (tc && p->K <= 4096) break;  // fused into the forward kernel
@@ -1198,8 +1208,7 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
         else launch_scale_conj(p->c, p->simt.fyT, p->ny, p->K, p->simt.p32, nullptr, s);
         break;
       default:
-        if (p->sep) launch_bwd_simt(p->ones, sep_fxT(p, s), p->simt.fyT, p->nx, p->ny, p->uy, p->amp,
-                                    p->phi, p->e32, nullptr, p->simt, s);
+        if (p->sep) enqueue_sep_inverse(p, nullptr, s);
         else if (tc) launch_bwd_tc(p, p->tc, nullptr, s);
         else launch_bwd_simt_product(p->simt.fxT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
                                      nullptr, p->simt, s);

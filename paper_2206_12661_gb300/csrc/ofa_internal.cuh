@@ -64,7 +64,7 @@ struct TcOperands {
 struct SimtWork {
   // pitch simt_ldk(contraction length), zero padded:
   float2* p32 = nullptr;      // [ny][ldk] conj(Fy[k,n]) c_k
-  float2* fxT = nullptr;      // [nx][ldk] conj(Fx)^T (separable: conj of the first inverse product^T)
+  float2* fxT = nullptr;      // [nx][ldk] conj(Fx)^T (separable: of the first inverse product)
   float2* fyT = nullptr;      // [ny][ldk] Fy^T (separable form: Fyu^T)
   float2* fws = nullptr;      // forward: [fwd_tiles][parts][64] partial per-focus dots
   unsigned* cnt = nullptr;    // forward: [fwd_tiles] arrival counters
