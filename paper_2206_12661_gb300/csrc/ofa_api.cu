@@ -17,6 +17,7 @@
 #include <string>
 #include <vector>
 
+#include "ofa_host.h"
 #include "ofa_internal.cuh"
 
 namespace {
@@ -835,14 +836,9 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     av = ah.data();
   }
   double amax = 0.0, energy = 0.0;
-  for (size_t i = 0; i < npix; ++i) {
-    const double a = av[i];
-    if (!std::isfinite(a) || a < 0.0) {
-      p->last_error = "amplitude must be finite and >= 0";
-      return fail(OFA_ERR_INVALID_ARG);
-    }
-    amax = std::fmax(amax, a);
-    energy += a * a;
+  if (!ofa_host::amplitude_stats(av, npix, &amax, &energy)) {
+    p->last_error = "amplitude must be finite and >= 0";
+    return fail(OFA_ERR_INVALID_ARG);
   }
   if (!(amax > 0.0)) {
     p->last_error = "amplitude is zero everywhere";
