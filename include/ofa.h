@@ -76,11 +76,11 @@ typedef struct ofa_options {
   int mem_space;             /* ofa_mem_space of focus_xy, target, amplitude and phi0 */
   int weighting;             /* 1 = generalized weighting of Algorithm 1 (default),
                                 0 = plain GS (w stays 1) */
-  int autotune;              /* tensor-core forms: 1 = time the candidate tile shapes,
-                                split-K factors and cluster multicast of both products
-                                at creation and keep the fastest (default; results are
-                                cached per device, size and precision for the process),
-                                0 = a static cost model */
+  int autotune;              /* tensor-core forms: 1 = time the candidate tile widths,
+                                split-K factors and CTA groups (single SMs or 2-SM pairs)
+                                of both products at creation and keep the fastest
+                                (default; results are cached per device, size and
+                                precision for the process), 0 = a static cost model */
   const double* focus_z;     /* [K] axial offsets z_k (m) of the foci from the focal plane
                                 (a 3D array), or NULL for z = 0.  Focus k's rows then carry
                                 the defocus phase of the pupil function, a Fresnel (paraxial)
@@ -98,6 +98,16 @@ typedef struct ofa_options {
                                 the precision.  -1 = when the work shrinks by more than
                                 20x for the tensor-core forms, 2x for FP32 (default),
                                 0 = never, 1 = always (OFA_ERR_UNSUPPORTED with focus_z) */
+  int kernel_config[5];      /* tensor-core forms: a fixed kernel configuration instead of
+                                the autotuner's choice, {forward tile width (128 or 256
+                                accumulator columns), forward split-K factor (1, 2 or 4),
+                                forward CTA group (1, or 2 for 2-SM pairs), inverse tile
+                                width (128 or 256), inverse CTA group (1 or 2)}.  All zero
+                                = chosen at creation (default).  A configuration these
+                                sizes cannot run (split-K beyond the contraction's
+                                k-blocks, 2-SM pairs over an odd number of 128-row tiles)
+                                -> OFA_ERR_UNSUPPORTED.  Ignored by the FP32 and separable
+                                forms. */
 } ofa_options;
 
 typedef struct ofa_stats {
@@ -152,7 +162,7 @@ ofa_status ofa_iterate(ofa_plan* plan, int n_iter, double threshold, int* iters_
 
 /*
  * ofa_iterate_measured -- one iteration in the camera-in-the-loop mode of the
- * paper's experiments (Sec. 3): once the intensity accuracy has passed a threshold
+ * paper's experiments (Results and discussion section): once the intensity accuracy has passed a threshold
  * (0.95 there), the calculated focus intensities are replaced by captured ones in
  * the weight update, w_j = w_{j-1} sqrt(I~ / I_meas) at unit sums; the focused field
  * keeps the phase of the calculated Theta (a camera records intensities only).
@@ -234,12 +244,12 @@ ofa_status ofa_adjoint(ofa_plan* plan, const float* phi, const float* theta,
  */
 ofa_status ofa_profile_kernels(ofa_plan* plan, int reps, double* ms_out);
 
-/* Kernel configuration chosen at creation (host output, 12 ints): forward tile width
- * (accumulator columns), forward split-K factor, forward multicast cluster shape x and
- * y, inverse tile width, inverse cluster shape x and y, 1 if the focal step runs in the
- * forward kernel's last CTA, forward and inverse operand row width per pipeline stage
- * (bytes of K), forward and inverse CTA group (1, or 2 for 2-SM MMA pairs of 256
- * accumulator rows).  The FP32 form reports zeros. */
+/* Kernel configuration of a plan (host output, 8 ints), in the order of
+ * ofa_options.kernel_config followed by three derived values: forward tile width
+ * (accumulator columns), forward split-K factor, forward CTA group (1, or 2 for 2-SM MMA
+ * pairs of 256 accumulator rows), inverse tile width, inverse CTA group, 1 if the focal
+ * step runs in the forward kernel's last CTA, forward and inverse operand row width per
+ * pipeline stage (bytes of K).  The FP32 and separable forms report zeros. */
 ofa_status ofa_plan_config(const ofa_plan* plan, int* config_out);
 
 /* Form of a plan: *separable = 1 with the U_x and U_y distinct focus coordinates it
@@ -292,9 +302,12 @@ ofa_status ofa_batch_info(const ofa_batch* batch, int* grouped, int* fwd_bn, int
  * Allocates nothing: its scratch is a 2 MiB static device array that every GPU
  * loading the library holds until the process exits.  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  All calls share the array, so calls that
- * overlap on the GPU race and must be serialised by the caller.  Enqueues only;
- * no synchronisation.
+ * call before any stream capture.  After a device reset the next call sees the new
+ * context and looks the address up again (again outside any capture).  All calls
+ * share the array, so calls that overlap on the GPU race and must be serialised by
+ * the caller.  A CUDA error left pending by earlier work is returned as
+ * OFA_ERR_CUDA (and cleared) before anything is launched.  Enqueues only; no
+ * synchronisation.
  */
 ofa_status ofa_forward_noalloc(int nx, int ny, double pitch_x, double pitch_y,
                                double wavelength, double focal_length, int n_foci,

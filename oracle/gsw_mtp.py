@@ -5,17 +5,19 @@ file and the CPU-baseline leg of the benchmark may import this module.  The
 CUDA library never calls it, and it shares no code, table or constant
 generator with the CUDA path.
 
-Everything here is plain complex128 numpy, written in the paper's order and
-notation so that a reader can check each step against the text by eye:
+Everything here is plain complex128 numpy in the paper's notation, one small
+function per quantity, so that a reader can check each against the text:
 
 * Eq. 1 / Eq. 2 -- far-field propagation written as a matrix triple product
-  Theta = Omega_y E Omega_x, evaluated only at the foci (the "identify and
-  remove zero elements" step of the method).  Per focus k this is
+  Theta = Omega_y E Omega_x, evaluated only at the foci (zero elements of the
+  focal plane removed).  Per focus k this is
   Theta_k = sum_n Fy[k,n] sum_m E[n,m] Fx[k,m] with
   Fx[k,m] = exp(-i 2 pi x_k u_m / (lambda f)) and Fy[k,n] likewise in y.
-* Algorithm 1 -- forward propagation, intensities, intensity accuracy xi,
-  generalized weighting w_j = w_{j-1} sqrt(I~/I), focused field
-  w_j sqrt(I~) exp(i arg Theta), inverse propagation, phase-only projection.
+* Results and discussion section -- the GSW weighting generalized to
+  nonuniform targets: one cycle (gsw_step) is forward operator, intensities,
+  intensity accuracy xi, weight update w sqrt(I~/I), focal amplitude
+  constraint w sqrt(I~) exp(i arg Theta), inverse operator, pupil amplitude
+  constraint (phase only); gsw() repeats it until xi passes a threshold.
 
 Readings where the paper is silent or loose (the same list is kept in the
 design notes of the repository):
@@ -60,7 +62,7 @@ def dft_rows(focal: np.ndarray, pupil: np.ndarray, lam_f: float, focus_z=None,
     Eq. 1 with spatial frequency pupil_m / (lambda f), one row per focus.
 
     3D foci (the axial position of a spot set by a defocus phase of the pupil
-    function, Sec. 4): with axial offsets z_k the pupil field seen by focus k
+    function, Conclusion and outlook section): with axial offsets z_k the pupil field seen by focus k
     carries the paraxial (Fresnel) defocus exp(-i pi z_k (u^2 + v^2) / (lambda f^2)),
     whose u and v factors fold into the two rows:
     Omega[k, m] *= exp(-i pi z_k pupil_m^2 / (lambda f^2)).
@@ -85,7 +87,7 @@ def plan_matrices(nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy, 
 
 # ------------------------------------------------------------- propagation
 def pupil_field(amplitude: np.ndarray, phi: np.ndarray) -> np.ndarray:
-    """E = A exp(i phi): pupil function of Eq. 1 and of Algorithm 1."""
+    """E = A exp(i phi): the pupil function of Eq. 1."""
     return np.asarray(amplitude, np.float64) * np.exp(1j * np.asarray(phi, np.float64))
 
 
@@ -108,7 +110,8 @@ def adjoint(theta: np.ndarray, fx: np.ndarray, fy: np.ndarray) -> np.ndarray:
 
 
 def phase_projection(E: np.ndarray) -> np.ndarray:
-    """phi = arg(E) in (-pi, pi], with arg(0) = 0 (Algorithm 1, update CGH)."""
+    """phi = arg(E) in (-pi, pi], with arg(0) = 0: the phase-only CGH (pupil amplitude
+    constraint)."""
     return np.arctan2(E.imag, E.real)
 
 
@@ -119,7 +122,8 @@ def normalise(v: np.ndarray) -> np.ndarray:
 
 
 def intensity_accuracy(target: np.ndarray, intensity: np.ndarray) -> float:
-    """xi = 1 - ||I~ - I|| / ||I|| over the foci, both normalised to unit sum (Alg. 1)."""
+    """Intensity accuracy xi = 1 - ||I~ - I|| / ||I|| over the foci, both normalised to
+    unit sum (the accuracy measure of the Results and discussion section)."""
     t = normalise(target)
     i = normalise(intensity)
     return float(1.0 - np.linalg.norm(t - i) / np.linalg.norm(i))
@@ -137,29 +141,30 @@ def uniformity(target: np.ndarray, intensity: np.ndarray) -> float:
     return float(1.0 - (r.max() - r.min()) / (r.max() + r.min()))
 
 
-# ------------------------------------------------------- weighting (Alg. 1)
+# ------------------- generalized weighting (Results and discussion section)
 IHAT_FLOOR = 1e-30
 
 
 def generalized_weights(w: np.ndarray, target: np.ndarray, intensity: np.ndarray) -> np.ndarray:
-    """w_j = w_{j-1} sqrt(I~ / I) with both intensities at unit sum (Alg. 1)."""
+    """Generalized weighting w_j = w_{j-1} sqrt(I~ / I), both intensities at unit sum."""
     t = normalise(target)
     i = np.maximum(normalise(intensity), IHAT_FLOOR)
     return np.asarray(w, np.float64) * np.sqrt(t / i)
 
 
 def focused_field(w: np.ndarray, target: np.ndarray, theta: np.ndarray) -> np.ndarray:
-    """Theta_j = w_j sqrt(I~) exp(i arg Theta_{j-1}) (Alg. 1), arg(0) = 0."""
+    """Focal amplitude constraint: w sqrt(I~) exp(i arg Theta), arg(0) = 0."""
     t = normalise(target)
     psi = np.arctan2(theta.imag, theta.real)
     return np.asarray(w, np.float64) * np.sqrt(t) * np.exp(1j * psi)
 
 
 def camera_step(amplitude, phi, fx, fy, target, w, measured):
-    """One iteration of the camera-in-the-loop mode (Sec. 3, experiments): the loop of
-    Algorithm 1 with the calculated intensities replaced by captured ones in the
-    weight update; the focused field keeps the phase of the calculated Theta (a
-    camera records intensities only).  Returns (phi, w, xi of the measurement)."""
+    """One cycle of the camera-in-the-loop mode (experiments of the Results and
+    discussion section): gsw_step with the calculated intensities replaced by captured
+    ones in the weight update; the focused field keeps the phase of the calculated
+    Theta (a camera records intensities only).  Returns (phi, w, xi of the
+    measurement)."""
     A = np.asarray(amplitude, np.float64)
     theta = forward(pupil_field(A, phi), fx, fy)
     meas = np.asarray(measured, np.float64)
@@ -170,41 +175,57 @@ def camera_step(amplitude, phi, fx, fy, target, w, measured):
 
 
 # ----------------------------------------------------------- the GSW loop
+def gsw_step(amplitude, phi, w, fx, fy, target, weighting=True):
+    """One cycle of the method (Results and discussion section: generalized weighting
+    with the MTP operator), from the CGH phase phi and the weights w.
+
+    The pupil function A exp(i phi) goes to the foci through the forward operator of
+    Eq. 2, giving complex amplitudes Theta and intensities I = |Theta|^2.  With the
+    target and calculated intensities the weights are updated, w <- w sqrt(I~/I)
+    (generalized weighting; weighting=False keeps them, which is plain GS).  The
+    focal-plane amplitude constraint replaces each focus amplitude by
+    w sqrt(I~) and keeps the phase of Theta; the inverse operator brings that field
+    back to the pupil, where the pupil amplitude constraint keeps only its phase.
+
+    Returns (theta, intensity, xi, w_new, phi_new); xi is the intensity accuracy of
+    the forward that starts the cycle.
+    """
+    theta = forward(pupil_field(amplitude, phi), fx, fy)
+    intensity = np.abs(theta) ** 2
+    xi = intensity_accuracy(target, intensity)
+    w_new = generalized_weights(w, target, intensity) if weighting else np.asarray(w, np.float64)
+    back = adjoint(focused_field(w_new, target, theta), fx, fy)
+    return theta, intensity, xi, w_new, phase_projection(back)
+
+
 def gsw(amplitude, phi0, fx, fy, target, n_iter, threshold=None, weighting=True, w0=None,
         record=False):
-    """Algorithm 1, iteration by iteration, in FP64.
+    """Drive gsw_step from phi0 for n_iter cycles in FP64.
 
-    Returns a dict with the final phase 'phi', weights 'w', the per-iteration
-    intensity accuracy 'xi_hist' (xi of the forward at the start of each
-    iteration), 'iters' (iterations completed), and the statistics of one
-    extra forward at the final phase: 'theta', 'xi', 'uniformity'.
+    The run stops early once the intensity accuracy of a cycle's forward exceeds
+    `threshold` (that cycle then makes no update), as the method iterates "until the
+    intensity accuracy reaches the threshold value".  Returns a dict with the final
+    phase 'phi', weights 'w', the accuracy of the forward that started each cycle
+    'xi_hist', the cycles completed 'iters', and the statistics of one extra
+    forward at the final phase: 'theta', 'intensity', 'xi', 'uniformity'.
     weighting=False is the plain GS loop (w stays 1).
     """
     A = np.asarray(amplitude, np.float64)
     phi = np.asarray(phi0, np.float64).copy()
     K = fx.shape[0]
     w = np.ones(K) if w0 is None else np.asarray(w0, np.float64).copy()
-    E = pupil_field(A, phi)
-    xi_hist = []
-    phis = []
+    xi_hist, phis = [], []
     iters = 0
-    for _ in range(int(n_iter)):
-        theta = forward(E, fx, fy)                       # forward propagation
-        intensity = np.abs(theta) ** 2                   # I = |Theta|^2
-        xi = intensity_accuracy(target, intensity)       # intensity accuracy
+    while iters < int(n_iter):
+        _, _, xi, w_next, phi_next = gsw_step(A, phi, w, fx, fy, target, weighting)
         xi_hist.append(xi)
-        if threshold is not None and xi > threshold:     # termination
+        if threshold is not None and xi > threshold:
             break
-        if weighting:
-            w = generalized_weights(w, target, intensity)
-        field = focused_field(w, target, theta)          # focused field update
-        E_back = adjoint(field, fx, fy)                  # inverse propagation
-        phi = phase_projection(E_back)                   # update CGH
-        E = pupil_field(A, phi)                          # update pupil function
+        phi, w = phi_next, w_next
         iters += 1
         if record:
             phis.append(phi.copy())
-    theta = forward(E, fx, fy)
+    theta = forward(pupil_field(A, phi), fx, fy)
     intensity = np.abs(theta) ** 2
     out = {"phi": phi, "w": w, "xi_hist": np.asarray(xi_hist), "iters": iters,
            "theta": theta, "intensity": intensity,

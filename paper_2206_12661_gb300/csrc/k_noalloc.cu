@@ -13,6 +13,8 @@
 // The array is shared by every call: each call overwrites all entries it later
 // reads, but calls that overlap on the GPU (different streams, or host threads
 // racing) race on it and must be serialised by the caller.
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "ofa_internal.cuh"
@@ -31,9 +33,29 @@ constexpr int T64 = 64;
 constexpr int TS = 16;
 
 // Device address of g_noalloc_part, looked up once per device (the symbol name
-// is a host-side stand-in, not a device address).
+// is a host-side stand-in, not a device address), together with the context it
+// was looked up in: after a device reset the runtime loads the module into a new
+// context, where the array may sit elsewhere, so a changed context looks it up
+// again.
 std::mutex g_noalloc_mu;
 float2* g_noalloc_addr[64] = {};
+CUcontext g_noalloc_ctx[64] = {};
+
+CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+  });
+  CUcontext c = nullptr;
+  if (fn == nullptr || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 
 __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, acc.x);
@@ -177,8 +199,17 @@ extern "C" ofa_status ofa_forward_noalloc(int nx, int ny, double pitch_x, double
                          "n_foci <= 8192, nx <= 32768)");
     return OFA_ERR_INVALID_ARG;
   }
+  // An error left pending by earlier, unrelated work is reported as such (and
+  // cleared), not mistaken for a failure of this call's launches.
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ofa_set_thread_error(std::string("ofa_forward_noalloc: a CUDA error from earlier work was "
+                                     "pending on entry (nothing was launched): ") +
+                         cudaGetErrorString(e));
+    return OFA_ERR_CUDA;
+  }
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 64) {
     ofa_set_thread_error("ofa_forward_noalloc: no usable current CUDA device");
     return OFA_ERR_CUDA;
@@ -186,8 +217,10 @@ extern "C" ofa_status ofa_forward_noalloc(int nx, int ny, double pitch_x, double
   float2* part = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-      // first call on this device: resolve the scratch array's device address
+    const CUcontext ctx = current_context();
+    if (!g_noalloc_addr[dev] || ctx != g_noalloc_ctx[dev]) {
+      // first call on this device (or in a new context): resolve the scratch
+      // array's device address with this device current
       void* a = nullptr;
       e = cudaGetSymbolAddress(&a, g_noalloc_part);
       if (e != cudaSuccess || a == nullptr) {
@@ -196,6 +229,7 @@ extern "C" ofa_status ofa_forward_noalloc(int nx, int ny, double pitch_x, double
         return OFA_ERR_CUDA;
       }
       g_noalloc_addr[dev] = static_cast<float2*>(a);
+      g_noalloc_ctx[dev] = current_context();
     }
     part = g_noalloc_addr[dev];
   }
@@ -204,11 +238,15 @@ extern "C" ofa_status ofa_forward_noalloc(int nx, int ny, double pitch_x, double
   dim3 grid((n_foci + T64 - 1) / T64, row_tiles);
   fwd_noalloc_kernel<<<grid, 256, 0, s>>>(phi, amplitude, focus_xy, nx, ny, n_foci, pitch_x,
                                           pitch_y, lam_f, part);
-  reduce_noalloc_kernel<<<(n_foci + 255) / 256, 256, 0, s>>>(
-      part, row_tiles, n_foci, reinterpret_cast<float2*>(theta), intensity);
   e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    reduce_noalloc_kernel<<<(n_foci + 255) / 256, 256, 0, s>>>(
+        part, row_tiles, n_foci, reinterpret_cast<float2*>(theta), intensity);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) {
-    ofa_set_thread_error("ofa_forward_noalloc: kernel launch failed");
+    ofa_set_thread_error(std::string("ofa_forward_noalloc: kernel launch failed: ") +
+                         cudaGetErrorString(e));
     return OFA_ERR_CUDA;
   }
   return OFA_OK;

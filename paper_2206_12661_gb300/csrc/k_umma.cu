@@ -38,15 +38,6 @@
 #include <vector>
 
 #include "ofa_internal.cuh"
-#ifdef OFA_PHASE_TRACE
-__device__ unsigned long long g_phase_trace[2][1024][16];
-#define OFA_FOCAL_STAMP(slot)                                                        \
-  do {                                                                               \
-    const unsigned long long t_ = (unsigned long long)clock64();                    \
-    const int lin_ = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); \
-    if (lin_ < 1024) g_phase_trace[0][lin_][slot] = t_;                              \
-  } while (0)
-#endif
 #include "ofa_focal.cuh"
 #include "ofa_math.cuh"
 #include "ofa_split.cuh"
@@ -70,21 +61,6 @@ constexpr uint64_t WAIT_NS = 1000000000ull;
 
 enum { EPI_FWD = 0, EPI_BWD = 1, EPI_GRAD = 2 };
 
-#ifdef OFA_PHASE_TRACE
-// Diagnostic build only: per-CTA %globaltimer stamps of the kernel phases
-// (entry, setup done, first TMA issued, first MMA issued, last MMA issued,
-// accumulator ready, epilogue done, exit; 8-15: inside the epilogue of warp 0,
-// and in the forward the focal tail) of the most recent launch.
-#define OFA_STAMP(slot)                                                            \
-  do {                                                                             \
-    const int lin_ = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); \
-    if (lin_ < 1024) g_phase_trace[EPI == EPI_FWD ? 0 : 1][lin_][slot] = gtimer();  \
-  } while (0)
-#else
-#define OFA_STAMP(slot) \
-  do {                  \
-  } while (0)
-#endif
 enum { KIND_F16 = 0, KIND_BF16 = 1, KIND_TF32 = 2 };
 
 struct EpiArgs {
@@ -178,16 +154,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
       : "memory");
 }
-// Multicast form: the tile lands at the same shared-memory offset in every CTA of
-// cta_mask and signals the barrier at the same offset in each of them.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                               int x, int y, uint16_t cta_mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(cta_mask)
-      : "memory");
-}
 __device__ __forceinline__ uint32_t cluster_ctarank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -274,20 +240,14 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
       : "memory");
 }
-// Arrive on the barrier at this offset in every CTA of cta_mask once all prior
-// tcgen05 operations of this thread have completed.
-template <int CG>
-__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t cta_mask) {
-  if (CG == 1)
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(bar), "h"(cta_mask)
-        : "memory");
-  else
-    asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(bar), "h"(cta_mask)
-        : "memory");
+// 2-SM pair: arrive on the barrier at this offset in both CTAs of the pair
+// (cta_mask) once all prior tcgen05 operations of this thread have completed.
+// This is an mbarrier signal, not a data copy.
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar), "h"(cta_mask)
+      : "memory");
 }
 // Shared::cluster address of the same shared-memory location in CTA `rank`.
 __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
@@ -400,14 +360,13 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
                                           const CUtensorMap* tmb_hi, const CUtensorMap* tmb_lo,
                                           const int m_tile, const int n_tile, const int split,
                                           const int kb0, const int nkb, const EpiArgs& ep,
-                                          const int* __restrict__ done, const int ccx,
-                                          const int ccy, const unsigned tail_count) {
+                                          const int* __restrict__ done,
+                                          const unsigned tail_count) {
   using C = Cfg<KIND, NPASS, BN, EPI, RB, CG>;
   constexpr bool PAIR = CG == 2;
   constexpr int WARP_TMA = Warps<EPI>::TMA, WARP_MMA = Warps<EPI>::MMA;
   constexpr int GROUPS = Warps<EPI>::EPI_THREADS / 128;   // epilogue warps per lane quarter
   constexpr int CPW = BN / (32 * GROUPS);                  // 32-column chunks per epilogue warp
-  if (threadIdx.x == 0) OFA_STAMP(0);
   pdl_launch_dependents();  // the next kernel may start its own set-up on free SMs
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -423,24 +382,15 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
   volatile uint32_t* slot =
       reinterpret_cast<volatile uint32_t*>(base + C::BAR_OFF + 16 * C::STAGES + 8);
 
-  // Cluster (ccx x ccy CTAs, ccx along the output columns, ccy along the rows):
-  // CTAs of one cluster row share the A tile, CTAs of one cluster column the B
-  // tile; each loads a 1/ccx slice of A and a 1/ccy slice of B and multicasts it.
   // PAIR: clusters of two CTAs along the rows (cluster shape 2 x 1 over a grid whose x
-  // runs over the row tiles) form a 2-SM MMA pair.
-  const bool mcast = !PAIR && (ccx * ccy) > 1;
-  const bool clustered = PAIR || mcast;
-  const int crank = clustered ? (int)cluster_ctarank() : 0;
+  // runs over the row tiles) form a 2-SM MMA pair; each CTA loads its own A rows and
+  // half of the B tile from global memory (no multicast).
+  const int crank = PAIR ? (int)cluster_ctarank() : 0;
   const bool leader = !PAIR || (crank & 1) == 0;
-  const int cx = crank % ccx, cy = crank / ccx;
-  uint16_t row_mask = 0, col_mask = 0;
-  for (int i = 0; i < ccx; ++i) row_mask |= (uint16_t)(1u << (i + cy * ccx));
-  for (int i = 0; i < ccy; ++i) col_mask |= (uint16_t)(1u << (cx + i * ccx));
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(bar_full + 8 * s, 1);
-      // every CTA that writes into this CTA's stages must have consumed them
-      mbar_init(bar_empty + 8 * s, mcast ? ccx + ccy - 1 : 1);
+      mbar_init(bar_empty + 8 * s, 1);
     }
     mbar_init(bar_accum, 1);
     fence_mbar_init();
@@ -455,7 +405,7 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
   }
   if (warp == WARP_MMA) tmem_alloc<CG>(slot_u32, BN);
   tc_fence_before();
-  if (clustered) cluster_sync_all();  // partners' barriers exist before any remote signal
+  if (PAIR) cluster_sync_all();  // partner's barriers exist before any remote signal
   else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
@@ -464,7 +414,6 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
   pdl_wait();
   // skip: the loop already stopped, or an earlier launch gave up (uniform over the grid)
   const bool skip = (done != nullptr && *done) || (*ep.err & OFA_ERRBIT_TIMEOUT);
-  if (threadIdx.x == 0) OFA_STAMP(1);
 
   if (skip) {
     // nothing to compute; fall through to the teardown
@@ -473,22 +422,13 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
     if (lane == 0) {
       int issued = 0;
       bool ok = true;
-#ifdef OFA_PHASE_TRACE
-      long long wait_cycles = 0;
-#endif
       for (int kb = 0; kb < nkb && ok; ++kb) {
         const int s = kb % C::STAGES;
         if (kb >= C::STAGES) {
-#ifdef OFA_PHASE_TRACE
-          const long long w0 = clock64();
-#endif
           if (!mbar_wait(bar_empty + 8 * s, ((kb / C::STAGES) - 1) & 1)) {
             ok = false;
             break;
           }
-#ifdef OFA_PHASE_TRACE
-          wait_cycles += clock64() - w0;
-#endif
         }
         const uint32_t st = base_u32 + s * C::STAGE_BYTES;
         const int x = (kb0 + kb) * C::BK;
@@ -503,7 +443,7 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
             tma_load_2d_pair(st + C::A_BYTES, tma_lo, fb, x, m_tile * BM);
             tma_load_2d_pair(st + C::PLANES * C::A_BYTES + C::B_BYTES, tmb_lo, fb, x, brow);
           }
-        } else if (!mcast) {
+        } else {
           mbar_expect_tx(bar_full + 8 * s, C::STAGE_BYTES);
           tma_load_2d(st, tma_hi, bar_full + 8 * s, x, m_tile * BM);
           tma_load_2d(st + C::PLANES * C::A_BYTES, tmb_hi, bar_full + 8 * s, x, n_tile * BN);
@@ -512,30 +452,10 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
             tma_load_2d(st + C::PLANES * C::A_BYTES + C::B_BYTES, tmb_lo, bar_full + 8 * s, x,
                         n_tile * BN);
           }
-        } else {
-          mbar_expect_tx(bar_full + 8 * s, C::STAGE_BYTES);  // whole stage, all sources
-          const int ar = BM / ccx, br = BN / ccy;   // slice rows
-          const uint32_t ao = (uint32_t)(cx * ar * RB), bo = (uint32_t)(cy * br * RB);
-          tma_load_2d_mc(st + ao, tma_hi, bar_full + 8 * s, x, m_tile * BM + cx * ar, row_mask);
-          tma_load_2d_mc(st + C::PLANES * C::A_BYTES + bo, tmb_hi, bar_full + 8 * s, x,
-                         n_tile * BN + cy * br, col_mask);
-          if (NPASS == 3) {
-            tma_load_2d_mc(st + C::A_BYTES + ao, tma_lo, bar_full + 8 * s, x,
-                           m_tile * BM + cx * ar, row_mask);
-            tma_load_2d_mc(st + C::PLANES * C::A_BYTES + C::B_BYTES + bo, tmb_lo,
-                           bar_full + 8 * s, x, n_tile * BN + cy * br, col_mask);
-          }
         }
-        if (issued == 0) OFA_STAMP(2);
         ++issued;
       }
       if (!ok) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
-#ifdef OFA_PHASE_TRACE
-      {
-        const int lin_ = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-        if (lin_ < 1024) g_phase_trace[EPI == EPI_FWD ? 0 : 1][lin_][15] = (unsigned long long)wait_cycles;
-      }
-#endif
       // Drain: every issued copy must have landed before the CTA may exit.  (The
       // odd CTA of a pair signals the leader's barriers; its copies have landed
       // once the leader's MMAs, which read them, complete.)
@@ -549,21 +469,12 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0 && leader) {
       bool ok = true;
-#ifdef OFA_PHASE_TRACE
-      long long wait_cycles = 0;
-#endif
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % C::STAGES;
-#ifdef OFA_PHASE_TRACE
-        const long long w0 = clock64();
-#endif
         if (!mbar_wait(bar_full + 8 * s, (kb / C::STAGES) & 1)) {
           ok = false;
           break;
         }
-#ifdef OFA_PHASE_TRACE
-        if (kb > 0) wait_cycles += clock64() - w0;
-#endif
         tc_fence_after();
         const uint32_t st = base_u32 + s * C::STAGE_BYTES;
         const uint64_t a_hi = sdesc<RB>(st);
@@ -573,29 +484,20 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
 #pragma unroll
         for (int kk = 0; kk < C::UMMA_K_STEPS; ++kk) {
           const uint64_t adv = (uint64_t)((kk * 32) >> 4);  // 32 bytes of K per MMA
-          if ((kb | kk) == 0) OFA_STAMP(3);
           umma<KIND, CG>(tmem, a_hi + adv, b_hi + adv, C::IDESC, (kb | kk) != 0);
           if (NPASS == 3) {
             umma<KIND, CG>(tmem, a_hi + adv, b_lo + adv, C::IDESC, 1);
             umma<KIND, CG>(tmem, a_lo + adv, b_hi + adv, C::IDESC, 1);
           }
         }
-        // stage free (in this CTA and for every CTA that writes into it) once
-        // these MMAs have read it
-        if (PAIR) umma_commit_mc<CG>(bar_empty + 8 * s, (uint16_t)(3u << (crank & ~1)));
-        else if (mcast) umma_commit_mc<CG>(bar_empty + 8 * s, (uint16_t)(row_mask | col_mask));
+        // stage free (in this CTA, and in the partner of a pair) once these MMAs
+        // have read it
+        if (PAIR) umma_commit_pair(bar_empty + 8 * s, (uint16_t)(3u << (crank & ~1)));
         else umma_commit(bar_empty + 8 * s);
       }
       if (!ok) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
-      OFA_STAMP(4);
-#ifdef OFA_PHASE_TRACE
-      {
-        const int lin_ = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-        if (lin_ < 1024) g_phase_trace[EPI == EPI_FWD ? 0 : 1][lin_][13] = (unsigned long long)wait_cycles;
-      }
-#endif
       // accumulator complete (or drained, on abort), in both CTAs of a pair
-      if (PAIR) umma_commit_mc<CG>(bar_accum, (uint16_t)(3u << (crank & ~1)));
+      if (PAIR) umma_commit_pair(bar_accum, (uint16_t)(3u << (crank & ~1)));
       else umma_commit(bar_accum);
     }
   } else {
@@ -618,7 +520,6 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
         for (int q = 0; q < 8; ++q) fy[c][q] = __ldg(fr + c * 8 + q);
       const bool ready = mbar_wait_sleep(bar_accum, 0);
       tc_fence_after();
-      if (threadIdx.x == 0) OFA_STAMP(5);
       if (!ready) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
       const bool valid = ready && nkb > 0;
       float* red = reinterpret_cast<float*>(base + C::STAGES * C::STAGE_BYTES);
@@ -656,7 +557,6 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
         // which CTA finishes last).
         __shared__ int tail_flag;
         __shared__ float focal_sh[4 * 33];
-        if (t == 0) OFA_STAMP(8);
         named_bar_epi();  // every partial of this CTA is written (CTA scope) ...
         if (t == 0) {
           __threadfence();  // ... and, cumulatively, visible GPU-wide before the arrival
@@ -668,7 +568,6 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
           }
         }
         named_bar_epi();
-        if (t == 0) OFA_STAMP(9);
         if (tail_flag) {
           const float2* pt = reinterpret_cast<const float2*>(ep.part);
           if (ep.K <= NUM_EPI_THREADS * 4)
@@ -689,7 +588,6 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
       // accumulator is complete) and each warp then stores 8 whole 64-pixel row
       // segments, every warp store 128 consecutive bytes.
       const bool row_ok = n < ep.ny;
-      if (threadIdx.x == 0) OFA_STAMP(14);
       float av[CPW * 16];
       float pv[EPI == EPI_GRAD ? CPW * 16 : 1];
 #pragma unroll
@@ -719,7 +617,6 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
       }
       const bool ready = mbar_wait_sleep(bar_accum, 0);
       tc_fence_after();
-      if (threadIdx.x == 0) OFA_STAMP(5);
       if (!ready) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
       const bool valid = ready && nkb > 0;
       constexpr int PITCH = 65;                    // words per staged row of 64 pixels
@@ -738,7 +635,6 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
         if (valid) {
           uint32_t v[32];
           tmem_ld32(tw + ch * 32, v);
-          if (threadIdx.x == 0 && c < 2) OFA_STAMP(8 + 3 * c);
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
@@ -763,7 +659,6 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
           }
         }
         named_bar_quarter(quarter);
-        if (threadIdx.x == 0 && c < 2) OFA_STAMP(9 + 3 * c);
         if (valid) {
           const int px0 = ((n_tile * BN) >> 1) + c * 64;  // first pixel of this pass
 #pragma unroll 2
@@ -794,23 +689,19 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
           }
         }
         named_bar_quarter(quarter);
-        if (threadIdx.x == 0 && c < 2) OFA_STAMP(10 + 3 * c);
       }
     }
   }
 
   // ------------------------------------------------------------ teardown
-  if (threadIdx.x == 0) OFA_STAMP(6);
   tc_fence_before();
   __syncthreads();
   if (warp == WARP_MMA) {
     tc_fence_after();
     tmem_dealloc<CG>(tmem, BN);
   }
-  // No CTA may leave while a partner can still multicast into its shared memory
-  // or arrive on its barriers.
-  if (clustered) cluster_sync_all();
-  if (threadIdx.x == 0) OFA_STAMP(7);
+  // No CTA of a pair may leave while its partner can still arrive on its barriers.
+  if (PAIR) cluster_sync_all();
 }
 
 // One plan: tile coordinates from the grid (2-SM pairs lie along the cluster's x
@@ -822,15 +713,14 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
                      const __grid_constant__ CUtensorMap tma_lo,
                      const __grid_constant__ CUtensorMap tmb_hi,
                      const __grid_constant__ CUtensorMap tmb_lo, int kb_per_split, int kb_total,
-                     const __grid_constant__ EpiArgs ep, const int* __restrict__ done, int ccx,
-                     int ccy) {
+                     const __grid_constant__ EpiArgs ep, const int* __restrict__ done) {
   constexpr bool PAIR = CG == 2;
   const int n_tile = PAIR ? blockIdx.y : blockIdx.x, m_tile = PAIR ? blockIdx.x : blockIdx.y;
   const int split = blockIdx.z;
   const int kb0 = split * kb_per_split;
   const int nkb = min(kb_per_split, kb_total - kb0);
   umma_tile<KIND, NPASS, BN, EPI, RB, CG>(&tma_hi, &tma_lo, &tmb_hi, &tmb_lo, m_tile, n_tile,
-                                          split, kb0, nkb, ep, done, ccx, ccy,
+                                          split, kb0, nkb, ep, done,
                                           gridDim.x * gridDim.y * gridDim.z);
 }
 
@@ -850,7 +740,7 @@ __global__ void __launch_bounds__(Warps<EPI>::THREADS, 1)
   const int4 t = tiles[blockIdx.x];
   const GroupItem* g = items + t.x;
   umma_tile<KIND, NPASS, BN, EPI, RB, 1>(&g->a_hi, &g->a_lo, &g->b_hi, &g->b_lo, t.y, t.z, 0, 0,
-                                         g->kb_total, g->ep, nullptr, 1, 1, g->tail_count);
+                                         g->kb_total, g->ep, nullptr, g->tail_count);
 }
 
 // Diagnostic: the bounded wait of the pipelines above, on a barrier nothing
@@ -934,37 +824,38 @@ void visit_variant(int prec, int bn, int rb, int cg, F&& f) {
   using C = Cfg<K_, NP_, BN_, EPI, RB_, CG_>;                                     \
   (void)sizeof(C)
 
+// Launch configuration: programmatic dependent launch always; a 2 x 1 cluster for
+// the CTA pairs of cta_group::2 (cg = 2), no cluster otherwise.
 cudaLaunchConfig_t make_cfg(dim3 grid, int threads, int smem, cudaStream_t s,
-                            cudaLaunchAttribute* attr, int ccx, int ccy) {
+                            cudaLaunchAttribute* attr, int cg) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = ccx;
-  attr[0].val.clusterDim.y = ccy;
-  attr[0].val.clusterDim.z = 1;
-  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = cg;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 2;
+  cfg.numAttrs = cg == 2 ? 2 : 1;
   return cfg;
 }
 
 template <int EPI>
-void launch_gemm(int prec, int bn, int rb, int cg, int ccx, int ccy, const CUtensorMap& a_hi,
+void launch_gemm(int prec, int bn, int rb, int cg, const CUtensorMap& a_hi,
                  const CUtensorMap& a_lo, const CUtensorMap& b_hi, const CUtensorMap& b_lo,
                  dim3 grid, int kbps, int kbt, const EpiArgs& ep, const int* done,
                  cudaStream_t s) {
   visit_variant(prec, bn, rb, cg, [&](auto kind, auto npass, auto bnc, auto rbc, auto cgc) {
     OFA_VARIANT_TYPES;
-    const int cx = CG_ == 2 ? 2 : ccx, cy = CG_ == 2 ? 1 : ccy;
     const dim3 g = CG_ == 2 ? dim3(grid.y, grid.x, grid.z) : grid;  // pairs: rows on x
     cudaLaunchAttribute attr[2];
-    cudaLaunchConfig_t cfg = make_cfg(g, Warps<EPI>::THREADS, C::SMEM, s, attr, cx, cy);
+    cudaLaunchConfig_t cfg = make_cfg(g, Warps<EPI>::THREADS, C::SMEM, s, attr, CG_);
     cudaLaunchKernelEx(&cfg, umma_gemm_kernel<K_, NP_, BN_, EPI, RB_, CG_>, a_hi, a_lo, b_hi,
-                       b_lo, kbps, kbt, ep, done, cx, cy);
+                       b_lo, kbps, kbt, ep, done);
   });
 }
 
@@ -980,23 +871,6 @@ cudaError_t set_attr_epi(int prec) {
         if (r != cudaSuccess) e = r;
       });
   return e;
-}
-
-template <int EPI>
-int max_clusters(int prec, int bn, int rb, int cg, int ccx, int ccy, dim3 grid) {
-  int n = 0;
-  visit_variant(prec, bn, rb, cg, [&](auto kind, auto npass, auto bnc, auto rbc, auto cgc) {
-    OFA_VARIANT_TYPES;
-    cudaLaunchAttribute attr[2];
-    cudaLaunchConfig_t cfg = make_cfg(grid, Warps<EPI>::THREADS, C::SMEM, 0, attr, ccx, ccy);
-    cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&n, umma_gemm_kernel<K_, NP_, BN_, EPI, RB_, CG_>, &cfg) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      n = 0;
-    }
-  });
-  return n;
 }
 
 EpiArgs base_args(ofa_plan* p) {
@@ -1019,11 +893,6 @@ EpiArgs base_args(ofa_plan* p) {
 
 }  // namespace
 
-#ifdef OFA_PHASE_TRACE
-extern "C" int ofa_debug_phase_trace(unsigned long long* out) {
-  return (int)cudaMemcpyFromSymbol(out, g_phase_trace, sizeof(g_phase_trace));  // [2][1024][16]
-}
-#endif
 
 // Opt every kernel variant of a precision into its dynamic shared memory (done
 // once per plan, outside any stream capture; the attribute is per device).
@@ -1042,34 +911,31 @@ void launch_selftest_wait(OfaDevState* st, cudaStream_t s) {
 
 namespace {
 struct TuneResult {
-  int fwd_bn, fwd_split, fwd_rb, fwd_ccx, fwd_ccy, fwd_cg, bwd_bn, bwd_rb, bwd_ccx, bwd_ccy,
-      bwd_cg;
+  int fwd_bn, fwd_split, fwd_cg, bwd_bn, bwd_cg;
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, TuneResult> g_tune_cache;
 
-int cluster_shape_ok(ofa_plan* p, int epi, int bn, int rb, int cg, int n_tiles, int m_tiles,
-                     int z, int ccx, int ccy) {
-  dim3 grid(n_tiles, m_tiles, z);
-  if (cg == 2) {  // a 2-SM pair: 2 x 1 cluster over a grid with the row tiles on x
-    if (ccx * ccy != 1 || m_tiles % 2 != 0) return 0;
-    grid = dim3(m_tiles, n_tiles, z);
-    ccx = 2;
-  } else if (n_tiles % ccx != 0 || m_tiles % ccy != 0) {
-    return 0;
-  }
-  if (ccx * ccy == 1) return 1;
-  if (epi == EPI_FWD) return max_clusters<EPI_FWD>(p->precision, bn, rb, cg, ccx, ccy, grid);
-  return max_clusters<EPI_BWD>(p->precision, bn, rb, cg, ccx, ccy, grid);
-}
-
 void apply(TcOperands& t, const TuneResult& r) {
-  t.fwd_bn = r.fwd_bn; t.fwd_split = r.fwd_split; t.fwd_rb = r.fwd_rb;
-  t.fwd_ccx = r.fwd_ccx; t.fwd_ccy = r.fwd_ccy; t.fwd_cg = r.fwd_cg;
-  t.bwd_bn = r.bwd_bn; t.bwd_rb = r.bwd_rb; t.bwd_ccx = r.bwd_ccx; t.bwd_ccy = r.bwd_ccy;
-  t.bwd_cg = r.bwd_cg;
+  t.fwd_bn = r.fwd_bn; t.fwd_split = r.fwd_split; t.fwd_cg = r.fwd_cg;
+  t.bwd_bn = r.bwd_bn; t.bwd_cg = r.bwd_cg;
 }
 }  // namespace
+
+bool tc_config_valid(const ofa_plan* p, const TcOperands& t, int fwd_bn, int fwd_split,
+                     int fwd_cg, int bwd_bn, int bwd_cg) {
+  const int tiles_m = p->nyp / BM;
+  const int kb_fwd = (2 * p->nxp * t.elem_bytes) / 128;
+  if (fwd_bn != 128 && fwd_bn != 256) return false;
+  if (bwd_bn != 128 && bwd_bn != 256) return false;
+  if (fwd_split != 1 && fwd_split != 2 && fwd_split != 4) return false;
+  if (kb_fwd < fwd_split) return false;
+  if (fwd_cg != 1 && fwd_cg != 2) return false;
+  if (bwd_cg != 1 && bwd_cg != 2) return false;
+  // a 2-SM pair covers two row tiles
+  if ((fwd_cg == 2 || bwd_cg == 2) && tiles_m % 2 != 0) return false;
+  return (2 * p->kp) % fwd_bn == 0 && (2 * p->nxp) % bwd_bn == 0;
+}
 
 bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
   const auto key = std::make_tuple(p->device, p->nx, p->ny, p->K, p->precision);
@@ -1094,7 +960,6 @@ bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
   if (!ok) err = "allocating autotune scratch";
-  const int tiles_m = p->nyp / BM;
   const int reps = 5;
   auto time_it = [&](auto&& launch) -> float {
     launch();  // warm-up
@@ -1113,32 +978,24 @@ bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
     if (cudaGetLastError() != cudaSuccess) return 1e30f;
     return ms;
   };
-  const int cl[4][2] = {{1, 1}, {2, 2}, {2, 1}, {1, 2}};
   float best_f = 1e30f, best_b = 1e30f;
-  TuneResult res = {t.fwd_bn, t.fwd_split, 128, 1, 1, 1, t.bwd_bn, 128, 1, 1, 1};
-  const int rb = 128;
-  const int kb_fwd = (2 * p->nxp * t.elem_bytes) / rb;
+  TuneResult res = {t.fwd_bn, t.fwd_split, 1, t.bwd_bn, 1};
+  const int kb_fwd = (2 * p->nxp * t.elem_bytes) / 128;
   for (int cg : {1, 2}) {
     for (int bn : {128, 256}) {
       for (int split = 1; split <= 4 && ok; split *= 2) {
         if (kb_fwd / split < 4) break;
-        for (auto& c : cl) {
-          const int n_tiles = (2 * p->kp) / bn;
-          if (!cluster_shape_ok(p, EPI_FWD, bn, rb, cg, n_tiles, tiles_m, split, c[0], c[1]))
-            continue;
-          TcOperands cand = t;
-          cand.fwd_bn = bn; cand.fwd_split = split; cand.fwd_rb = rb; cand.fwd_cg = cg;
-          cand.fwd_ccx = c[0]; cand.fwd_ccy = c[1];
-          if (!tc_encode_maps(p, cand, err)) { ok = false; break; }
-          const float ms = time_it([&] { launch_fwd_tc(p, cand, nullptr, p->stream, false); });
-          if (verbose)
-            fprintf(stderr, "ofa autotune forward bn=%d split=%d cg=%d cluster=%dx%d: %.2f us\n",
-                    bn, split, cg, c[0], c[1], 1000.f * ms / reps);
-          if (ms < best_f) {
-            best_f = ms;
-            res.fwd_bn = bn; res.fwd_split = split; res.fwd_rb = rb; res.fwd_cg = cg;
-            res.fwd_ccx = c[0]; res.fwd_ccy = c[1];
-          }
+        if (!tc_config_valid(p, t, bn, split, cg, 128, 1)) continue;
+        TcOperands cand = t;
+        cand.fwd_bn = bn; cand.fwd_split = split; cand.fwd_cg = cg;
+        if (!tc_encode_maps(p, cand, err)) { ok = false; break; }
+        const float ms = time_it([&] { launch_fwd_tc(p, cand, nullptr, p->stream, false); });
+        if (verbose)
+          fprintf(stderr, "ofa autotune forward bn=%d split=%d cg=%d: %.2f us\n", bn, split, cg,
+                  1000.f * ms / reps);
+        if (ms < best_f) {
+          best_f = ms;
+          res.fwd_bn = bn; res.fwd_split = split; res.fwd_cg = cg;
         }
       }
     }
@@ -1146,27 +1003,22 @@ bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
   for (int cg : {1, 2}) {
     for (int bn : {128, 256}) {
       if (!ok) break;
-      for (auto& c : cl) {
-        const int n_tiles = (2 * p->nxp) / bn;
-        if (!cluster_shape_ok(p, EPI_BWD, bn, rb, cg, n_tiles, tiles_m, 1, c[0], c[1])) continue;
-        TcOperands cand = t;
-        cand.e_hi = e_scr[0];
-        cand.e_lo = e_scr[1];
-        cand.bwd_bn = bn; cand.bwd_rb = rb; cand.bwd_cg = cg;
-        cand.bwd_ccx = c[0]; cand.bwd_ccy = c[1];
-        if (!tc_encode_maps(p, cand, err)) { ok = false; break; }
-        float* keep = p->phi;
-        p->phi = phi_scratch;
-        const float ms = time_it([&] { launch_bwd_tc(p, cand, nullptr, p->stream); });
-        p->phi = keep;
-        if (verbose)
-          fprintf(stderr, "ofa autotune inverse bn=%d cg=%d cluster=%dx%d: %.2f us\n", bn, cg,
-                  c[0], c[1], 1000.f * ms / reps);
-        if (ms < best_b) {
-          best_b = ms;
-          res.bwd_bn = bn; res.bwd_rb = rb; res.bwd_cg = cg;
-          res.bwd_ccx = c[0]; res.bwd_ccy = c[1];
-        }
+      if (!tc_config_valid(p, t, 128, 1, 1, bn, cg)) continue;
+      TcOperands cand = t;
+      cand.e_hi = e_scr[0];
+      cand.e_lo = e_scr[1];
+      cand.bwd_bn = bn; cand.bwd_cg = cg;
+      if (!tc_encode_maps(p, cand, err)) { ok = false; break; }
+      float* keep = p->phi;
+      p->phi = phi_scratch;
+      const float ms = time_it([&] { launch_bwd_tc(p, cand, nullptr, p->stream); });
+      p->phi = keep;
+      if (verbose)
+        fprintf(stderr, "ofa autotune inverse bn=%d cg=%d: %.2f us\n", bn, cg,
+                1000.f * ms / reps);
+      if (ms < best_b) {
+        best_b = ms;
+        res.bwd_bn = bn; res.bwd_cg = cg;
       }
     }
   }
@@ -1187,10 +1039,9 @@ bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err) {
   const int eb = t.elem_bytes;
   const uint64_t e_cols = 2 * (uint64_t)p->nxp, k_cols = 2 * (uint64_t)p->kp;
   bool ok = true;
-  // boxes are the per-CTA slices of a cluster's multicast (whole tiles without clusters)
-  // a 2-SM pair loads half of the B tile per CTA
-  const uint32_t e_box = BM / t.fwd_ccx, bx_box = t.fwd_bn / (t.fwd_ccy * t.fwd_cg);
-  const uint32_t p_box = BM / t.bwd_ccx, q_box = t.bwd_bn / (t.bwd_ccy * t.bwd_cg);
+  // boxes are whole tiles; a 2-SM pair loads half of the B tile per CTA
+  const uint32_t e_box = BM, bx_box = t.fwd_bn / t.fwd_cg;
+  const uint32_t p_box = BM, q_box = t.bwd_bn / t.bwd_cg;
   const int fr = t.fwd_rb, br = t.bwd_rb;
   ok = ok && encode(&t.tm_e_hi, t.e_hi, eb, e_cols, p->nyp, e_box, fr, err);
   ok = ok && encode(&t.tm_bx_hi, t.bx_hi, eb, e_cols, 2 * (uint64_t)p->kp, bx_box, fr, err);
@@ -1230,7 +1081,7 @@ void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream
     ep.stw = p->st;
     ep.weighting = p->weighting;
   }
-  launch_gemm<EPI_FWD>(p->precision, t.fwd_bn, t.fwd_rb, t.fwd_cg, t.fwd_ccx, t.fwd_ccy, t.tm_e_hi,
+  launch_gemm<EPI_FWD>(p->precision, t.fwd_bn, t.fwd_rb, t.fwd_cg, t.tm_e_hi,
                        t.tm_e_lo, t.tm_bx_hi, t.tm_bx_lo, grid, kbps, kb_total, ep, done, s);
 }
 
@@ -1241,7 +1092,7 @@ void launch_bwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream
   ep.out = p->phi;
   ep.e_hi = t.e_hi;
   ep.e_lo = t.e_lo;
-  launch_gemm<EPI_BWD>(p->precision, t.bwd_bn, t.bwd_rb, t.bwd_cg, t.bwd_ccx, t.bwd_ccy, t.tm_p_hi,
+  launch_gemm<EPI_BWD>(p->precision, t.bwd_bn, t.bwd_rb, t.bwd_cg, t.tm_p_hi,
                        t.tm_p_lo, t.tm_q_hi, t.tm_q_lo, grid, kb_total, kb_total, ep, done, s);
 }
 
@@ -1253,7 +1104,7 @@ void launch_grad_tc(ofa_plan* p, const TcOperands& t, const float* phi, float sc
   EpiArgs ep = base_args(p);
   ep.out = grad;
   ep.phi_in = phi;
-  launch_gemm<EPI_GRAD>(p->precision, t.bwd_bn, t.bwd_rb, t.bwd_cg, t.bwd_ccx, t.bwd_ccy, t.tm_p_hi,
+  launch_gemm<EPI_GRAD>(p->precision, t.bwd_bn, t.bwd_rb, t.bwd_cg, t.tm_p_hi,
                         t.tm_p_lo, t.tm_q_hi, t.tm_q_lo, grid, kb_total, kb_total, ep, nullptr, s);
 }
 
@@ -1363,7 +1214,7 @@ void launch_group(int prec, const TcGroupSet& set, cudaStream_t s) {
     if constexpr (CG_ == 1) {
       cudaLaunchAttribute attr[2];
       cudaLaunchConfig_t cfg =
-          make_cfg(dim3(set.n_tiles), Warps<EPI>::THREADS, C::SMEM, s, attr, 1, 1);
+          make_cfg(dim3(set.n_tiles), Warps<EPI>::THREADS, C::SMEM, s, attr, 1);
       cudaLaunchKernelEx(&cfg, umma_group_kernel<K_, NP_, BN_, EPI, RB_>, set.items, set.tiles);
     }
   });

@@ -490,12 +490,11 @@ ofa_status ofa_check_foci(int n_foci, const double* xy, double px, double py, do
 
 ofa_status ofa_plan_config(const ofa_plan* p, int* c) {
   if (!p || !c) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "NULL argument");
-  for (int i = 0; i < 12; ++i) c[i] = 0;
+  for (int i = 0; i < 8; ++i) c[i] = 0;
   if (!use_tc(p)) return OFA_OK;
   const TcOperands& t = p->tc;
-  c[0] = t.fwd_bn; c[1] = t.fwd_split; c[2] = t.fwd_ccx; c[3] = t.fwd_ccy;
-  c[4] = t.bwd_bn; c[5] = t.bwd_ccx; c[6] = t.bwd_ccy; c[7] = p->K <= 4096 ? 1 : 0;
-  c[8] = t.fwd_rb; c[9] = t.bwd_rb; c[10] = t.fwd_cg; c[11] = t.bwd_cg;
+  c[0] = t.fwd_bn; c[1] = t.fwd_split; c[2] = t.fwd_cg; c[3] = t.bwd_bn; c[4] = t.bwd_cg;
+  c[5] = p->K <= 4096 ? 1 : 0; c[6] = t.fwd_rb; c[7] = t.bwd_rb;
   return OFA_OK;
 }
 
@@ -877,7 +876,18 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     OFA_TRY(prepare_precision(dev, p->precision), "setting kernel shared-memory attributes");
     choose_tiles(p, p->tc, sm_count);
     std::string err;
-    if (opt.autotune) {
+    const int* kc = opt.kernel_config;
+    const bool forced = kc[0] | kc[1] | kc[2] | kc[3] | kc[4];
+    if (forced) {
+      if (!tc_config_valid(p, p->tc, kc[0], kc[1], kc[2], kc[3], kc[4])) {
+        p->last_error = "kernel_config {" + std::to_string(kc[0]) + ", " + std::to_string(kc[1]) +
+                        ", " + std::to_string(kc[2]) + ", " + std::to_string(kc[3]) + ", " +
+                        std::to_string(kc[4]) + "} cannot run these sizes";
+        return fail(OFA_ERR_UNSUPPORTED);
+      }
+      p->tc.fwd_bn = kc[0]; p->tc.fwd_split = kc[1]; p->tc.fwd_cg = kc[2];
+      p->tc.bwd_bn = kc[3]; p->tc.bwd_cg = kc[4];
+    } else if (opt.autotune) {
       OFA_TRY(cudaStreamSynchronize(p->stream), "plan set-up");
       if (!tc_autotune(p, p->tc, err)) {
         p->last_error = err;

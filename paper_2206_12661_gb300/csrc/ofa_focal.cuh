@@ -12,11 +12,6 @@
 #pragma once
 #include "ofa_internal.cuh"
 
-#ifndef OFA_FOCAL_STAMP
-#define OFA_FOCAL_STAMP(slot) \
-  do {                        \
-  } while (0)
-#endif
 
 namespace ofa_focal {
 
@@ -207,7 +202,6 @@ __device__ inline void iterate_regs(const float2* part, int n_part, int K, int k
                                     float2* __restrict__ c, double* __restrict__ hist,
                                     OfaDevState* __restrict__ st, int weighting, float* sh,
                                     int tid, Bar bar) {
-  if (tid == 0) OFA_FOCAL_STAMP(14);
   const double thr = st->threshold;
   const int hcount = st->hist_count;
   const int j0 = st->j;
@@ -248,7 +242,6 @@ __device__ inline void iterate_regs(const float2* part, int n_part, int K, int k
     ik[i] = th[i].x * th[i].x + th[i].y * th[i].y;
     r1[0] += ik[i];
   }
-  if (tid == 0) OFA_FOCAL_STAMP(10);
   block_sum<NT>(r1, sh, tid, bar);
   const float S = r1[0];
   if (!(S > 0.f) || !isfinite(S)) {
@@ -274,7 +267,6 @@ __device__ inline void iterate_regs(const float2* part, int n_part, int K, int k
     mx = fmaxf(mx, wk[i] * sq[i]);
   }
   block_sum2_max<NT>(r2, mx, sh + 33, tid, bar);
-  if (tid == 0) OFA_FOCAL_STAMP(11);
   const float xi = 1.f - sqrtf(r2[0] / r2[1]);
   if (tid == 0) {
     hist[hcount % OFA_HIST_CAP] = (double)xi;
@@ -306,7 +298,6 @@ __device__ inline void iterate_regs(const float2* part, int n_part, int K, int k
   if (tid == 0) {
     st->j = j0 + 1;
     st->c_scale = scale;
-    OFA_FOCAL_STAMP(12);
   }
 }
 

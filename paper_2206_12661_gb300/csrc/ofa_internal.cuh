@@ -55,7 +55,6 @@ struct TcOperands {
   int fwd_bn = 256, fwd_split = 1, bwd_bn = 256;
   int fwd_rb = 128, bwd_rb = 128;                          // operand row bytes per stage
   int fwd_cg = 1, bwd_cg = 1;                              // 2 = 2-SM MMA pairs
-  int fwd_ccx = 1, fwd_ccy = 1, bwd_ccx = 1, bwd_ccy = 1;  // thread-block cluster shapes
 };
 
 // FP32 form scratch: the inverse's transposed operands and the forward's
@@ -218,6 +217,10 @@ cudaError_t tc_prepare(int prec);
 // fastest in t (cached per device, size and precision for the process).
 bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err);
 bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err);
+// Whether a kernel configuration (tile widths in accumulator columns 128 | 256,
+// forward split-K 1 | 2 | 4, CTA groups 1 | 2) can run this plan's sizes.
+bool tc_config_valid(const ofa_plan* p, const TcOperands& t, int fwd_bn, int fwd_split,
+                     int fwd_cg, int bwd_bn, int bwd_cg);
 // One thread waits, with the bounded wait of the tensor-core kernels, on an mbarrier
 // nothing arrives at; it sets OFA_ERRBIT_TIMEOUT in st->err when the wait gives up.
 void launch_selftest_wait(OfaDevState* st, cudaStream_t s);

@@ -43,7 +43,8 @@ class ofa_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("seed", C.c_uint64), ("cuda_stream", C.c_void_p),
                 ("amplitude", C.c_void_p), ("waist_frac", C.c_double), ("phi0", C.c_void_p),
                 ("mem_space", C.c_int), ("weighting", C.c_int), ("autotune", C.c_int),
-                ("focus_z", C.c_void_p), ("separable", C.c_int)]
+                ("focus_z", C.c_void_p), ("separable", C.c_int),
+                ("kernel_config", C.c_int * 5)]
 
 
 class ofa_stats(C.Structure):
@@ -221,11 +222,10 @@ def ofa_profile_kernels(plan, reps: int = 20) -> np.ndarray:
 
 
 def ofa_plan_config(plan) -> dict:
-    c = np.zeros(12, dtype=np.int32)
+    c = np.zeros(8, dtype=np.int32)
     _check(_lib.ofa_plan_config(plan, _ptr(c)), plan)
-    keys = ["fwd_bn", "fwd_split", "fwd_cluster_x", "fwd_cluster_y", "inv_bn", "inv_cluster_x",
-            "inv_cluster_y", "focal_fused", "fwd_row_bytes", "inv_row_bytes", "fwd_cta_group",
-            "inv_cta_group"]
+    keys = ["fwd_bn", "fwd_split", "fwd_cta_group", "inv_bn", "inv_cta_group", "focal_fused",
+            "fwd_row_bytes", "inv_row_bytes"]
     return dict(zip(keys, (int(x) for x in c)))
 
 
@@ -313,7 +313,7 @@ class Plan:
     def __init__(self, nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy, target,
                  precision="f16x3", amplitude=None, phi0=None, seed=0, weighting=True,
                  stream=None, waist_frac=0.4, mem_space=OFA_MEM_HOST, autotune=True,
-                 focus_z=None, separable=-1):
+                 focus_z=None, separable=-1, kernel_config=None):
         opt = ofa_options_default()
         opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opt.seed = int(seed)
@@ -321,6 +321,9 @@ class Plan:
         opt.weighting = 1 if weighting else 0
         opt.autotune = 1 if autotune else 0
         opt.separable = int(separable)
+        if kernel_config is not None:
+            for i, v in enumerate(kernel_config):
+                opt.kernel_config[i] = int(v)
         opt.waist_frac = float(waist_frac)
         opt.mem_space = int(mem_space)
         if mem_space == OFA_MEM_HOST:

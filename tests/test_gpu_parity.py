@@ -225,6 +225,27 @@ def test_full_run_poisson1000(ofa, dev, prec):
     assert abs(st.uniformity - ref["uniformity"]) < 1e-3
 
 
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_gs_flag_matches_oracle_plain_gs(ofa, dev, prec):
+    """weighting = 0 is the plain GS loop (w stays 1): xi history and final xi, U
+    against oracle.gsw(weighting=False); GS stays below the weighted loop here."""
+    w = I.named("pupil256_grid100_uniform")
+    w.target = np.random.default_rng(4).uniform(0.5, 1.0, w.n_foci).astype(np.float32)
+    fx, fy = oracle_mats(w)
+    ref = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, 30, weighting=False)
+    gsw = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, 30)
+    plan = ofa.Plan.from_workload(w, precision=prec, weighting=False)
+    it, xi = plan.iterate(30, want_stats=True)
+    st = plan.stats()
+    hist = plan.xi_history()
+    _, wts, _ = plan.get_state()
+    plan.close()
+    assert it == 30 and np.all(wts == 1.0)
+    assert np.max(np.abs(hist - ref["xi_hist"])) < 1e-3
+    assert abs(xi - ref["xi"]) < 1e-3 and abs(st.uniformity - ref["uniformity"]) < 1e-3
+    assert ref["xi"] < gsw["xi"] - 1e-3
+
+
 @pytest.fixture(scope="module")
 def oracle_1920(dev):
     w = I.named("pupil1920x1152_grid2500")

@@ -152,6 +152,73 @@ def test_3d_single_focus_lens_phase():
     assert np.abs(off[0]) < 0.99 * A2.sum()
 
 
+def fresnel_axial_intensity(E, pitch, wavelength, focal_length, distances):
+    """On-axis intensity behind a thin lens, by the paraxial Fresnel diffraction
+    integral written out as a plain FP64 sum (independent of the oracle's rows).
+
+    The pupil field E[n, m] at (u_m, v_n) passes the lens transmission
+    exp(-i pi rho^2 / (lambda f)) and propagates a distance d; on the axis the
+    Fresnel kernel is exp(i pi rho^2 / (lambda d)) / (i lambda d).  The quadratic
+    phase separates in u and v, so each distance costs two matrix-vector products.
+    """
+    ny, nx = E.shape
+    u = (np.arange(nx) - (nx - 1) / 2.0) * pitch
+    v = (np.arange(ny) - (ny - 1) / 2.0) * pitch
+    d = np.asarray(distances, np.float64)
+    a = 1.0 / (wavelength * d) - 1.0 / (wavelength * focal_length)        # [D]
+    bu = np.exp(1j * np.pi * np.outer(u ** 2, a))                          # [nx][D]
+    bv = np.exp(1j * np.pi * np.outer(v ** 2, a))                          # [ny][D]
+    s = np.sum(bv * (np.asarray(E, np.complex128) @ bu), axis=0) * pitch * pitch
+    return np.abs(s) ** 2 / (wavelength * d) ** 2
+
+
+def axial_focus_of_3d_oracle_phase(z0, n=512):
+    """Distance behind the lens where the oracle's one-cycle phase for a single focus
+    at (0, 0, z0) puts the on-axis intensity maximum (0.1 mm sweep, 150-300 mm)."""
+    A = O.default_amplitude(n, n, P, P)
+    fx, fy = O.plan_matrices(n, n, P, P, LAM, F, [[0.0, 0.0]], focus_z=[z0])
+    phi = O.gsw(A, np.zeros((n, n)), fx, fy, np.array([1.0]), n_iter=1)["phi"]
+    d = np.arange(0.150, 0.300, 1e-4)
+    inten = fresnel_axial_intensity(O.pupil_field(A, phi), P, LAM, F, d)
+    return d[int(np.argmax(inten))]
+
+
+# The oracle's defocus term is first order in z/f: the lens phase pi z0 rho^2 /
+# (lambda f^2) it writes moves the focus to f^2 / (f - z0) = f + z0 + z0^2/f + ...
+# The pin allows 1.5 z0^2 / f plus two sweep steps: at |z0| = 25 mm that is 4.9 mm,
+# while a flipped sign misses by 47 mm, a doubled term by 42 mm, a halved one by 12 mm.
+Z_DEFOCUS = 25e-3
+
+
+def defocus_tolerance(z0):
+    return 1.5 * z0 * z0 / F + 2e-4
+
+
+@pytest.mark.parametrize("z0", [Z_DEFOCUS, -Z_DEFOCUS])
+def test_3d_defocus_term_focuses_at_z0_by_fresnel_propagation(z0):
+    """The oracle's defocus sign and scale, pinned by physics: the phase it writes for
+    a single 3D focus at z0, propagated by the Fresnel integral, peaks on the axis at
+    f + z0 (to first order in z0 / f)."""
+    peak = axial_focus_of_3d_oracle_phase(z0)
+    assert abs(peak - (F + z0)) < defocus_tolerance(z0), (peak, F + z0)
+
+
+@pytest.mark.parametrize("mistake", [-1.0, 2.0, 0.5], ids=["sign", "doubled", "halved"])
+def test_3d_defocus_pin_catches_a_planted_mistake(monkeypatch, mistake):
+    """A wrong defocus term planted in the oracle (sign flipped, scale doubled or
+    halved) moves the Fresnel focus outside the pin's tolerance."""
+    import oracle.gsw_mtp as M
+    real = M.dft_rows
+
+    def planted(focal, pupil, lam_f, focus_z=None, focal_length=None):
+        z = None if focus_z is None else mistake * np.asarray(focus_z, np.float64)
+        return real(focal, pupil, lam_f, z, focal_length)
+
+    monkeypatch.setattr(M, "dft_rows", planted)
+    peak = axial_focus_of_3d_oracle_phase(Z_DEFOCUS)
+    assert abs(peak - (F + Z_DEFOCUS)) > defocus_tolerance(Z_DEFOCUS), peak
+
+
 def test_3d_forward_equals_brute_force_sum():
     """Separable rows against the non-separated sum with the full 2D exponent."""
     rng = np.random.default_rng(22)
