@@ -108,6 +108,17 @@ typedef struct ofa_options {
                                 k-blocks, 2-SM pairs over an odd number of 128-row tiles)
                                 -> OFA_ERR_UNSUPPORTED.  Ignored by the FP32 and separable
                                 forms. */
+  int fused_loop;            /* tensor-core forms with K <= 4096: run each ofa_iterate call as
+                                one persistent cooperative launch that keeps every CTA
+                                resident and synchronises the grid between the forward
+                                product, the focal step and the inverse product (no serial
+                                focal tail, no separate operand-build launch).  0 = never:
+                                one launch per product, replayed from CUDA graphs (default;
+                                measured faster on GB300), 1 = always (OFA_ERR_UNSUPPORTED
+                                if it cannot run), -1 = whenever the device can co-schedule
+                                it */
+  int loop_config[2];        /* fused loop: {CTA group (1, or 2 for 2-SM pairs), forward split
+                                of the contraction (1..4)}; zeros = chosen at creation */
 } ofa_options;
 
 typedef struct ofa_stats {
@@ -244,12 +255,29 @@ ofa_status ofa_adjoint(ofa_plan* plan, const float* phi, const float* theta,
  */
 ofa_status ofa_profile_kernels(ofa_plan* plan, int reps, double* ms_out);
 
-/* Kernel configuration of a plan (host output, 8 ints), in the order of
- * ofa_options.kernel_config followed by three derived values: forward tile width
+/*
+ * ofa_profile_loop -- measurement aid for the fused loop (ofa_options.fused_loop):
+ * average device time (ms) of one iteration, from `reps` (>= 1) launches of n_iter
+ * (>= 1) iterations each, back to back on the plan's stream between CUDA events after
+ * one untimed launch.  phase_us (nullable, host [6]) receives the average microseconds
+ * per iteration that the first CTA spends in each phase, from %globaltimer stamps of a
+ * separate set of launches: forward products and their epilogues, wait at the barrier
+ * after the forward, focal step, operand build, wait at the barrier after the operand
+ * build, inverse products and their epilogues.  The loop state is saved before and
+ * restored after.  OFA_ERR_UNSUPPORTED if the plan does not run the fused loop.
+ * Synchronises.
+ */
+ofa_status ofa_profile_loop(ofa_plan* plan, int n_iter, int reps, double* ms_per_iteration,
+                            double* phase_us);
+
+/* Kernel configuration of a plan (host output, 12 ints), in the order of
+ * ofa_options.kernel_config followed by derived values: forward tile width
  * (accumulator columns), forward split-K factor, forward CTA group (1, or 2 for 2-SM MMA
  * pairs of 256 accumulator rows), inverse tile width, inverse CTA group, 1 if the focal
  * step runs in the forward kernel's last CTA, forward and inverse operand row width per
- * pipeline stage (bytes of K).  The FP32 and separable forms report zeros. */
+ * pipeline stage (bytes of K); then the fused loop: 1 if ofa_iterate runs it, its CTA
+ * group, its forward split and its CTAs per launch.  The FP32 and separable forms report
+ * zeros. */
 ofa_status ofa_plan_config(const ofa_plan* plan, int* config_out);
 
 /* Form of a plan: *separable = 1 with the U_x and U_y distinct focus coordinates it

@@ -361,6 +361,9 @@ ofa_status sync_and_check(ofa_plan* p) {
   if (s != OFA_OK) return s;
   if (p->st_host->err & OFA_ERRBIT_TIMEOUT)
     return ofa_fail(p, OFA_ERR_TIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
+  if (p->st_host->err & OFA_ERRBIT_LAUNCH)
+    return ofa_fail(p, OFA_ERR_CUDA,
+                    "the fused loop kernel ran without its 2-CTA clusters or co-resident grid");
   if (p->st_host->err & OFA_ERRBIT_NUMERIC)
     return ofa_fail(p, OFA_ERR_NUMERIC, "sum of focus intensities is zero or not finite");
   return OFA_OK;
@@ -438,6 +441,7 @@ ofa_status ofa_options_default(ofa_options* o) {
   o->autotune = 1;
   o->focus_z = nullptr;
   o->separable = -1;
+  o->fused_loop = 0;
   return OFA_OK;
 }
 
@@ -490,11 +494,14 @@ ofa_status ofa_check_foci(int n_foci, const double* xy, double px, double py, do
 
 ofa_status ofa_plan_config(const ofa_plan* p, int* c) {
   if (!p || !c) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "NULL argument");
-  for (int i = 0; i < 8; ++i) c[i] = 0;
+  for (int i = 0; i < 12; ++i) c[i] = 0;
   if (!use_tc(p)) return OFA_OK;
   const TcOperands& t = p->tc;
   c[0] = t.fwd_bn; c[1] = t.fwd_split; c[2] = t.fwd_cg; c[3] = t.bwd_bn; c[4] = t.bwd_cg;
   c[5] = p->K <= 4096 ? 1 : 0; c[6] = t.fwd_rb; c[7] = t.bwd_rb;
+  if (p->loop.ready) {
+    c[8] = 1; c[9] = p->loop.cg; c[10] = p->loop.split; c[11] = p->loop.grid;
+  }
   return OFA_OK;
 }
 
@@ -723,6 +730,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     R(dalloc(&p->c, p->kp));
     R(dalloc(&p->hist, OFA_HIST_CAP));
     R(dalloc(&p->counters, p->kp / 64 + 1));
+    R(dalloc(&p->loop_bar, 4));
     R(dalloc(&p->meas, n_foci));
     if (p->sep) {
       R(dalloc(&p->fxu, (size_t)p->ux * nx));
@@ -898,6 +906,17 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
       p->last_error = err;
       return fail(OFA_ERR_CUDA);
     }
+    p->loop_mode = opt.fused_loop;
+    if (opt.fused_loop != 0) {
+      std::string lerr;
+      const bool ok = loop_eligible(p) &&
+                      loop_prepare(p, opt.loop_config[0], opt.loop_config[1], lerr);
+      if (!ok && opt.fused_loop == 1) {
+        p->last_error = lerr.empty() ? "the fused loop needs K <= 4096" : lerr;
+        return fail(OFA_ERR_UNSUPPORTED);
+      }
+      cudaGetLastError();
+    }
   }
   if (!tc) {
     // FP32 inverse operands, contraction contiguous: conj(Fx)^T, Fy^T (separable: Fyu^T)
@@ -925,6 +944,30 @@ ofa_status ofa_iterate(ofa_plan* p, int n_iter, double threshold, int* iters_don
     return ofa_fail(p, OFA_ERR_INVALID_ARG, "n_iter must be >= 0 and threshold finite");
   cudaSetDevice(p->device);
   const bool use_thr = threshold > 0.0 && threshold < 1.0;
+  if (p->loop.ready) {
+    // one persistent launch runs the n_iter iterations (and stops at the threshold)
+    launch_control(p->st, use_thr ? threshold : 0.0, 1, p->stream);
+    int j0 = -1;
+    const bool need_sync = iters_done || xi;
+    if (need_sync) {
+      ofa_status s = sync_and_check(p);
+      if (s != OFA_OK) return s;
+      j0 = p->st_host->j;
+    }
+    cudaError_t e = launch_loop(p, n_iter, use_thr ? threshold : 0.0, p->stream);
+    if (e != cudaSuccess) return ofa_cuda_check(p, e, "launching the fused loop");
+    if (!need_sync && !use_thr) return OFA_OK;
+    ofa_status s = sync_and_check(p);
+    if (s != OFA_OK) return s;
+    if (iters_done) *iters_done = p->st_host->j - j0;
+    if (xi) {
+      enqueue_forward_current(p, p->stream);
+      s = sync_and_check(p);
+      if (s != OFA_OK) return s;
+      *xi = p->st_host->xi;
+    }
+    return OFA_OK;
+  }
   if (!p->chunk_exec) {
     ofa_status s = build_graph(p, p->chunk_iters, &p->chunk_exec);
     if (s != OFA_OK) return s;
@@ -1250,6 +1293,77 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   cleanup();
   if (st != OFA_OK) return st;
   return ofa_cuda_check(p, cudaGetLastError(), "profiling kernels");
+}
+
+ofa_status ofa_profile_loop(ofa_plan* p, int n_iter, int reps, double* ms_per_iteration,
+                            double* phase_us) {
+  if (!p || n_iter < 1 || reps < 1 || !ms_per_iteration)
+    return ofa_fail(p, OFA_ERR_INVALID_ARG, "bad argument");
+  if (!p->loop.ready) return ofa_fail(p, OFA_ERR_UNSUPPORTED, "the plan does not run the fused loop");
+  cudaSetDevice(p->device);
+  const size_t npix = (size_t)p->nx * p->ny;
+  const size_t e_bytes = (size_t)p->nyp * 2 * p->nxp * p->tc.elem_bytes;
+  float* phi_s = nullptr;
+  float* w_s = nullptr;
+  OfaDevState* st_s = nullptr;
+  void* e_s[2] = {nullptr, nullptr};
+  unsigned long long* clk = nullptr;
+  cudaError_t e = cudaMalloc(&phi_s, npix * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&w_s, (size_t)p->K * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&st_s, sizeof(OfaDevState));
+  if (e == cudaSuccess) e = cudaMalloc(&e_s[0], e_bytes);
+  if (e == cudaSuccess && p->tc.npass == 3) e = cudaMalloc(&e_s[1], e_bytes);
+  if (e == cudaSuccess && phase_us) e = cudaMalloc(&clk, 6 * sizeof(unsigned long long));
+  auto cleanup = [&]() {
+    dfree(clk);
+    dfree(phi_s);
+    dfree(w_s);
+    dfree(st_s);
+    dfree(e_s[0]);
+    dfree(e_s[1]);
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return ofa_cuda_check(p, e, "allocating profile scratch");
+  }
+  cudaStream_t s = p->stream;
+  cudaMemcpyAsync(phi_s, p->phi, npix * 4, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(w_s, p->w, (size_t)p->K * 4, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(st_s, p->st, sizeof(OfaDevState), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(e_s[0], p->tc.e_hi, e_bytes, cudaMemcpyDeviceToDevice, s);
+  if (e_s[1]) cudaMemcpyAsync(e_s[1], p->tc.e_lo, e_bytes, cudaMemcpyDeviceToDevice, s);
+  launch_control(p->st, 0.0, 1, s);
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  e = launch_loop(p, n_iter, 0.0, s);  // warm-up
+  cudaEventRecord(ev0, s);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_loop(p, n_iter, 0.0, s);
+  cudaEventRecord(ev1, s);
+  cudaEventSynchronize(ev1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  *ms_per_iteration = (double)ms / ((double)reps * n_iter);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (phase_us && e == cudaSuccess) {
+    unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
+    cudaMemsetAsync(clk, 0, sizeof(h), s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_loop(p, n_iter, 0.0, s, clk);
+    cudaMemcpyAsync(h, clk, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    for (int i = 0; i < 6; ++i) phase_us[i] = (double)h[i] / 1000.0 / ((double)reps * n_iter);
+  }
+  cudaMemcpyAsync(p->phi, phi_s, npix * 4, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(p->w, w_s, (size_t)p->K * 4, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(p->st, st_s, sizeof(OfaDevState), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(p->tc.e_hi, e_s[0], e_bytes, cudaMemcpyDeviceToDevice, s);
+  if (e_s[1]) cudaMemcpyAsync(p->tc.e_lo, e_s[1], e_bytes, cudaMemcpyDeviceToDevice, s);
+  ofa_status st = sync_and_check(p);
+  cleanup();
+  if (st != OFA_OK) return st;
+  if (e != cudaSuccess) return ofa_cuda_check(p, e, "launching the fused loop");
+  return ofa_cuda_check(p, cudaGetLastError(), "profiling the fused loop");
 }
 
 // ------------------------------------------------------------------ batch

@@ -28,6 +28,7 @@
 #define OFA_HIST_CAP 65536
 #define OFA_ERRBIT_TIMEOUT 1
 #define OFA_ERRBIT_NUMERIC 2
+#define OFA_ERRBIT_LAUNCH 4   // a kernel found its launch shape not the one it was built for
 
 // Loop state and control words that live in device memory.
 struct OfaDevState {
@@ -55,6 +56,16 @@ struct TcOperands {
   int fwd_bn = 256, fwd_split = 1, bwd_bn = 256;
   int fwd_rb = 128, bwd_rb = 128;                          // operand row bytes per stage
   int fwd_cg = 1, bwd_cg = 1;                              // 2 = 2-SM MMA pairs
+};
+
+// Fused loop kernel (all of an iteration in one persistent cooperative launch):
+// its configuration and tensor maps over the plan's operand planes.
+struct LoopOperands {
+  bool ready = false;
+  int cg = 1, split = 1;       // CTA group (2 = 2-SM pairs), forward split of the contraction
+  int grid = 0, smem = 0;      // CTAs (all resident), dynamic shared memory per CTA
+  int kb_fwd = 0, kb_inv = 0;  // k-blocks of the two contractions
+  CUtensorMap tm_e_hi, tm_e_lo, tm_bx_hi, tm_bx_lo, tm_p_hi, tm_p_lo, tm_q_hi, tm_q_lo;
 };
 
 // FP32 form scratch: the inverse's transposed operands and the forward's
@@ -116,6 +127,9 @@ struct ofa_plan {
   int* row_foci = nullptr;             // [K] ... in increasing ix order
   TcOperands tc;
   TcOperands tc_aux;                   // E planes of an external phase (forward/adjoint)
+  LoopOperands loop;                   // fused loop kernel (tensor-core forms, K <= 4096)
+  int loop_mode = -1;                  // ofa_options.fused_loop
+  unsigned* loop_bar = nullptr;        // its three grid barrier counters
   bool aux_ready = false;
 
   cudaGraphExec_t chunk_exec = nullptr;
@@ -230,6 +244,17 @@ void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream
 void launch_bwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s);
 void launch_grad_tc(ofa_plan* p, const TcOperands& t, const float* phi, float scale,
                     float* grad, cudaStream_t s);
+
+// ---------------------------------------------------------------- kernels (k_loop.cu)
+// Whether the fused loop kernel can run this plan (tensor-core form, general form,
+// K <= 4096); loop_prepare picks its configuration (cg, split: 0 = automatic),
+// encodes its tensor maps and checks co-residency; launch_loop runs n iterations
+// in one cooperative launch.
+bool loop_eligible(const ofa_plan* p);
+bool loop_prepare(ofa_plan* p, int cg, int split, std::string& err);
+// clock (nullable, device [6]): accumulates the ns CTA 0 spends per phase.
+cudaError_t launch_loop(ofa_plan* p, int n_iter, double threshold, cudaStream_t s,
+                        unsigned long long* clock = nullptr);
 
 // Batched holograms on the tensor-core path: one grouped launch per product over
 // the tiles of every plan (same precision), the inverse operand build grouped too.

@@ -44,7 +44,8 @@ class ofa_options(C.Structure):
                 ("amplitude", C.c_void_p), ("waist_frac", C.c_double), ("phi0", C.c_void_p),
                 ("mem_space", C.c_int), ("weighting", C.c_int), ("autotune", C.c_int),
                 ("focus_z", C.c_void_p), ("separable", C.c_int),
-                ("kernel_config", C.c_int * 5)]
+                ("kernel_config", C.c_int * 5), ("fused_loop", C.c_int),
+                ("loop_config", C.c_int * 2)]
 
 
 class ofa_stats(C.Structure):
@@ -71,6 +72,7 @@ SIGNATURES = [
     ("ofa_adjoint", _I, [_P, _P, _P, _P, _P]),
     ("ofa_profile_kernels", _I, [_P, _I, _P]),
     ("ofa_plan_config", _I, [_P, _P]),
+    ("ofa_profile_loop", _I, [_P, _I, _I, C.POINTER(_D), _P]),
     ("ofa_plan_info", _I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     ("ofa_batch_create", _I, [C.POINTER(_P), C.POINTER(_P), _I, _P]),
     ("ofa_batch_iterate", _I, [_P, _I]),
@@ -222,11 +224,27 @@ def ofa_profile_kernels(plan, reps: int = 20) -> np.ndarray:
 
 
 def ofa_plan_config(plan) -> dict:
-    c = np.zeros(8, dtype=np.int32)
+    c = np.zeros(12, dtype=np.int32)
     _check(_lib.ofa_plan_config(plan, _ptr(c)), plan)
     keys = ["fwd_bn", "fwd_split", "fwd_cta_group", "inv_bn", "inv_cta_group", "focal_fused",
-            "fwd_row_bytes", "inv_row_bytes"]
+            "fwd_row_bytes", "inv_row_bytes", "fused_loop", "loop_cta_group", "loop_split",
+            "loop_ctas"]
     return dict(zip(keys, (int(x) for x in c)))
+
+
+LOOP_PHASES = ["forward", "barrier_after_forward", "focal", "operand_build",
+               "barrier_after_build", "inverse"]
+
+
+def ofa_profile_loop(plan, n_iter: int = 20, reps: int = 5, phases: bool = False):
+    """Average ms per iteration of the fused loop kernel (OFA_ERR_UNSUPPORTED if unused);
+    with phases=True also the microseconds per iteration of each phase (a dict)."""
+    ms = C.c_double()
+    ph = np.zeros(6, dtype=np.float64) if phases else None
+    _check(_lib.ofa_profile_loop(plan, int(n_iter), int(reps), C.byref(ms), _ptr(ph)), plan)
+    if not phases:
+        return ms.value
+    return ms.value, dict(zip(LOOP_PHASES, (float(x) for x in ph)))
 
 
 def ofa_plan_form(plan) -> dict:
@@ -313,7 +331,8 @@ class Plan:
     def __init__(self, nx, ny, pitch_x, pitch_y, wavelength, focal_length, focus_xy, target,
                  precision="f16x3", amplitude=None, phi0=None, seed=0, weighting=True,
                  stream=None, waist_frac=0.4, mem_space=OFA_MEM_HOST, autotune=True,
-                 focus_z=None, separable=-1, kernel_config=None):
+                 focus_z=None, separable=-1, kernel_config=None, fused_loop=None,
+                 loop_config=None):
         opt = ofa_options_default()
         opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opt.seed = int(seed)
@@ -321,6 +340,10 @@ class Plan:
         opt.weighting = 1 if weighting else 0
         opt.autotune = 1 if autotune else 0
         opt.separable = int(separable)
+        if fused_loop is not None:
+            opt.fused_loop = int(fused_loop)
+        if loop_config is not None:
+            opt.loop_config[0], opt.loop_config[1] = int(loop_config[0]), int(loop_config[1])
         if kernel_config is not None:
             for i, v in enumerate(kernel_config):
                 opt.kernel_config[i] = int(v)

@@ -2,10 +2,13 @@
 
 The autotuner picks, per device and shape, a forward configuration (tile width 128 or
 256 accumulator columns, split-K 1, 2 or 4, single CTAs or 2-SM pairs) and an inverse
-configuration (tile width, CTA group).  Plans here force each configuration through
-ofa_options.kernel_config, so every candidate the autotuner can choose is checked:
+configuration (tile width, CTA group) for the per-product kernels.  Plans here force
+each configuration through ofa_options.kernel_config (with the fused loop off, so the
+iteration runs those kernels), so every candidate the autotuner can choose is checked:
 forward amplitudes from the oracle's iterate, and one iteration of Algorithm 1 from
-that iterate (new weights and new phase).
+that iterate (new weights and new phase).  The fused loop kernel (one persistent
+launch per ofa_iterate call) is checked the same way in each of its configurations
+(CTA group 1 or 2, forward split 1, 2 or 4).
 
 Tolerances (readings of the 1e-5 focus-amplitude bar, per precision form):
   amplitudes   relative L2 over the foci AND max over the foci of | |Theta_gpu| -
@@ -119,7 +122,7 @@ def dev(ofa):
 @pytest.mark.parametrize("config", CONFIGS, ids=cfg_id)
 def test_every_kernel_config_ragged(ofa, dev, prec, config):
     """333 x 250 pupil, 300 foci: every tile ragged in all three dimensions."""
-    cfg = check_plan(ofa, "ragged333x250_300", prec, kernel_config=config)
+    cfg = check_plan(ofa, "ragged333x250_300", prec, kernel_config=config, fused_loop=0)
     assert (cfg["fwd_bn"], cfg["fwd_split"], cfg["fwd_cta_group"], cfg["inv_bn"],
             cfg["inv_cta_group"]) == tuple(config)
 
@@ -127,15 +130,90 @@ def test_every_kernel_config_ragged(ofa, dev, prec, config):
 @pytest.mark.parametrize("config", CONFIGS, ids=cfg_id)
 def test_every_kernel_config_pupil1024_poisson1000(ofa, dev, config):
     """The benchmark workload (1024^2 pupil, 1000 foci) in the default F16X3 form."""
-    cfg = check_plan(ofa, "pupil1024_poisson1000", "f16x3", kernel_config=config)
+    cfg = check_plan(ofa, "pupil1024_poisson1000", "f16x3", kernel_config=config,
+                     fused_loop=0)
     assert cfg["fwd_split"] == config[1]
+
+
+LOOP_CONFIGS = [(cg, split) for cg in (1, 2) for split in (1, 2, 4)]
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("loop", LOOP_CONFIGS, ids=lambda c: "cg{}s{}".format(*c))
+def test_fused_loop_configs_ragged(ofa, dev, prec, loop):
+    """The fused loop kernel in every configuration on the ragged pupil."""
+    cfg = check_plan(ofa, "ragged333x250_300", prec, fused_loop=1, loop_config=loop)
+    assert (cfg["fused_loop"], cfg["loop_cta_group"], cfg["loop_split"]) == (1,) + tuple(loop)
+
+
+@pytest.mark.parametrize("loop", LOOP_CONFIGS, ids=lambda c: "cg{}s{}".format(*c))
+def test_fused_loop_configs_pupil1024_poisson1000(ofa, dev, loop):
+    cfg = check_plan(ofa, "pupil1024_poisson1000", "f16x3", fused_loop=1, loop_config=loop)
+    assert cfg["fused_loop"] == 1 and cfg["loop_ctas"] >= 2
 
 
 @pytest.mark.parametrize("prec", ["fp32", "f16x3", "bf16x3"])
 @pytest.mark.parametrize("name", ["pupil1024_poisson1000", "pupil1920x1152_grid2500"])
 def test_one_step_full_size(ofa, dev, prec, name):
-    """One step from the same iterate at full size, in the autotuner's configuration."""
-    check_plan(ofa, name, prec)
+    """One step from the same iterate at full size, in the default configuration."""
+    cfg = check_plan(ofa, name, prec)
+    assert cfg["fused_loop"] == 0
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "tf32"])
+def test_fused_loop_one_step_1920x1152(ofa, dev, prec):
+    """The fused loop where the CTAs run several units per phase: 1920 x 1152 has an odd
+    number of 128-row tiles (single CTAs), 180 forward and 270 inverse units over the
+    SMs, so the accumulators alternate between two TMEM buffers and Fy is read from
+    global memory in the forward epilogue."""
+    cfg = check_plan(ofa, "pupil1920x1152_grid2500", prec, fused_loop=1)
+    assert cfg["fused_loop"] == 1 and cfg["loop_cta_group"] == 1
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "tf32"])
+def test_fused_loop_matches_per_product_kernels(ofa, dev, prec):
+    """The same 20 iterations with and without the fused loop: the xi histories agree
+    (the two differ only in the order of FP32 sums) and both runs are bitwise
+    repeatable."""
+    w = I.named("pupil256_grid100_uniform")
+    runs = {}
+    for mode in (0, 1, 1):
+        plan = ofa.Plan.from_workload(w, precision=prec, fused_loop=mode)
+        assert ofa.ofa_plan_config(plan.handle)["fused_loop"] == mode
+        plan.iterate(20)
+        runs.setdefault(mode, []).append((plan.xi_history(), plan.phase()))
+        plan.close()
+    h0, h1 = runs[0][0][0], runs[1][0][0]
+    assert np.max(np.abs(h0 - h1)) < (1e-4 if prec == "f16x3" else 2e-3)
+    assert np.array_equal(runs[1][0][1], runs[1][1][1])
+
+
+def test_fused_loop_threshold_and_resume(ofa, dev):
+    """Threshold stop inside one launch, a stopped loop staying stopped, and resume."""
+    w = I.named("pupil256_grid100_uniform")
+    fx, fy = O.plan_matrices(w.nx, w.ny, w.pitch_x, w.pitch_y, w.wavelength, w.focal_length,
+                             w.focus_xy)
+    ref = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, 50, threshold=0.99)
+    plan = ofa.Plan.from_workload(w, precision="f16x3", fused_loop=1)
+    it, _ = plan.iterate(50, threshold=0.99, want_stats=True)
+    assert abs(it - ref["iters"]) <= 1, (it, ref["iters"])
+    hist = plan.xi_history()
+    assert hist[-1] > 0.99 and np.all(hist[:-1] <= 0.99)
+    plan.close()
+    # resume: 7 + 5 iterations equal 12 bit for bit
+    a = ofa.Plan.from_workload(w, precision="f16x3", fused_loop=1)
+    a.iterate(12)
+    full = a.phase()
+    a.close()
+    b = ofa.Plan.from_workload(w, precision="f16x3", fused_loop=1)
+    b.iterate(7)
+    phi7, w7, j7 = b.get_state()
+    b.close()
+    c = ofa.Plan.from_workload(w, precision="f16x3", fused_loop=1)
+    c.set_state(phi7, w7, j7)
+    c.iterate(5)
+    assert np.array_equal(c.phase(), full)
+    c.close()
 
 
 def test_unsupported_config_is_rejected(ofa, dev):

@@ -5,6 +5,8 @@ Tolerances (relative L2 over the foci of | |Theta_gpu| - |Theta_ref| |):
   tf32                 2e-3   one TF32 product (u = 2^-11; measured ~2e-4 on CPU emulation)
   bf16                 1e-2   one BF16 product (u = 2^-8; ~1.5e-3 on CPU emulation)
 Full runs: final xi and uniformity within 1e-3 (absolute) of the oracle.
+One step from the same iterate: weights within 2x and the |E'|-weighted phase within 3x
+the amplitude tolerance.
 """
 import math
 
@@ -18,6 +20,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 AMP_TOL = {"fp32": 1e-5, "f16x3": 1e-5, "bf16x3": 1e-5, "tf32": 2e-3, "bf16": 1e-2}
+# One step from the same iterate: the new weights carry the relative amplitude error of
+# each focus once (w_k scales with 1 / |Theta_k|), the new phase (weighted by |E'|) the
+# weight and phase errors of the focused field plus the inverse product's own rounding.
+W_FACTOR, PHASE_FACTOR = 2.0, 3.0
 ALL = list(AMP_TOL)
 ACCURATE = ["fp32", "f16x3", "bf16x3"]
 
@@ -142,11 +148,11 @@ def test_one_step_from_same_iterate(ofa, dev, prec):
     plan.close()
     assert j == 8
     wrel = np.linalg.norm(w_g - w_new) / np.linalg.norm(w_new)
-    assert wrel < 20 * AMP_TOL[prec], wrel
+    assert wrel < W_FACTOR * AMP_TOL[prec], wrel
     mag = np.abs(back)
     d = np.abs(np.exp(1j * phi_g) - np.exp(1j * np.angle(back)))
     werr = math.sqrt(np.sum((mag * d) ** 2) / np.sum(mag ** 2))
-    assert werr < 20 * AMP_TOL[prec], werr
+    assert werr < PHASE_FACTOR * AMP_TOL[prec], werr
     assert phi_g.min() >= -np.pi and phi_g.max() <= np.pi
 
 
@@ -171,11 +177,11 @@ def test_one_step_split_contraction_ragged(ofa, dev, prec):
     plan.close()
     assert j == 5
     wrel = np.linalg.norm(w_g - w_new) / np.linalg.norm(w_new)
-    assert wrel < 20 * AMP_TOL[prec], wrel
+    assert wrel < W_FACTOR * AMP_TOL[prec], wrel
     mag = np.abs(back)
     d = np.abs(np.exp(1j * phi_g) - np.exp(1j * np.angle(back)))
     werr = math.sqrt(np.sum((mag * d) ** 2) / np.sum(mag ** 2))
-    assert werr < 20 * AMP_TOL[prec], werr
+    assert werr < PHASE_FACTOR * AMP_TOL[prec], werr
 
 
 def test_deterministic_split_contraction(ofa, dev):
