@@ -119,6 +119,13 @@ typedef struct ofa_options {
                                 it */
   int loop_config[2];        /* fused loop: {CTA group (1, or 2 for 2-SM pairs), forward split
                                 of the contraction (1..4)}; zeros = chosen at creation */
+  int shard_row0;
+  int shard_ny_total;        /* row shard (see ofa_shard_forward): this plan holds pupil rows
+                                [shard_row0, shard_row0 + ny) of a pupil of shard_ny_total rows;
+                                pupil row n sits at v = (shard_row0 + n - (shard_ny_total - 1)/2)
+                                pitch_y, and the default amplitude and phase are that pupil's
+                                rows.  Both 0 = the whole pupil (default).  Not with the
+                                separable form. */
 } ofa_options;
 
 typedef struct ofa_stats {
@@ -238,6 +245,60 @@ ofa_status ofa_forward(ofa_plan* plan, const float* phi, float* theta, float* in
  */
 ofa_status ofa_adjoint(ofa_plan* plan, const float* phi, const float* theta,
                        const float* grad_intensity, float* grad_phi);
+
+/*
+ * Row shards -- one hologram split by pupil rows over several plans (devices or ranks).
+ * Eq. 2 separates over the pupil rows: Theta_k = sum over the shards of
+ * sum_{n in shard} Fy[k,n] sum_m E[n,m] Fx[k,m].  So each shard (a plan created with
+ * ofa_options.shard_row0 / shard_ny_total) computes its partial Theta, the partials are
+ * summed over the shards (an all-reduce of K complex values), and each shard runs the
+ * generalized weighting update on the sum -- identically, so every shard keeps the same
+ * weights -- and the inverse product for its own rows:
+ *   ofa_shard_forward  theta_partial (device [K] complex, the plan's amplitude units) =
+ *                      Eq. 2 at the foci over this shard's rows at its current phase
+ *   ofa_shard_update   theta_total (device [K] complex, the sum of all shards' partials):
+ *                      intensities, xi (recorded in the plan's history), w <- w
+ *                      sqrt(I~/I), focused field, inverse product and phi = arg for this
+ *                      shard's rows; j advances by one
+ * Both enqueue on the plan's stream.  The caller sums the partials in a fixed order to
+ * keep runs reproducible.  Threshold stops are the caller's (compare xi across calls).
+ */
+ofa_status ofa_shard_forward(ofa_plan* plan, float* theta_partial);
+ofa_status ofa_shard_update(ofa_plan* plan, const float* theta_total);
+
+/*
+ * ofa_loss_adjoint -- the intensity loss of the differentiable form and its gradient,
+ * all in the library: from the theta that ofa_forward returned for phi,
+ *   L = sum_k (I_k / S - t_k)^2,  I = |theta|^2,  S = sum I,  t = I~ / sum I~,
+ *   g_k = dL/dI_k = (2 / S) [(I_k / S - t_k) - sum_j (I_j / S - t_j) I_j / S],
+ * and grad_phi = dL/dphi = 2 Im(conj(E) B), B = P_MTP^H(g * theta) (the adjoint product
+ * of ofa_adjoint).  S and the sums are reduced in FP64.
+ *   phi, theta   device [ny][nx], [K] complex (as for ofa_adjoint)
+ *   grad_phi     device [ny][nx] output
+ *   loss_hist    device float array of loss_capacity (>= 1) values (nullable):
+ *                loss_hist[*step] = L (or [0] if step is NULL); an index outside
+ *                [0, loss_capacity) is not written
+ *   step         device int (nullable), e.g. the counter of ofa_adam_step
+ * Enqueued on the plan's stream.  Buffers the caller initialises on another stream must
+ * be ready before the call (the library orders nothing across streams).  (The loss is
+ * this library's reading of the paper's intensity-precision goal; the paper itself
+ * optimises by GSW, not by gradients.)
+ */
+ofa_status ofa_loss_adjoint(ofa_plan* plan, const float* phi, const float* theta,
+                            float* grad_phi, float* loss_hist, int loss_capacity,
+                            const int* step);
+
+/*
+ * ofa_adam_step -- one Adam update of the phase (Kingma and Ba; the bias-corrected form
+ * with torch's order of operations): t = *step + 1, m <- b1 m + (1 - b1) g,
+ * v <- b2 v + (1 - b2) g^2, phi <- phi - lr / (1 - b1^t) m / (sqrt(v) / sqrt(1 - b2^t) + eps),
+ * then *step = t.  phi, grad_phi, m, v are device [ny][nx] float32 (m and v zero at the
+ * start), step a device int (0 at the start).  lr > 0, 0 <= b1, b2 < 1, eps > 0, else
+ * OFA_ERR_INVALID_ARG.  Enqueued on the plan's stream; the step counter lives on the
+ * device so that a captured CUDA graph of forward, loss adjoint and update replays.
+ */
+ofa_status ofa_adam_step(ofa_plan* plan, float* phi, const float* grad_phi, float* m, float* v,
+                         int* step, float lr, float beta1, float beta2, float eps);
 
 /*
  * ofa_profile_kernels -- measurement aid: average device time (ms) of each kernel

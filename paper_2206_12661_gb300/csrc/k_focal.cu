@@ -306,6 +306,95 @@ __global__ void __launch_bounds__(FT) grad_c_kernel(const float2* __restrict__ t
   if (threadIdx.x == 0) st->c_scale = scale;
 }
 
+// The intensity loss of the differentiable form and the start of its adjoint, one
+// block: I_k = |Theta_k|^2, S = sum I, Ihat = I / S, d = Ihat - t,
+//   L = sum_k d_k^2,   g_k = dL/dI_k = (2 / S) (d_k - sum_j d_j Ihat_j),
+// then c_k = g_k Theta_k scaled by the power of two that brings max |c| into [1/2, 1)
+// (recorded in st->c_scale; the gradient epilogue divides it out).  S, L and the inner
+// sum are reduced in FP64.  loss_hist[*step] (or [0] without a step counter) = L when
+// that index lies in [0, loss_cap).
+__global__ void __launch_bounds__(FT) loss_grad_c_kernel(const float2* __restrict__ theta,
+                                                         const float* __restrict__ t, int K,
+                                                         int kp, float2* __restrict__ c,
+                                                         OfaDevState* __restrict__ st,
+                                                         float* __restrict__ loss_hist,
+                                                         int loss_cap,
+                                                         const int* __restrict__ step) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < K; k += FT) {
+    const float2 a = theta[k];
+    s += (double)a.x * a.x + (double)a.y * a.y;
+  }
+  const double S = block_sum(s, sh);
+  const double inv_s = S > 0.0 ? 1.0 / S : 0.0;
+  double l = 0.0, dsum = 0.0;
+  for (int k = threadIdx.x; k < K; k += FT) {
+    const float2 a = theta[k];
+    const double ih = ((double)a.x * a.x + (double)a.y * a.y) * inv_s;
+    const double d = ih - (double)t[k];
+    l += d * d;
+    dsum += d * ih;
+  }
+  const double L = block_sum(l, sh);
+  const double D = block_sum(dsum, sh);
+  double mx = 0.0;
+  for (int k = threadIdx.x; k < K; k += FT) {
+    const float2 a = theta[k];
+    const double ih = ((double)a.x * a.x + (double)a.y * a.y) * inv_s;
+    const double g = 2.0 * inv_s * ((ih - (double)t[k]) - D);
+    mx = fmax(mx, fabs(g) * sqrt((double)a.x * a.x + (double)a.y * a.y));
+  }
+  mx = block_max(mx, sh);
+  int e = 0;
+  frexp(mx, &e);
+  const double scale = mx > 0.0 ? ldexp(1.0, -e) : 1.0;
+  for (int k = threadIdx.x; k < kp; k += FT) {
+    float2 ck = make_float2(0.f, 0.f);
+    if (k < K) {
+      const float2 a = theta[k];
+      const double ih = ((double)a.x * a.x + (double)a.y * a.y) * inv_s;
+      const double g = 2.0 * inv_s * ((ih - (double)t[k]) - D) * scale;
+      ck = make_float2((float)(g * a.x), (float)(g * a.y));
+    }
+    c[k] = ck;
+  }
+  if (threadIdx.x == 0) {
+    st->c_scale = (float)scale;
+    const int i = step ? *step : 0;
+    if (loss_hist && i >= 0 && i < loss_cap) loss_hist[i] = (float)L;
+  }
+}
+
+// One Adam update of n parameters (the published algorithm with torch's defaults for
+// the order of operations): t = *step + 1, m <- b1 m + (1 - b1) g,
+// v <- b2 v + (1 - b2) g^2, x <- x - lr / (1 - b1^t) m / (sqrt(v) / sqrt(1 - b2^t) + eps).
+__global__ void adam_kernel(float* __restrict__ x, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v,
+                            const int* __restrict__ step, size_t n, float lr, float b1, float b2,
+                            float eps) {
+  // the bias corrections once per block (FP64 is slow on this GPU: not per element)
+  __shared__ float sc[2];
+  if (threadIdx.x == 0) {
+    const int t = *step + 1;
+    sc[0] = (float)((double)lr / (1.0 - pow((double)b1, (double)t)));
+    sc[1] = (float)sqrt(1.0 - pow((double)b2, (double)t));
+  }
+  __syncthreads();
+  const float step_size = sc[0], bc2_sqrt = sc[1];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    x[i] -= step_size * (mi / (sqrtf(vi) / bc2_sqrt + eps));
+  }
+}
+
+__global__ void step_increment_kernel(int* step) { *step += 1; }
+
 // P[n][2k..2k+1] = conj(Fy[k,n]) c_k in the operand format of the precision;
 // four foci per thread (kp is a multiple of 128): 16-byte loads and stores.
 __global__ void build_p_kernel(const float2* __restrict__ fyT, const float2* __restrict__ c,
@@ -432,6 +521,20 @@ void launch_set_j(OfaDevState* st, int j, int reset_hist, cudaStream_t s) {
 void launch_grad_c(const float2* theta, const float* g, int K, int kp, float in_scale, float2* c,
                    OfaDevState* st, cudaStream_t s) {
   grad_c_kernel<<<1, FT, 0, s>>>(theta, g, K, kp, in_scale, c, st);
+}
+
+void launch_loss_grad_c(const float2* theta, const float* t, int K, int kp, float2* c,
+                        OfaDevState* st, float* loss_hist, int loss_cap, const int* step,
+                        cudaStream_t s) {
+  loss_grad_c_kernel<<<1, FT, 0, s>>>(theta, t, K, kp, c, st, loss_hist, loss_cap, step);
+}
+
+void launch_adam(float* x, const float* g, float* m, float* v, int* step, size_t n, float lr,
+                 float b1, float b2, float eps, cudaStream_t s) {
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, g, m, v, step, n, lr, b1, b2, eps);
+  step_increment_kernel<<<1, 1, 0, s>>>(step);
 }
 
 void launch_build_p(const float2* fyT, const float2* c, const int* done, int nyp, int kp,

@@ -14,16 +14,18 @@ namespace {
 // Fx[k][m] = exp(-i 2 pi (x_k u_m / (lambda f) + z_k u_m^2 / (2 lambda f^2))): the
 // DFT row of Eq. 2 and, for a 3D focus (focus_z non-NULL), the separable Fresnel
 // defocus phase of the pupil function that moves the focus z_k off the focal plane.
+// Pupil sample m sits at u_m = (m - origin) pitch: origin = (n - 1) / 2 centres a
+// whole pupil; a shard of rows passes the axis position of the whole pupil.
 __global__ void dft_rows_kernel(const double* __restrict__ focus_xy,
                                 const double* __restrict__ focus_z, int coord, int K, int n,
-                                double pitch, double lam_f, double lam_f2,
+                                double pitch, double origin, double lam_f, double lam_f2,
                                 float2* __restrict__ out) {
   size_t total = (size_t)K * n;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
     int k = (int)(i / n);
     int m = (int)(i % n);
-    double u = ((double)m - 0.5 * (double)(n - 1)) * pitch;
+    double u = ((double)m - origin) * pitch;
     double turns = focus_xy[2 * (size_t)k + coord] * u / lam_f;
     if (focus_z != nullptr) turns += focus_z[k] * u * u / (2.0 * lam_f2);
     double r = turns - rint(turns);                 // FP64 reduction to [-1/2, 1/2]
@@ -33,15 +35,15 @@ __global__ void dft_rows_kernel(const double* __restrict__ focus_xy,
   }
 }
 
-__global__ void default_amplitude_kernel(float* __restrict__ amp, int nx, int ny, double px,
-                                         double py, double wf) {
+__global__ void default_amplitude_kernel(float* __restrict__ amp, int nx, int ny, int row0,
+                                         int ny_total, double px, double py, double wf) {
   size_t total = (size_t)nx * ny;
-  double wx = wf * nx * px, wy = wf * ny * py;
+  double wx = wf * nx * px, wy = wf * ny_total * py;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
     int n = (int)(i / nx), m = (int)(i % nx);
     double u = ((double)m - 0.5 * (nx - 1)) * px;
-    double v = ((double)n - 0.5 * (ny - 1)) * py;
+    double v = ((double)(n + row0) - 0.5 * (ny_total - 1)) * py;
     amp[i] = (float)exp(-(u * u / (wx * wx) + v * v / (wy * wy)));
   }
 }
@@ -54,11 +56,12 @@ __device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-__global__ void default_phase_kernel(float* __restrict__ phi, size_t total, uint64_t seed) {
+__global__ void default_phase_kernel(float* __restrict__ phi, size_t total, size_t index0,
+                                     uint64_t seed) {
   const uint64_t gamma = 0x9E3779B97F4A7C15ull;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
-    uint64_t v = splitmix64_mix(seed + (uint64_t)(i + 1) * gamma);
+    uint64_t v = splitmix64_mix(seed + (uint64_t)(i + index0 + 1) * gamma);
     double u01 = (double)(v >> 11) * (1.0 / 9007199254740992.0);
     phi[i] = (float)(u01 * 6.283185307179586 - 3.141592653589793);
   }
@@ -137,18 +140,21 @@ inline int grid_for(size_t n, int threads = 256) {
 }  // namespace
 
 void launch_dft_rows(const double* focus_xy, const double* focus_z, int coord, int K, int n,
-                     double pitch, double lam_f, double lam_f2, float2* out, cudaStream_t s) {
+                     double pitch, double origin, double lam_f, double lam_f2, float2* out,
+                     cudaStream_t s) {
   dft_rows_kernel<<<grid_for((size_t)K * n), 256, 0, s>>>(focus_xy, focus_z, coord, K, n, pitch,
-                                                           lam_f, lam_f2, out);
+                                                           origin, lam_f, lam_f2, out);
 }
 
-void launch_default_amplitude(float* amp, int nx, int ny, double px, double py, double wf,
-                              cudaStream_t s) {
-  default_amplitude_kernel<<<grid_for((size_t)nx * ny), 256, 0, s>>>(amp, nx, ny, px, py, wf);
+void launch_default_amplitude(float* amp, int nx, int ny, int row0, int ny_total, double px,
+                              double py, double wf, cudaStream_t s) {
+  default_amplitude_kernel<<<grid_for((size_t)nx * ny), 256, 0, s>>>(amp, nx, ny, row0, ny_total,
+                                                                      px, py, wf);
 }
 
-void launch_default_phase(float* phi, int nx, int ny, uint64_t seed, cudaStream_t s) {
-  default_phase_kernel<<<grid_for((size_t)nx * ny), 256, 0, s>>>(phi, (size_t)nx * ny, seed);
+void launch_default_phase(float* phi, int nx, int ny, int row0, uint64_t seed, cudaStream_t s) {
+  default_phase_kernel<<<grid_for((size_t)nx * ny), 256, 0, s>>>(phi, (size_t)nx * ny,
+                                                                  (size_t)row0 * nx, seed);
 }
 
 void launch_scale(float* x, size_t n, float f, cudaStream_t s) {

@@ -599,13 +599,24 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   ofa_status vs = ofa_check_foci(n_foci, xy.data(), pitch_x, pitch_y, wavelength, focal_length,
                                  nullptr);
   if (vs != OFA_OK) return vs;
+  // row shard: rows [row0, row0 + ny) of a pupil of ny_total rows
+  const bool shard = opt.shard_ny_total != 0;
+  const int row0 = shard ? opt.shard_row0 : 0;
+  const int ny_total = shard ? opt.shard_ny_total : ny;
+  if (shard && (row0 < 0 || opt.shard_ny_total < ny || row0 > opt.shard_ny_total - ny))
+    return ofa_fail(nullptr, OFA_ERR_INVALID_ARG,
+                    "a row shard needs 0 <= shard_row0 and shard_row0 + ny <= shard_ny_total");
+  if (!shard && opt.shard_row0 != 0)
+    return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "shard_row0 needs shard_ny_total");
+  if (shard && opt.separable == 1)
+    return ofa_fail(nullptr, OFA_ERR_UNSUPPORTED, "the separable form runs whole pupils only");
   if (opt.focus_z) {
     // the defocus phase shifts the local spatial frequency at the pupil edge by
     // z u_max / (lambda f^2): the effective position |x| + |z| u_max / f must stay
     // inside the alias-free field
     const double hx = wavelength * focal_length / (2.0 * pitch_x);
     const double hy = wavelength * focal_length / (2.0 * pitch_y);
-    const double ux = 0.5 * (nx - 1) * pitch_x, uy = 0.5 * (ny - 1) * pitch_y;
+    const double ux = 0.5 * (nx - 1) * pitch_x, uy = 0.5 * (ny_total - 1) * pitch_y;
     for (int k = 0; k < n_foci; ++k) {
       const double z = zz[k];
       if (!std::isfinite(z))
@@ -642,6 +653,8 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   p->device = dev;
   p->nx = nx;
   p->ny = ny;
+  p->row0 = row0;
+  p->ny_total = ny_total;
   p->K = n_foci;
   p->precision = opt.precision;
   p->weighting = opt.weighting ? 1 : 0;
@@ -657,7 +670,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   // y coordinates, Eq. 2 factors through those values (Theta on the grid is
   // Fyu E Fxu^T), costing nx ny (ux + uy) complex products instead of 2 nx ny K.
   std::vector<double> xs, ys;
-  if (opt.separable != 0 && !opt.focus_z) {
+  if (opt.separable != 0 && !opt.focus_z && !shard) {
     for (int k = 0; k < n_foci; ++k) {
       xs.push_back(xy[2 * k]);
       ys.push_back(xy[2 * k + 1]);
@@ -802,9 +815,11 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
       ce = cudaMemcpy(p->ones, ones.data(), ones.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) {
       const double lf = wavelength * focal_length;
-      launch_dft_rows(dcoord, nullptr, 0, p->ux, nx, pitch_x, lf, lf * focal_length, p->fxu,
+      launch_dft_rows(dcoord, nullptr, 0, p->ux, nx, pitch_x, 0.5 * (nx - 1), lf, lf * focal_length,
+                      p->fxu,
                       p->stream);
-      launch_dft_rows(dcoord + ux2.size(), nullptr, 1, p->uy, ny, pitch_y, lf, lf * focal_length,
+      launch_dft_rows(dcoord + ux2.size(), nullptr, 1, p->uy, ny, pitch_y, 0.5 * (ny - 1), lf,
+                      lf * focal_length,
                       p->fyu, p->stream);
       ce = cudaStreamSynchronize(p->stream);
     }
@@ -830,7 +845,8 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
                             p->stream),
             "copy amplitude");
   } else {
-    launch_default_amplitude(p->amp, nx, ny, pitch_x, pitch_y, opt.waist_frac, p->stream);
+    launch_default_amplitude(p->amp, nx, ny, row0, ny_total, pitch_x, pitch_y, opt.waist_frac,
+                             p->stream);
   }
   std::vector<float> ah;
   const float* av = opt.amplitude;
@@ -863,15 +879,17 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
                             p->stream),
             "copy phi0");
   } else {
-    launch_default_phase(p->phi, nx, ny, opt.seed, p->stream);
+    launch_default_phase(p->phi, nx, ny, row0, opt.seed, p->stream);
   }
 
   // Kernel (a): DFT rows with FP64 phase reduction.
   const double lam_f = wavelength * focal_length;
   const double lam_f2 = lam_f * focal_length;
-  launch_dft_rows(p->focus_xy, p->focus_z, 0, n_foci, nx, pitch_x, lam_f, lam_f2, p->fx,
+  launch_dft_rows(p->focus_xy, p->focus_z, 0, n_foci, nx, pitch_x, 0.5 * (nx - 1), lam_f, lam_f2,
+                  p->fx,
                   p->stream);
-  launch_dft_rows(p->focus_xy, p->focus_z, 1, n_foci, ny, pitch_y, lam_f, lam_f2, p->fy,
+  launch_dft_rows(p->focus_xy, p->focus_z, 1, n_foci, ny, pitch_y, 0.5 * (ny_total - 1) - row0,
+                  lam_f, lam_f2, p->fy,
                   p->stream);
   if (tc) {
     launch_transpose_fy(p->fy, n_foci, ny, p->kp, p->nyp, p->fyT, p->stream);
@@ -1173,6 +1191,51 @@ ofa_status ofa_forward(ofa_plan* p, const float* phi, float* theta, float* inten
   return ofa_cuda_check(p, cudaGetLastError(), "launching forward");
 }
 
+ofa_status ofa_shard_forward(ofa_plan* p, float* theta_partial) {
+  if (!p || !theta_partial) return ofa_fail(p, OFA_ERR_INVALID_ARG, "NULL argument");
+  cudaSetDevice(p->device);
+  // the forward at the loop's current phase (the plan's own field), output only
+  float2* th = reinterpret_cast<float2*>(theta_partial);
+  const float out_scale = ldexpf(1.f, p->amp_exp);
+  if (p->sep) {
+    enqueue_sep_forward(p, p->e32, p->stream);
+    launch_focal(p->part, 1, p->kp, p->K, p->t, p->w, th, p->inten, p->c, p->hist, p->st, 2,
+                 p->weighting, out_scale, p->amp_energy, p->stream);
+  } else if (!use_tc(p)) {
+    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr, p->simt,
+                    p->stream);
+    launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, th, p->inten, p->c,
+                 p->hist, p->st, 2, p->weighting, out_scale, p->amp_energy, p->stream);
+  } else {
+    launch_fwd_tc(p, p->tc, nullptr, p->stream, false);
+    launch_focal(p->part, fwd_n_part(p->nyp, p->tc), p->kp, p->K, p->t, p->w, th, p->inten, p->c,
+                 p->hist, p->st, 2, p->weighting, out_scale, p->amp_energy, p->stream);
+  }
+  return ofa_cuda_check(p, cudaGetLastError(), "launching the shard forward");
+}
+
+ofa_status ofa_shard_update(ofa_plan* p, const float* theta_total) {
+  if (!p || !theta_total) return ofa_fail(p, OFA_ERR_INVALID_ARG, "NULL argument");
+  cudaSetDevice(p->device);
+  // statistics, weight update and focused field from the summed Theta (one partial
+  // row of K values), then the inverse product and projection for this shard's rows
+  cudaStream_t s = p->stream;
+  launch_control(p->st, 0.0, 1, s);
+  launch_focal(reinterpret_cast<const float2*>(theta_total), 1, p->kp, p->K, p->t, p->w,
+               p->theta, p->inten, p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
+  if (p->sep) {
+    launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj, s);
+    enqueue_sep_inverse(p, nullptr, s);
+  } else if (use_tc(p)) {
+    launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
+    launch_bwd_tc(p, p->tc, nullptr, s);
+  } else {
+    launch_bwd_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
+                    nullptr, p->simt, s);
+  }
+  return ofa_cuda_check(p, cudaGetLastError(), "launching the shard update");
+}
+
 ofa_status ofa_adjoint(ofa_plan* p, const float* phi, const float* theta,
                        const float* grad_intensity, float* grad_phi) {
   if (!p || !phi || !theta || !grad_intensity || !grad_phi)
@@ -1196,6 +1259,44 @@ ofa_status ofa_adjoint(ofa_plan* p, const float* phi, const float* theta,
     launch_grad_tc(p, p->tc, phi, amp_factor, grad_phi, p->stream);
   }
   return ofa_cuda_check(p, cudaGetLastError(), "launching adjoint");
+}
+
+ofa_status ofa_loss_adjoint(ofa_plan* p, const float* phi, const float* theta, float* grad_phi,
+                            float* loss_hist, int loss_capacity, const int* step) {
+  if (!p || !phi || !theta || !grad_phi) return ofa_fail(p, OFA_ERR_INVALID_ARG, "NULL argument");
+  if (loss_hist && loss_capacity < 1)
+    return ofa_fail(p, OFA_ERR_INVALID_ARG, "loss_capacity must be >= 1 with loss_hist");
+  cudaSetDevice(p->device);
+  launch_loss_grad_c(reinterpret_cast<const float2*>(theta), p->t, p->K, p->kp, p->c, p->st,
+                     loss_hist, loss_hist ? loss_capacity : 0, step, p->stream);
+  const float amp_factor = ldexpf(1.f, p->amp_exp);
+  if (p->sep) {
+    launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj,
+                 p->stream);
+    sep_transpose_t(p, p->stream);
+    launch_grad_simt(p->ones, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->uy, phi, p->amp,
+                     amp_factor, p->st, grad_phi, p->simt, p->stream);
+  } else if (!use_tc(p)) {
+    launch_grad_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, phi, p->amp,
+                     amp_factor, p->st, grad_phi, p->simt, p->stream);
+  } else {
+    launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo,
+                   p->stream);
+    launch_grad_tc(p, p->tc, phi, amp_factor, grad_phi, p->stream);
+  }
+  return ofa_cuda_check(p, cudaGetLastError(), "launching the loss adjoint");
+}
+
+ofa_status ofa_adam_step(ofa_plan* p, float* phi, const float* grad_phi, float* m, float* v,
+                         int* step, float lr, float beta1, float beta2, float eps) {
+  if (!p || !phi || !grad_phi || !m || !v || !step)
+    return ofa_fail(p, OFA_ERR_INVALID_ARG, "NULL argument");
+  if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
+      !(eps > 0.f))
+    return ofa_fail(p, OFA_ERR_INVALID_ARG, "Adam needs lr > 0, 0 <= betas < 1, eps > 0");
+  cudaSetDevice(p->device);
+  launch_adam(phi, grad_phi, m, v, step, (size_t)p->nx * p->ny, lr, beta1, beta2, eps, p->stream);
+  return ofa_cuda_check(p, cudaGetLastError(), "launching the Adam update");
 }
 
 ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {

@@ -86,6 +86,7 @@ struct ofa_plan {
   cudaStream_t cap_stream = nullptr;   // private stream used only for graph capture
   bool own_stream = false;
   int nx = 0, ny = 0, K = 0, precision = 0, weighting = 1;
+  int row0 = 0, ny_total = 0;          // row shard: rows [row0, row0 + ny) of ny_total
   double px = 0, py = 0, lambda = 0, focal = 0;
   int nxp = 0, nyp = 0, kp = 0;        // padded sizes (tensor-core tiles)
   int amp_exp = 0;                     // stored A = user A * 2^-amp_exp
@@ -150,11 +151,15 @@ ofa_status ofa_cuda_check(ofa_plan* p, cudaError_t e, const char* what);
 void ofa_set_thread_error(const std::string& msg);
 
 // ---------------------------------------------------------------- kernels (k_gen.cu)
+// origin: index of the optical axis along the sampled coordinate ((n - 1) / 2 for a
+// whole pupil; a row shard passes the whole pupil's axis relative to its first row).
 void launch_dft_rows(const double* focus_xy, const double* focus_z, int coord, int K, int n,
-                     double pitch, double lam_f, double lam_f2, float2* out, cudaStream_t s);
-void launch_default_amplitude(float* amp, int nx, int ny, double px, double py, double waist_frac,
-                              cudaStream_t s);
-void launch_default_phase(float* phi, int nx, int ny, uint64_t seed, cudaStream_t s);
+                     double pitch, double origin, double lam_f, double lam_f2, float2* out,
+                     cudaStream_t s);
+// rows [row0, row0 + ny) of the default amplitude / phase of a pupil of ny_total rows
+void launch_default_amplitude(float* amp, int nx, int ny, int row0, int ny_total, double px,
+                              double py, double waist_frac, cudaStream_t s);
+void launch_default_phase(float* phi, int nx, int ny, int row0, uint64_t seed, cudaStream_t s);
 void launch_scale(float* x, size_t n, float f, cudaStream_t s);
 // dst [nyp][kp] = src [K][ny] transposed (conjugated when conj), zero padded
 void launch_transpose_fy(const float2* fy, int K, int ny, int kp, int nyp, float2* fyT,
@@ -224,6 +229,15 @@ void launch_grad_c(const float2* theta, const float* g, int K, int kp, float in_
                    float2* c, OfaDevState* st, cudaStream_t s);
 void launch_build_p(const float2* fyT, const float2* c, const int* done, int nyp, int kp,
                     int prec, void* hi, void* lo, cudaStream_t s);
+// Intensity loss sum (I/S - t)^2 of Theta, its gradient g = dL/dI folded into
+// c = g Theta (scaled; st->c_scale), loss_hist[*step] = L when the index lies in
+// [0, loss_cap) (step, loss_hist nullable).
+void launch_loss_grad_c(const float2* theta, const float* t, int K, int kp, float2* c,
+                        OfaDevState* st, float* loss_hist, int loss_cap, const int* step,
+                        cudaStream_t s);
+// Adam update of n parameters with the device step counter (then incremented).
+void launch_adam(float* x, const float* g, float* m, float* v, int* step, size_t n, float lr,
+                 float b1, float b2, float eps, cudaStream_t s);
 
 // ---------------------------------------------------------------- kernels (k_umma.cu)
 cudaError_t tc_prepare(int prec);

@@ -45,7 +45,8 @@ class ofa_options(C.Structure):
                 ("mem_space", C.c_int), ("weighting", C.c_int), ("autotune", C.c_int),
                 ("focus_z", C.c_void_p), ("separable", C.c_int),
                 ("kernel_config", C.c_int * 5), ("fused_loop", C.c_int),
-                ("loop_config", C.c_int * 2)]
+                ("loop_config", C.c_int * 2), ("shard_row0", C.c_int),
+                ("shard_ny_total", C.c_int)]
 
 
 class ofa_stats(C.Structure):
@@ -73,6 +74,10 @@ SIGNATURES = [
     ("ofa_profile_kernels", _I, [_P, _I, _P]),
     ("ofa_plan_config", _I, [_P, _P]),
     ("ofa_profile_loop", _I, [_P, _I, _I, C.POINTER(_D), _P]),
+    ("ofa_shard_forward", _I, [_P, _P]),
+    ("ofa_loss_adjoint", _I, [_P, _P, _P, _P, _P, _I, _P]),
+    ("ofa_adam_step", _I, [_P, _P, _P, _P, _P, _P, C.c_float, C.c_float, C.c_float, C.c_float]),
+    ("ofa_shard_update", _I, [_P, _P]),
     ("ofa_plan_info", _I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     ("ofa_batch_create", _I, [C.POINTER(_P), C.POINTER(_P), _I, _P]),
     ("ofa_batch_iterate", _I, [_P, _I]),
@@ -211,6 +216,25 @@ def ofa_forward(plan, phi, theta=None, intensity=None):
     _check(_lib.ofa_forward(plan, _ptr(phi), _ptr(theta), _ptr(intensity)), plan)
 
 
+def ofa_loss_adjoint(plan, phi, theta, grad_phi, loss_hist=None, step=None):
+    cap = int(loss_hist.numel()) if loss_hist is not None else 0
+    _check(_lib.ofa_loss_adjoint(plan, _ptr(phi), _ptr(theta), _ptr(grad_phi), _ptr(loss_hist),
+                                 cap, _ptr(step)), plan)
+
+
+def ofa_adam_step(plan, phi, grad_phi, m, v, step, lr=0.05, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(_lib.ofa_adam_step(plan, _ptr(phi), _ptr(grad_phi), _ptr(m), _ptr(v), _ptr(step),
+                              float(lr), float(beta1), float(beta2), float(eps)), plan)
+
+
+def ofa_shard_forward(plan, theta_partial):
+    _check(_lib.ofa_shard_forward(plan, _ptr(theta_partial)), plan)
+
+
+def ofa_shard_update(plan, theta_total):
+    _check(_lib.ofa_shard_update(plan, _ptr(theta_total)), plan)
+
+
 def ofa_adjoint(plan, phi, theta, grad_intensity, grad_phi):
     _check(_lib.ofa_adjoint(plan, _ptr(phi), _ptr(theta), _ptr(grad_intensity), _ptr(grad_phi)),
            plan)
@@ -332,7 +356,7 @@ class Plan:
                  precision="f16x3", amplitude=None, phi0=None, seed=0, weighting=True,
                  stream=None, waist_frac=0.4, mem_space=OFA_MEM_HOST, autotune=True,
                  focus_z=None, separable=-1, kernel_config=None, fused_loop=None,
-                 loop_config=None):
+                 loop_config=None, shard=None):
         opt = ofa_options_default()
         opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opt.seed = int(seed)
@@ -340,6 +364,8 @@ class Plan:
         opt.weighting = 1 if weighting else 0
         opt.autotune = 1 if autotune else 0
         opt.separable = int(separable)
+        if shard is not None:           # (row0, ny_total): rows [row0, row0 + ny)
+            opt.shard_row0, opt.shard_ny_total = int(shard[0]), int(shard[1])
         if fused_loop is not None:
             opt.fused_loop = int(fused_loop)
         if loop_config is not None:
@@ -365,6 +391,8 @@ class Plan:
         self.nx, self.ny, self.K = int(nx), int(ny), int(focus_xy.shape[0])
         self.handle = ofa_plan_create(nx, ny, pitch_x, pitch_y, wavelength, focal_length,
                                       focus_xy, target, opt)
+        # the stream the caller gave (None or 0: a stream the library created)
+        self.stream = int(stream) if stream else None
         self._keep = None
 
     @classmethod
