@@ -17,8 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libofa.so")
-SOURCES = ["ofa_api.cu", "k_gen.cu", "k_simt.cu", "k_focal.cu", "k_umma.cu", "k_loop.cu",
-           "k_noalloc.cu"]
+SOURCES = ["ofa_api.cu", "k_gen.cu", "k_simt.cu", "k_sep.cu", "k_focal.cu", "k_umma.cu",
+           "k_loop.cu", "k_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

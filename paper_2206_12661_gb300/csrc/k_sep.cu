@@ -1,0 +1,554 @@
+// Separable grid form of one loop iteration in three launches (FP32, CUDA cores).
+//
+// With the foci on the grid of their U_x distinct x and U_y distinct y values, Eq. 2 at
+// focus k = (ix_k, iy_k) is Theta_k = sum_n Fyu[iy_k][n] G[n][ix_k] with the first
+// product G[n][ix] = sum_m E[n][m] Fxu[ix][m], and the adjoint factors the same way:
+// E'[n][m] = sum_iy conj(Fyu[iy][n]) T[iy][m], T[iy][m] = sum_ix C[iy][ix] conj(Fxu[ix][m])
+// with C the focused field c laid out on the grid (zero where the grid has no focus).
+//
+//   sep_fwd_kernel        block b: pupil rows [b R, b R + R), 512 threads in two groups
+//                         of 256, each over half of the rows.  A thread holds E of its
+//                         rows at 4 pixel columns in registers; the rows of Fxu stream
+//                         through a block-wide cp.async ring four grid columns at a time;
+//                         the per-thread G contributions are summed by a warp
+//                         reduce-scatter and then over the group's 8 warps in order.  The
+//                         block writes its partial Theta row (sum over its rows); for
+//                         K <= 512 the last block to finish sums the rows and runs the
+//                         focal step (no second launch).
+//   sep_sum_focal_kernel  32 foci per block: the partial rows summed in fixed order into
+//                         Theta; the block that finishes last runs the focal step
+//   sep_inv_kernel        tile of 32 pixel columns x 256 pupil rows, 512 threads: C
+//                         gathered from c, T for the tile's columns, the rank-U_y product
+//                         (16 rows per warp, a lane per column), phi = arg E' and the next
+//                         field A exp(i phi), formed as A E' / |E'|
+//
+// The three kernels are launched as programmatic dependents: each stages the operands
+// that do not change over the loop (Fxu, Fyu, the grid map, A) while the kernel before
+// it finishes, and waits for that kernel only before it reads what it produced.
+//
+// Every sum runs in a fixed order, so runs and resumes are bitwise reproducible.
+#include <type_traits>
+
+#include "ofa_focal.cuh"
+#include "ofa_internal.cuh"
+#include "ofa_math.cuh"
+#include "umma_ptx.cuh"
+
+namespace {
+
+using ofa_ptx::pdl_launch_dependents;
+using ofa_ptx::pdl_wait;
+
+constexpr int SEP_THREADS = 256;  // the sum kernel
+constexpr int SEP_WARPS = SEP_THREADS / 32;
+constexpr int SEP_MAX_R = 8;      // pupil rows per forward block
+constexpr int FWD_THREADS = 512;  // two groups of 256, each over half of the block's rows
+constexpr int FWD_GROUP = 256;
+constexpr int FWD_WARPS = FWD_THREADS / 32;
+constexpr int FWD_MT = 4;         // pixel columns per forward thread: nx <= 1024
+constexpr int FWD_STAGES = 3;     // quads of Fxu rows in the ring
+constexpr int INV_THREADS = 512;
+constexpr int INV_WARPS = INV_THREADS / 32;
+constexpr int INV_COLS = 32;      // pixel columns of an inverse tile (a lane each)
+constexpr int INV_ROWS = 256;     // pupil rows of an inverse tile (16 per warp)
+constexpr int INV_RPW = INV_ROWS / INV_WARPS;
+constexpr int INV_MAX_UY = 64;    // grid rows the inverse's T accumulators cover
+
+__device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) b
+__device__ __forceinline__ void cmac_conj(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
+// 8-byte asynchronous copy global -> shared; with valid == false the destination is
+// zero-filled and nothing is read (src must still be a valid address).
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// 16-byte copy through L2 only (both addresses 16-byte aligned; used also for data
+// other blocks of this launch wrote); with valid == false the destination is
+// zero-filled and nothing is read
+__device__ __forceinline__ void cp_async16_cg(void* dst, const void* src, bool valid = true) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Butterfly reduce-scatter of 32 values over the 32 lanes: afterwards lane l holds
+// the warp-wide sum of element l (31 shuffles for 32 sums, fixed order).
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      const float send = upper ? v[i] : v[i + off];
+      const float keep = upper ? v[i + off] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0];
+}
+
+// Shared memory of the forward: the Fxu ring [FWD_STAGES][4][FWD_MT][FWD_GROUP], the
+// per-warp sums [nquad][FWD_WARPS][32], G [R][ux] and the block's Fyu columns [uy][R].
+constexpr size_t FWD_SLOT = (size_t)4 * FWD_MT * FWD_GROUP;
+constexpr size_t FWD_RING = (size_t)FWD_STAGES * FWD_SLOT;
+
+// Block: pupil rows [n0, n0 + R), R <= 2 RT; thread (group g, t) holds E of rows
+// n0 + g RT + [0, RT) at the columns t + 256 j, j < 4.  With f.on, the block that
+// finishes last also sums the partial rows (staged in the idle ring) into Theta and
+// runs the focal step (K <= FWD_THREADS).
+template <int RT>
+__global__ void __launch_bounds__(FWD_THREADS, 1) sep_fwd_kernel(
+    const float2* __restrict__ e32, const float2* __restrict__ fxu,
+    const float2* __restrict__ fyu, const int2* __restrict__ ixy, int nx, int ny, int ux, int uy,
+    int K, int kp, int R, float2* __restrict__ part, const int* __restrict__ done, SepFocal f) {
+  pdl_launch_dependents();
+  extern __shared__ float4 sep_smem4[];
+  float2* ring = reinterpret_cast<float2*>(sep_smem4);
+  const int nquad = (ux + 3) >> 2;
+  float* red = reinterpret_cast<float*>(ring + FWD_RING);                         // [nquad][16][32]
+  float2* gs = reinterpret_cast<float2*>(red + (size_t)nquad * FWD_WARPS * 32);   // [R][ux]
+  float2* fs = gs + (size_t)R * ux;                                                // [uy][R]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = tid / FWD_GROUP, t = tid % FWD_GROUP;
+  const int n0 = blockIdx.x * R;
+  const int rows = min(R, ny - n0);
+  const int rows_g = max(0, min(RT, rows - g * RT));
+
+  // Fxu rows 4q .. 4q + 3 into ring slot q % FWD_STAGES, all columns: element
+  // (c, j, t) is Fxu[4q + c][t + 256 j]
+  auto issue = [&](int q) {
+    if (q < nquad) {
+      float2* dst = ring + (size_t)(q % FWD_STAGES) * FWD_SLOT;
+#pragma unroll
+      for (int i = 0; i < (int)(FWD_SLOT / FWD_THREADS); ++i) {
+        const int idx = tid + i * FWD_THREADS;
+        const int c = idx / (FWD_MT * FWD_GROUP);
+        const int m = idx % (FWD_MT * FWD_GROUP);   // = t' + 256 j'
+        const int ix = 4 * q + c;
+        const bool ok = ix < ux && m < nx;
+        cp_async8(dst + idx, ok ? fxu + (size_t)ix * nx + m : fxu, ok);
+      }
+    }
+    cp_async_commit();   // an empty group past the end keeps the group count uniform
+  };
+#pragma unroll
+  for (int q = 0; q < FWD_STAGES - 1; ++q) issue(q);
+  for (int i = tid; i < uy * R; i += FWD_THREADS) {
+    const int iy = i / R, r = i - iy * R;
+    fs[i] = r < rows ? __ldg(fyu + (size_t)iy * ny + n0 + r) : make_float2(0.f, 0.f);
+  }
+  // grid indices of this thread's first foci
+  constexpr int KR = 4;
+  int2 xyr[KR];
+#pragma unroll
+  for (int i = 0; i < KR; ++i) {
+    const int k = tid + i * FWD_THREADS;
+    xyr[i] = k < K ? __ldg(ixy + k) : make_int2(0, 0);
+  }
+
+  pdl_wait();   // E and the stop flag come from the kernels before this one
+  const int stop = done != nullptr ? __ldcg(done) : 0;
+  // this thread's E values, all loads in flight together
+  float2 e[RT][FWD_MT];
+#pragma unroll
+  for (int r = 0; r < RT; ++r)
+#pragma unroll
+    for (int j = 0; j < FWD_MT; ++j) {
+      const int m = t + j * FWD_GROUP;
+      e[r][j] = (r < rows_g && m < nx) ? __ldcg(e32 + (size_t)(n0 + g * RT + r) * nx + m)
+                                       : make_float2(0.f, 0.f);
+    }
+  if (stop) {
+    cp_async_wait<0>();   // no copy may land after the block has left
+    return;
+  }
+
+  for (int q = 0; q < nquad; ++q) {
+    cp_async_wait<FWD_STAGES - 2>();   // this thread's copies of quad q have landed
+    __syncthreads();                   // everyone's have; slot (q - 1) % S is free
+    issue(q + FWD_STAGES - 1);
+    const float2* src = ring + (size_t)(q % FWD_STAGES) * FWD_SLOT;
+    // v[8 c + 2 r + {0, 1}]: this thread's part of G[n0 + g RT + r][4q + c]
+    float v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int j = 0; j < FWD_MT; ++j) {
+        const float2 fv = src[(c * FWD_MT + j) * FWD_GROUP + t];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+          float2 a = make_float2(v[8 * c + 2 * r], v[8 * c + 2 * r + 1]);
+          cmac(a, e[r][j], fv);
+          v[8 * c + 2 * r] = a.x;
+          v[8 * c + 2 * r + 1] = a.y;
+        }
+      }
+    red[((size_t)q * FWD_WARPS + warp) * 32 + lane] = reduce_scatter32(v, lane);
+  }
+  __syncthreads();
+  // G[r][ix] = sum over the 8 warps of the row's group, in order
+  for (int i = tid; i < R * ux; i += FWD_THREADS) {
+    const int r = i / ux, ix = i - r * ux;
+    const int gr = r / RT, rr = r - gr * RT;
+    const int el = (ix & 3) * 8 + 2 * rr;
+    const float* s = red + ((size_t)(ix >> 2) * FWD_WARPS + gr * (FWD_GROUP / 32)) * 32;
+    float2 gv = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int w = 0; w < FWD_GROUP / 32; ++w) {
+      gv.x += s[w * 32 + el];
+      gv.y += s[w * 32 + el + 1];
+    }
+    gs[i] = gv;
+  }
+  __syncthreads();
+  // this block's partial Theta: sum over its rows of Fyu[iy_k][n] G[n][ix_k]
+  float2* dst = part + (size_t)blockIdx.x * kp;
+#pragma unroll
+  for (int i = 0; i < KR; ++i) {
+    const int k = tid + i * FWD_THREADS;
+    if (k >= kp) break;
+    float2 a = make_float2(0.f, 0.f);
+    if (k < K)
+      for (int r = 0; r < R; ++r) cmac(a, fs[xyr[i].y * R + r], gs[r * ux + xyr[i].x]);
+    dst[k] = a;
+  }
+  for (int k = tid + KR * FWD_THREADS; k < kp; k += FWD_THREADS) {
+    float2 a = make_float2(0.f, 0.f);
+    if (k < K) {
+      const int2 xy = __ldg(ixy + k);
+      for (int r = 0; r < R; ++r) cmac(a, fs[xy.y * R + r], gs[r * ux + xy.x]);
+    }
+    dst[k] = a;
+  }
+  if (!f.on) return;
+
+  // the last block: Theta = sum of the partial rows in order, then the focal step
+  __shared__ int last;
+  __shared__ float focal_sh[4 * 33 + 4];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    last = atomicAdd(f.counter, 1u) == gridDim.x - 1;
+    if (last) {
+      __threadfence();
+      *f.counter = 0u;
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  const int nb = gridDim.x, k2 = (K + 1) >> 1;   // 16-byte pairs of foci per row
+  float2* ps = ring;                               // [nb][2 k2]
+  for (int i = tid; i < nb * k2; i += FWD_THREADS) {
+    const int p = i / k2, j = i - p * k2;
+    cp_async16_cg(ps + 2 * i, part + (size_t)p * kp + 2 * j);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  if (tid < K) {
+    float2 a = ps[tid];
+    for (int p = 1; p < nb; ++p) {
+      const float2 v = ps[(size_t)p * 2 * k2 + tid];
+      a.x += v.x;
+      a.y += v.y;
+    }
+    part[tid] = a;   // Theta over partial row 0
+  }
+  __syncthreads();
+  ofa_focal::iterate_regs<FWD_THREADS, 1>(part, 1, K, kp, f.t, f.w, f.c, f.hist, f.st,
+                                          f.weighting, focal_sh, tid, ofa_focal::BarBlock());
+}
+
+// Theta_k = sum over the nb partial rows in order; with focal != 0 the last block to
+// finish runs the focal step of the loop on Theta.
+__global__ void __launch_bounds__(SEP_THREADS) sep_sum_focal_kernel(
+    const float2* __restrict__ part, int nb, int K, int kp, float2* __restrict__ theta,
+    int focal, const float* __restrict__ t, float* __restrict__ w, float2* __restrict__ c,
+    double* __restrict__ hist, OfaDevState* __restrict__ st, int weighting,
+    unsigned* __restrict__ counter, const int* __restrict__ done) {
+  pdl_launch_dependents();
+  __shared__ float2 red[SEP_WARPS][32];
+  __shared__ float focal_sh[4 * 33 + 4];
+  __shared__ int last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = blockIdx.x * 32 + lane;
+  pdl_wait();
+  if (done != nullptr && __ldcg(done)) return;
+  // warp w sums rows w, w + 8, ...; U rows of loads in flight at a time
+  constexpr int U = 24;
+  float2 a = make_float2(0.f, 0.f);
+  if (k < K)
+    for (int p0 = warp; p0 < nb; p0 += SEP_WARPS * U) {
+      float2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int p = p0 + u * SEP_WARPS;
+        v[u] = p < nb ? __ldcg(part + (size_t)p * kp + k) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (p0 + u * SEP_WARPS < nb) {
+          a.x += v[u].x;
+          a.y += v[u].y;
+        }
+    }
+  red[warp][lane] = a;
+  __syncthreads();
+  if (tid < 32 && k < K) {
+    float2 s = red[0][tid];
+#pragma unroll
+    for (int q = 1; q < SEP_WARPS; ++q) {
+      s.x += red[q][tid].x;
+      s.y += red[q][tid].y;
+    }
+    theta[k] = s;
+  }
+  if (!focal) return;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    if (last) {
+      __threadfence();
+      *counter = 0u;
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  if (K <= SEP_THREADS * 4)
+    ofa_focal::iterate_regs<SEP_THREADS, 4>(theta, 1, K, kp, t, w, c, hist, st, weighting,
+                                            focal_sh, tid, ofa_focal::BarBlock());
+  else if (K <= SEP_THREADS * 16)
+    ofa_focal::iterate_regs<SEP_THREADS, 16>(theta, 1, K, kp, t, w, c, hist, st, weighting,
+                                             focal_sh, tid, ofa_focal::BarBlock());
+  else
+    ofa_focal::iterate<SEP_THREADS>(theta, K, kp, t, w, c, hist, st, weighting, focal_sh, tid,
+                                    ofa_focal::BarBlock());
+}
+
+// Shared memory of the inverse: Fyu rows of the tile [uy][INV_ROWS] (first: 16-byte
+// aligned for its paired loads), C [uy][ux], Fxu columns of the tile [ux][INV_COLS],
+// T [uy][INV_COLS].
+__global__ void __launch_bounds__(INV_THREADS, 1) sep_inv_kernel(
+    const float2* __restrict__ c, const int* __restrict__ gridk, const float2* __restrict__ fxu,
+    const float2* __restrict__ fyu, const float* __restrict__ amp, int nx, int ny, int ux,
+    int uy, float* __restrict__ phi, float2* __restrict__ e32, const int* __restrict__ done) {
+  pdl_launch_dependents();
+  extern __shared__ float4 sep_smem4[];
+  float2* fys = reinterpret_cast<float2*>(sep_smem4);
+  float2* cs = fys + (size_t)uy * INV_ROWS;
+  float2* fxs = cs + (size_t)uy * ux;
+  float2* ts = fxs + (size_t)ux * INV_COLS;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.x * INV_COLS, n0 = blockIdx.y * INV_ROWS;
+  const int nw0 = n0 + warp * INV_RPW;   // this warp's first row
+  // the tile's constant operands, asynchronously
+  for (int i = tid; i < uy * INV_ROWS; i += INV_THREADS) {
+    const int iy = i / INV_ROWS, n = n0 + (i - iy * INV_ROWS);
+    cp_async8(fys + i, n < ny ? fyu + (size_t)iy * ny + n : fyu, n < ny);
+  }
+  for (int i = tid; i < ux * INV_COLS; i += INV_THREADS) {
+    const int ix = i / INV_COLS, m = m0 + (i - ix * INV_COLS);
+    cp_async8(fxs + i, m < nx ? fxu + (size_t)ix * nx + m : fxu, m < nx);
+  }
+  cp_async_commit();
+  // the grid map (the focus index in the low word until c is known) and the
+  // amplitudes of this thread's pixels
+  for (int i = tid; i < uy * ux; i += INV_THREADS)
+    cs[i] = make_float2(__int_as_float(__ldg(gridk + i)), 0.f);
+  const int m = m0 + lane;
+  float av[INV_RPW];
+#pragma unroll
+  for (int i = 0; i < INV_RPW; ++i)
+    av[i] = (nw0 + i < ny && m < nx) ? __ldg(amp + (size_t)(nw0 + i) * nx + m) : 0.f;
+
+  pdl_wait();   // c and the stop flag come from the kernel before this one
+  const int stop = done != nullptr ? __ldcg(done) : 0;
+  // C on the grid: each thread fills the entries it mapped above
+  for (int i = tid; i < uy * ux; i += INV_THREADS) {
+    const int k = __float_as_int(cs[i].x);
+    cs[i] = k >= 0 ? __ldcg(c + k) : make_float2(0.f, 0.f);
+  }
+  cp_async_wait<0>();
+  if (stop) return;
+  __syncthreads();
+  // T[iy][m0 + lane] for iy = warp, warp + 16, ...: sum over ix in order of
+  // C[iy][ix] conj(Fxu[ix][m])
+  {
+    constexpr int TI = INV_MAX_UY / INV_WARPS;
+    float2 ta[TI];
+#pragma unroll
+    for (int i = 0; i < TI; ++i) ta[i] = make_float2(0.f, 0.f);
+    for (int ix = 0; ix < ux; ++ix) {
+      const float2 f = fxs[ix * INV_COLS + lane];
+#pragma unroll
+      for (int i = 0; i < TI; ++i) {
+        const int iy = warp + i * INV_WARPS;
+        if (iy < uy) cmac_conj(ta[i], f, cs[iy * ux + ix]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < TI; ++i) {
+      const int iy = warp + i * INV_WARPS;
+      if (iy < uy) ts[iy * INV_COLS + lane] = ta[i];
+    }
+  }
+  __syncthreads();
+  // E'[nw0 + i][m0 + lane] = sum over iy in order of conj(Fyu[iy][n]) T[iy][m]
+  float2 acc[INV_RPW];
+#pragma unroll
+  for (int i = 0; i < INV_RPW; ++i) acc[i] = make_float2(0.f, 0.f);
+  for (int iy = 0; iy < uy; ++iy) {
+    const float2 tv = ts[iy * INV_COLS + lane];
+    const float4* f4 =
+        reinterpret_cast<const float4*>(fys + (size_t)iy * INV_ROWS + warp * INV_RPW);
+#pragma unroll
+    for (int i = 0; i < INV_RPW / 2; ++i) {
+      const float4 q = f4[i];
+      cmac_conj(acc[2 * i], make_float2(q.x, q.y), tv);
+      cmac_conj(acc[2 * i + 1], make_float2(q.z, q.w), tv);
+    }
+  }
+  if (m >= nx) return;
+  // projection: phi = arg E' and the next field A exp(i phi) = A E' / |E'| (A at
+  // E' = 0); the pixels are independent, so their chains interleave
+#pragma unroll
+  for (int i = 0; i < INV_RPW; ++i) {
+    const float ph = ofa_arg(acc[i].y, acc[i].x);   // arg(0) = 0
+    const float r2 = acc[i].x * acc[i].x + acc[i].y * acc[i].y;
+    const float s = r2 > 0.f ? av[i] * rsqrtf(r2) : 0.f;
+    const float2 ev = r2 > 0.f ? make_float2(s * acc[i].x, s * acc[i].y) : make_float2(av[i], 0.f);
+    if (nw0 + i < ny) {
+      const size_t o = (size_t)(nw0 + i) * nx + m;
+      phi[o] = ph;
+      e32[o] = ev;
+    }
+  }
+}
+
+size_t fwd_smem(int R, int ux, int uy) {
+  return sizeof(float2) * FWD_RING + sizeof(float) * (size_t)((ux + 3) / 4) * FWD_WARPS * 32 +
+         sizeof(float2) * ((size_t)R * ux + (size_t)uy * R);
+}
+
+// rows of a forward thread group: RT = ceil(R / 2)
+template <class F>
+void visit_rt(int R, F&& f) {
+  switch ((R + 1) / 2) {
+    case 1: f(std::integral_constant<int, 1>()); break;
+    case 2: f(std::integral_constant<int, 2>()); break;
+    case 3: f(std::integral_constant<int, 3>()); break;
+    default: f(std::integral_constant<int, 4>()); break;
+  }
+}
+
+// Launch as a programmatic dependent of the previous kernel in the stream.
+template <class... P, class... A>
+void launch_pdl(void (*kernel)(P...), dim3 grid, int threads, size_t smem, cudaStream_t s,
+                A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
+}  // namespace
+
+int sep_rows_per_block(int ny, int sms) {
+  const int r = (ny + sms - 1) / sms;
+  return r < 1 ? 1 : (r > SEP_MAX_R ? SEP_MAX_R : r);
+}
+
+int sep_fwd_blocks(int ny, int sms) {
+  const int r = sep_rows_per_block(ny, sms);
+  return (ny + r - 1) / r;
+}
+
+size_t sep_fwd_smem(int ny, int ux, int uy, int sms) {
+  return fwd_smem(sep_rows_per_block(ny, sms), ux, uy);
+}
+
+size_t sep_inv_smem(int ux, int uy) {
+  return sizeof(float2) * ((size_t)uy * INV_ROWS + (size_t)uy * ux + (size_t)ux * INV_COLS +
+                           (size_t)uy * INV_COLS);
+}
+
+bool sep_fast_shape(int nx, int uy) { return nx <= FWD_MT * FWD_GROUP && uy <= INV_MAX_UY; }
+
+cudaError_t sep_prepare(int ny, int ux, int uy, int sms) {
+  cudaError_t e = cudaSuccess;
+  visit_rt(sep_rows_per_block(ny, sms), [&](auto rc) {
+    e = cudaFuncSetAttribute(sep_fwd_kernel<decltype(rc)::value>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sep_fwd_smem(ny, ux, uy, sms));
+  });
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sep_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sep_inv_smem(ux, uy));
+}
+
+bool sep_fwd_fuses_focal(int ny, int K, int sms) {
+  const size_t staged = (size_t)sep_fwd_blocks(ny, sms) * (size_t)((K + 1) / 2) * 2;
+  return K <= FWD_THREADS && staged <= FWD_RING;
+}
+
+void launch_sep_fwd(const float2* e32, const float2* fxu, const float2* fyu, const int2* ixy,
+                    int nx, int ny, int ux, int uy, int K, int kp, int sms, float2* part,
+                    const SepFocal& f, const int* done, cudaStream_t s) {
+  const int R = sep_rows_per_block(ny, sms);
+  const size_t smem = fwd_smem(R, ux, uy);
+  const int blocks = sep_fwd_blocks(ny, sms);
+  SepFocal fk = f;
+  fk.on = f.on && sep_fwd_fuses_focal(ny, K, sms);
+  visit_rt(R, [&](auto rc) {
+    launch_pdl(sep_fwd_kernel<decltype(rc)::value>, dim3(blocks), FWD_THREADS, smem, s, e32, fxu,
+               fyu, ixy, nx, ny, ux, uy, K, kp, R, part, done, fk);
+  });
+}
+
+void launch_sep_sum_focal(const float2* part, int nb, int K, int kp, float2* theta, int focal,
+                          const float* t, float* w, float2* c, double* hist, OfaDevState* st,
+                          int weighting, unsigned* counter, const int* done, cudaStream_t s) {
+  launch_pdl(sep_sum_focal_kernel, dim3((K + 31) / 32), SEP_THREADS, 0, s, part, nb, K, kp, theta,
+             focal, t, w, c, hist, st, weighting, counter, done);
+}
+
+void launch_sep_inverse(const float2* c, const int* gridk, const float2* fxu, const float2* fyu,
+                        const float* amp, int nx, int ny, int ux, int uy, float* phi,
+                        float2* e32, const int* done, cudaStream_t s) {
+  dim3 grid((nx + INV_COLS - 1) / INV_COLS, (ny + INV_ROWS - 1) / INV_ROWS);
+  launch_pdl(sep_inv_kernel, grid, INV_THREADS, sep_inv_smem(ux, uy), s, c, gridk, fxu, fyu, amp,
+             nx, ny, ux, uy, phi, e32, done);
+}

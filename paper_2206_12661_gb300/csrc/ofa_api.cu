@@ -283,25 +283,48 @@ void sep_transpose_t(ofa_plan* p, cudaStream_t s) {
   launch_transpose_fy(p->tconj, p->uy, p->nx, simt_ldk(p->uy), p->nx, p->simt.fxT, s, true);
 }
 
-// Separable form, second inverse product fused with the phase projection.
+// Separable form, the inverse from c: T by grid rows, then the second inverse product
+// fused with the phase projection (one launch forming T per tile when it fits).
 void enqueue_sep_inverse(ofa_plan* p, const int* done, cudaStream_t s) {
+  if (p->sep_fast) {
+    launch_sep_inverse(p->c, p->sep_gridk, p->fxu, p->fyu, p->amp, p->nx, p->ny, p->ux, p->uy,
+                       p->phi, p->e32, done, s);
+    return;
+  }
+  launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj, s);
   sep_transpose_t(p, s);
   launch_bwd_simt(p->ones, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->uy, p->amp, p->phi, p->e32,
                   done, p->simt, s);
 }
 
+// Separable form, forward at the foci for the field e32: Theta in partial row 0.
 void enqueue_sep_forward(ofa_plan* p, const float2* e32, cudaStream_t s) {
+  if (p->sep_fast) {
+    const SepFocal off = {};
+    launch_sep_fwd(e32, p->fxu, p->fyu, p->ixy, p->nx, p->ny, p->ux, p->uy, p->K, p->kp,
+                   p->sm_count, p->part, off, nullptr, s);
+    launch_sep_sum_focal(p->part, sep_fwd_blocks(p->ny, p->sm_count), p->K, p->kp, p->part, 0,
+                         p->t, p->w, p->c, p->hist, p->st, p->weighting, p->counters, nullptr, s);
+    return;
+  }
   launch_sep_forward(e32, p->fxu, p->nx, p->ny, p->ux, p->sep_parts, p->gt, s);
   launch_sep_theta(p->gt, p->fyu, p->ixy, p->K, p->ny, p->ux, p->sep_parts, p->part, s);
 }
 
 void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
   const int* done = done_ptr(p);
-  if (p->sep) {
+  if (p->sep && p->sep_fast) {
+    const SepFocal f = {p->t, p->w, p->c, p->hist, p->st, p->weighting, p->counters, 1};
+    launch_sep_fwd(p->e32, p->fxu, p->fyu, p->ixy, p->nx, p->ny, p->ux, p->uy, p->K, p->kp,
+                   p->sm_count, p->part, f, done, s);
+    if (!sep_fwd_fuses_focal(p->ny, p->K, p->sm_count))
+      launch_sep_sum_focal(p->part, sep_fwd_blocks(p->ny, p->sm_count), p->K, p->kp, p->part, 1,
+                           p->t, p->w, p->c, p->hist, p->st, p->weighting, p->counters, done, s);
+    enqueue_sep_inverse(p, done, s);
+  } else if (p->sep) {
     enqueue_sep_forward(p, p->e32, s);
     launch_focal(p->part, 1, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist, p->st,
                  0, p->weighting, 1.f, p->amp_energy, s);
-    launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj, s);
     enqueue_sep_inverse(p, done, s);
   } else if (!use_tc(p)) {
     launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, done, p->simt, s);
@@ -539,7 +562,7 @@ ofa_status ofa_destroy(ofa_plan* p) {
                   p->fy,       p->fyT,   p->part,  p->theta, p->inten, p->c,
                   p->hist,     p->st,    p->scratch_phi, p->counters, p->e32, p->e32_aux,
                   p->meas,     p->fxu,   p->fyu,   p->gt,    p->tconj, p->ones, p->ixy,
-                  p->row_ptr,  p->row_foci};
+                  p->row_ptr,  p->row_foci, p->sep_gridk};
   for (void* b : bufs) dfree(b);
   if (p->st_host) give_back_st_host(p->device, p->st_host);
   free_tc(p->tc);
@@ -662,6 +685,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   p->py = pitch_y;
   p->lambda = wavelength;
   p->focal = focal_length;
+  p->sm_count = sm_count;
   p->nxp = round_up(nx, 128);
   p->nyp = round_up(ny, 128);
   p->kp = round_up(n_foci, 128);
@@ -722,7 +746,8 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
           "creating capture stream");
 
   const bool tc = use_tc(p);
-  const int n_part_max = tc ? (p->nyp / 128) * 8 : simt_fwd_tiles(ny);
+  const int n_part_max = tc ? (p->nyp / 128) * 8
+                            : std::max(simt_fwd_tiles(ny), p->sep ? sep_fwd_blocks(ny, sm_count) : 1);
   // Reserve every device buffer, then carve them out of one allocation.
   std::vector<ArenaReq> reqs;
   g_arena = &reqs;
@@ -755,6 +780,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
       R(dalloc(&p->ixy, (size_t)n_foci));
       R(dalloc(&p->row_ptr, (size_t)p->uy + 1));
       R(dalloc(&p->row_foci, (size_t)n_foci));
+      R(dalloc(&p->sep_gridk, (size_t)p->ux * p->uy));
       R(dalloc(&p->sep_coord, 2 * ((size_t)p->ux + p->uy)));
     }
     R(dalloc(&p->st, 1));
@@ -793,6 +819,15 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
       order[k] = k;
     }
     for (int r = 0; r < p->uy; ++r) count[r + 1] += count[r];
+    // the focus at each grid point (a grid point holding two foci keeps the
+    // general-order T of launch_sep_t)
+    std::vector<int> gridk((size_t)p->ux * p->uy, -1);
+    bool grid_unique = true;
+    for (int k = 0; k < n_foci; ++k) {
+      int& g = gridk[(size_t)ixy[k].y * p->ux + ixy[k].x];
+      if (g >= 0) grid_unique = false;
+      g = k;
+    }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
       return ixy[a].y != ixy[b].y ? ixy[a].y < ixy[b].y : ixy[a].x < ixy[b].x;
     });
@@ -813,6 +848,9 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
                       cudaMemcpyHostToDevice);
     if (ce == cudaSuccess)
       ce = cudaMemcpy(p->ones, ones.data(), ones.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(p->sep_gridk, gridk.data(), gridk.size() * sizeof(int),
+                      cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) {
       const double lf = wavelength * focal_length;
       launch_dft_rows(dcoord, nullptr, 0, p->ux, nx, pitch_x, 0.5 * (nx - 1), lf, lf * focal_length,
@@ -824,6 +862,13 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
       ce = cudaStreamSynchronize(p->stream);
     }
     OFA_TRY(ce, "separable grid set-up");
+    // the three-launch separable iteration when its shared-memory staging fits
+    const size_t limit = 200 * 1024;
+    p->sep_fast = grid_unique && sep_fast_shape(nx, p->uy) &&
+                  sep_fwd_smem(ny, p->ux, p->uy, sm_count) <= limit &&
+                  sep_inv_smem(p->ux, p->uy) <= limit &&
+                  sep_prepare(ny, p->ux, p->uy, sm_count) == cudaSuccess;
+    cudaGetLastError();
   }
 
   // Small inputs.
@@ -1059,7 +1104,6 @@ ofa_status ofa_iterate_measured(ofa_plan* p, const float* measured, int mem_spac
   launch_focal_measured(p->part, n_part, p->kp, p->K, p->t, p->w, p->theta, p->c, p->hist, p->st,
                         p->weighting, p->meas, s);
   if (p->sep) {
-    launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj, s);
     enqueue_sep_inverse(p, nullptr, s);
   } else if (use_tc(p)) {
     launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
@@ -1224,7 +1268,6 @@ ofa_status ofa_shard_update(ofa_plan* p, const float* theta_total) {
   launch_focal(reinterpret_cast<const float2*>(theta_total), 1, p->kp, p->K, p->t, p->w,
                p->theta, p->inten, p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
   if (p->sep) {
-    launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj, s);
     enqueue_sep_inverse(p, nullptr, s);
   } else if (use_tc(p)) {
     launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
@@ -1351,9 +1394,12 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
                      p->st, 0, p->weighting, 1.f, p->amp_energy, s);
         break;
       case 2:
-        if (p->sep) launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx,
-                                 p->tconj, s);
-        else if (tc) launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision,
+        if (p->sep) {
+          // the three-launch separable form builds T inside the inverse (reported there)
+          if (!p->sep_fast)
+            launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj,
+                         s);
+        } else if (tc) launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision,
                                     p->tc.p_hi, p->tc.p_lo, s);
         else launch_scale_conj(p->c, p->simt.fyT, p->ny, p->K, p->simt.p32, nullptr, s);
         break;

@@ -124,8 +124,11 @@ struct ofa_plan {
   float2* tconj = nullptr;             // [uy][nx] first inverse product, conjugated
   float2* ones = nullptr;              // [uy] unit weights of the second inverse product
   int2* ixy = nullptr;                 // [K] (ix, iy) of each focus
+  bool sep_fast = false;               // the three-launch separable iteration (k_sep.cu)
+  int sm_count = 0;
   int* row_ptr = nullptr;              // [uy + 1] foci of each grid row ...
   int* row_foci = nullptr;             // [K] ... in increasing ix order
+  int* sep_gridk = nullptr;            // [uy][ux] focus at each grid point, or -1
   TcOperands tc;
   TcOperands tc_aux;                   // E planes of an external phase (forward/adjoint)
   LoopOperands loop;                   // fused loop kernel (tensor-core forms, K <= 4096)
@@ -209,6 +212,39 @@ void launch_sep_theta(float2* gt, const float2* fyu, const int2* ixy, int K, int
                       int parts, float2* part, cudaStream_t s);
 void launch_sep_t(const float2* c, const float2* fxu, const int2* ixy, const int* row_ptr,
                   const int* row_foci, int uy, int nx, float2* tconj, cudaStream_t s);
+// ---------------------------------------------------------------- kernels (k_sep.cu)
+// The separable iteration in three launches: partial Theta rows of blocks of pupil rows,
+// their fixed-order sum (Theta written over partial row 0) with the focal step in the
+// last block (focal != 0), and the inverse with C gathered from c through gridk
+// ([uy][ux] focus index or -1) and T formed per tile.
+int sep_fwd_blocks(int ny, int sms);
+size_t sep_fwd_smem(int ny, int ux, int uy, int sms);
+size_t sep_inv_smem(int ux, int uy);
+bool sep_fast_shape(int nx, int uy);
+cudaError_t sep_prepare(int ny, int ux, int uy, int sms);
+// The focal step's operands for a kernel that runs it in its last block (on != 0).
+struct SepFocal {
+  const float* t;
+  float* w;
+  float2* c;
+  double* hist;
+  OfaDevState* st;
+  int weighting;
+  unsigned* counter;
+  int on;
+};
+// With f.on the forward runs the focal step itself when sep_fwd_fuses_focal (small
+// K); otherwise launch_sep_sum_focal follows it.
+bool sep_fwd_fuses_focal(int ny, int K, int sms);
+void launch_sep_fwd(const float2* e32, const float2* fxu, const float2* fyu, const int2* ixy,
+                    int nx, int ny, int ux, int uy, int K, int kp, int sms, float2* part,
+                    const SepFocal& f, const int* done, cudaStream_t s);
+void launch_sep_sum_focal(const float2* part, int nb, int K, int kp, float2* theta, int focal,
+                          const float* t, float* w, float2* c, double* hist, OfaDevState* st,
+                          int weighting, unsigned* counter, const int* done, cudaStream_t s);
+void launch_sep_inverse(const float2* c, const int* gridk, const float2* fxu, const float2* fyu,
+                        const float* amp, int nx, int ny, int ux, int uy, float* phi,
+                        float2* e32, const int* done, cudaStream_t s);
 void launch_grad_simt(const float2* c, const float2* fxT, const float2* fyT, int nx, int ny, int K,
                       const float* phi, const float* amp, float amp_factor,
                       const OfaDevState* st, float* grad, const SimtWork& w, cudaStream_t s);

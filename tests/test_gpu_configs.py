@@ -58,7 +58,9 @@ def ragged(nx=333, ny=250, K=300, seed=21):
 
 WORKLOADS = {"ragged333x250_300": ragged, "pupil1024_poisson1000":
              lambda: I.named("pupil1024_poisson1000"),
-             "pupil1920x1152_grid2500": lambda: I.named("pupil1920x1152_grid2500")}
+             "pupil1920x1152_grid2500": lambda: I.named("pupil1920x1152_grid2500"),
+             "table1_grid9x9": lambda: I.named("table1_grid9x9"),
+             "table1_grid45x47": lambda: I.named("table1_grid45x47")}
 
 
 @functools.lru_cache(maxsize=None)
@@ -77,8 +79,8 @@ def reference(name, j=2):
     return w, j, phi_j, w_j, theta, w_new, back
 
 
-def check_plan(ofa, name, prec, **kw):
-    w, j, phi_j, w_j, theta, w_new, back = reference(name)
+def check_plan(ofa, name, prec, j=2, **kw):
+    w, j, phi_j, w_j, theta, w_new, back = reference(name, j)
     plan = ofa.Plan.from_workload(w, precision=prec,
                                   stream=torch.cuda.current_stream().cuda_stream, **kw)
     cfg = ofa.ofa_plan_config(plan.handle)
@@ -157,6 +159,15 @@ def test_fused_loop_configs_pupil1024_poisson1000(ofa, dev, loop):
 def test_one_step_full_size(ofa, dev, prec, name):
     """One step from the same iterate at full size, in the default configuration."""
     cfg = check_plan(ofa, name, prec)
+    assert cfg["fused_loop"] == 0
+
+
+@pytest.mark.parametrize("j", [2, 5])
+@pytest.mark.parametrize("name", ["table1_grid9x9", "table1_grid45x47"])
+def test_separable_one_step(ofa, dev, name, j):
+    """The separable grid form (FP32): forward amplitudes and one iteration from the
+    oracle's iterate j, at the start and in the steep climb of xi (iteration 5)."""
+    cfg = check_plan(ofa, name, "fp32", j=j, separable=1)
     assert cfg["fused_loop"] == 0
 
 

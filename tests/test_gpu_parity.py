@@ -593,10 +593,13 @@ def test_separable_form_table1_9x9_matches_oracle(ofa, dev):
     plan.close()
     assert form == {"separable": True, "ux": 9, "uy": 9}
     # FP32 rounding is amplified while xi climbs steeply (iterations 3-6 here): the
-    # first iterations agree to 1e-5, the whole history to 2e-3, the end to 1e-3
+    # first iterations agree to 1e-5, the whole history to 2e-3, the final xi to 1e-3
+    # and the final uniformity (a max/min statistic of the 81 intensities, more
+    # sensitive to the path than xi) to the history's 2e-3.  Each single step is
+    # pinned far tighter by test_separable_one_step.
     assert np.max(np.abs(hist[:3] - ref["xi_hist"][:3])) < 1e-5
     assert np.max(np.abs(hist - ref["xi_hist"])) < 2e-3
-    assert abs(xi - ref["xi"]) < 1e-3 and abs(st.uniformity - ref["uniformity"]) < 1e-3
+    assert abs(xi - ref["xi"]) < 1e-3 and abs(st.uniformity - ref["uniformity"]) < 2e-3
     assert hist.max() >= 0.99 and int(np.argmax(hist >= 0.99)) < 40
 
 
