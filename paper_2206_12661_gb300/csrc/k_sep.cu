@@ -53,6 +53,7 @@ constexpr int INV_COLS = 32;      // pixel columns of an inverse tile (a lane ea
 constexpr int INV_ROWS = 256;     // pupil rows of an inverse tile (16 per warp)
 constexpr int INV_RPW = INV_ROWS / INV_WARPS;
 constexpr int INV_MAX_UY = 64;    // grid rows the inverse's T accumulators cover
+constexpr size_t SEP_SMEM_LIMIT = 200 * 1024;   // dynamic shared memory of either kernel
 
 __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, acc.x);
@@ -507,16 +508,21 @@ size_t sep_inv_smem(int ux, int uy) {
 
 bool sep_fast_shape(int nx, int uy) { return nx <= FWD_MT * FWD_GROUP && uy <= INV_MAX_UY; }
 
-cudaError_t sep_prepare(int ny, int ux, int uy, int sms) {
+size_t sep_smem_limit() { return SEP_SMEM_LIMIT; }
+
+// The attribute is per function, shared by every plan of the process: it is set to
+// the fixed ceiling the fast path admits, never to one plan's own size (a later plan
+// with a smaller grid would otherwise lower it under an earlier plan's launches).
+cudaError_t sep_prepare() {
   cudaError_t e = cudaSuccess;
-  visit_rt(sep_rows_per_block(ny, sms), [&](auto rc) {
-    e = cudaFuncSetAttribute(sep_fwd_kernel<decltype(rc)::value>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sep_fwd_smem(ny, ux, uy, sms));
-  });
+  for (int r = 1; r <= SEP_MAX_R && e == cudaSuccess; ++r)
+    visit_rt(r, [&](auto rc) {
+      e = cudaFuncSetAttribute(sep_fwd_kernel<decltype(rc)::value>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEP_SMEM_LIMIT);
+    });
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(sep_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sep_inv_smem(ux, uy));
+                              (int)SEP_SMEM_LIMIT);
 }
 
 bool sep_fwd_fuses_focal(int ny, int K, int sms) {

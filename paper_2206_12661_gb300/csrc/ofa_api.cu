@@ -863,11 +863,10 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     }
     OFA_TRY(ce, "separable grid set-up");
     // the three-launch separable iteration when its shared-memory staging fits
-    const size_t limit = 200 * 1024;
+    const size_t limit = sep_smem_limit();
     p->sep_fast = grid_unique && sep_fast_shape(nx, p->uy) &&
                   sep_fwd_smem(ny, p->ux, p->uy, sm_count) <= limit &&
-                  sep_inv_smem(p->ux, p->uy) <= limit &&
-                  sep_prepare(ny, p->ux, p->uy, sm_count) == cudaSuccess;
+                  sep_inv_smem(p->ux, p->uy) <= limit && sep_prepare() == cudaSuccess;
     cudaGetLastError();
   }
 

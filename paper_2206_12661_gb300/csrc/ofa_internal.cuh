@@ -221,7 +221,8 @@ int sep_fwd_blocks(int ny, int sms);
 size_t sep_fwd_smem(int ny, int ux, int uy, int sms);
 size_t sep_inv_smem(int ux, int uy);
 bool sep_fast_shape(int nx, int uy);
-cudaError_t sep_prepare(int ny, int ux, int uy, int sms);
+size_t sep_smem_limit();
+cudaError_t sep_prepare();
 // The focal step's operands for a kernel that runs it in its last block (on != 0).
 struct SepFocal {
   const float* t;

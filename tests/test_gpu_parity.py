@@ -648,6 +648,25 @@ def test_separable_45x47_forward_and_gradient(ofa, dev):
     assert rel < 1e-4, rel
 
 
+def test_separable_plans_of_different_grids_coexist(ofa, dev):
+    """A plan with a small grid created after one with a large grid leaves the large
+    one's launches intact (kernel attributes are shared by every plan of a process):
+    the large plan's steps are bitwise those of a run with no other plan."""
+    big, small = I.named("table1_grid45x47"), I.named("table1_grid9x9")
+    p1 = ofa.Plan.from_workload(big, precision="fp32", separable=1)
+    p1.iterate(3)
+    h_alone = p1.xi_history()
+    p1.close()
+    p1 = ofa.Plan.from_workload(big, precision="fp32", separable=1)
+    p2 = ofa.Plan.from_workload(small, precision="fp32", separable=1)
+    p2.iterate(2)
+    p1.iterate(3)
+    h_both = p1.xi_history()
+    p1.close()
+    p2.close()
+    assert np.array_equal(h_alone, h_both), (h_alone, h_both)
+
+
 def test_separable_refused_for_3d(ofa, dev):
     w = I.named("table1_grid9x9")
     with pytest.raises(ofa.OfaError) as e:
