@@ -366,34 +366,155 @@ __global__ void __launch_bounds__(FT) loss_grad_c_kernel(const float2* __restric
   }
 }
 
-// One Adam update of n parameters (the published algorithm with torch's defaults for
-// the order of operations): t = *step + 1, m <- b1 m + (1 - b1) g,
-// v <- b2 v + (1 - b2) g^2, x <- x - lr / (1 - b1^t) m / (sqrt(v) / sqrt(1 - b2^t) + eps).
-__global__ void adam_kernel(float* __restrict__ x, const float* __restrict__ g,
-                            float* __restrict__ m, float* __restrict__ v,
-                            const int* __restrict__ step, size_t n, float lr, float b1, float b2,
-                            float eps) {
-  // the bias corrections once per block (FP64 is slow on this GPU: not per element)
-  __shared__ float sc[2];
-  if (threadIdx.x == 0) {
-    const int t = *step + 1;
-    sc[0] = (float)((double)lr / (1.0 - pow((double)b1, (double)t)));
-    sc[1] = (float)sqrt(1.0 - pow((double)b2, (double)t));
+// The loss adjoint for K <= 256 KPR foci, each thread's foci held in registers, 256
+// threads.  The same quantities as loss_grad_c_kernel; the FP64 work is what carries
+// the cancellation: d_k = Ihat_k - t_k is formed in FP64 from the FP32 Theta (then
+// rounded), and the cross-warp partial sums are added in FP64.  Per-element products
+// and the in-warp sums are FP32.
+constexpr int LT = 256;
+template <int KPR>
+__global__ void __launch_bounds__(LT) loss_grad_c_regs_kernel(
+    const float2* __restrict__ theta, const float* __restrict__ t, int K, int kp,
+    float2* __restrict__ c, OfaDevState* __restrict__ st, float* __restrict__ loss_hist,
+    int loss_cap, const int* __restrict__ step) {
+  __shared__ double shd[3 * (LT / 32) + 4];
+  __shared__ float shm[LT / 32 + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // sum over the block: in-warp FP32 butterfly, then thread 0 adds the warp partials
+  // in FP64 in warp order and every thread reads the result
+  auto block_sum_fd = [&](float (&v)[2], int n, double (&out)[2]) {
+    for (int i = 0; i < n; ++i)
+#pragma unroll
+      for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    __syncthreads();
+    if (lane == 0)
+      for (int i = 0; i < n; ++i) shd[i * (LT / 32) + warp] = (double)v[i];
+    __syncthreads();
+    if (tid == 0)
+      for (int i = 0; i < n; ++i) {
+        double r = 0.0;
+#pragma unroll
+        for (int w = 0; w < LT / 32; ++w) r += shd[i * (LT / 32) + w];
+        shd[3 * (LT / 32) + i] = r;
+        if (i == 0 && n == 1) shd[3 * (LT / 32) + 1] = r > 0.0 ? 1.0 / r : 0.0;
+      }
+    __syncthreads();
+    for (int i = 0; i < 2; ++i) out[i] = shd[3 * (LT / 32) + i];
+  };
+  float2 a[KPR];
+  float tk[KPR];
+#pragma unroll
+  for (int i = 0; i < KPR; ++i) {
+    const int k = tid + i * LT;
+    a[i] = k < K ? theta[k] : make_float2(0.f, 0.f);
+    tk[i] = k < K ? t[k] : 0.f;
   }
+  float v[2] = {0.f, 0.f};
+  double r[2];
+#pragma unroll
+  for (int i = 0; i < KPR; ++i) v[0] += fmaf(a[i].x, a[i].x, a[i].y * a[i].y);
+  block_sum_fd(v, 1, r);   // r = {S, 1 / S}
+  const double inv_s = r[1];
+  const float inv_sf = (float)inv_s;
+  float df[KPR];
+  v[0] = v[1] = 0.f;
+#pragma unroll
+  for (int i = 0; i < KPR; ++i) {
+    const double ih = ((double)a[i].x * a[i].x + (double)a[i].y * a[i].y) * inv_s;
+    df[i] = tid + i * LT < K ? (float)(ih - (double)tk[i]) : 0.f;
+    v[0] += df[i] * df[i];
+    v[1] += df[i] * (float)ih;
+  }
+  block_sum_fd(v, 2, r);
+  const double L = r[0];
+  const float Df = (float)r[1];
+  float g[KPR], mx = 0.f;
+#pragma unroll
+  for (int i = 0; i < KPR; ++i) {
+    g[i] = 2.f * inv_sf * (df[i] - Df);
+    mx = fmaxf(mx, fabsf(g[i]) * sqrtf(fmaf(a[i].x, a[i].x, a[i].y * a[i].y)));
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) shm[warp] = mx;
   __syncthreads();
-  const float step_size = sc[0], bc2_sqrt = sc[1];
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    x[i] -= step_size * (mi / (sqrtf(vi) / bc2_sqrt + eps));
+  mx = shm[0];
+#pragma unroll
+  for (int w = 1; w < LT / 32; ++w) mx = fmaxf(mx, shm[w]);
+  int e = 0;
+  frexpf(mx, &e);
+  const float scale = mx > 0.f ? ldexpf(1.f, -e) : 1.f;
+#pragma unroll
+  for (int i = 0; i < KPR; ++i) {
+    const int k = tid + i * LT;
+    if (k >= kp) break;
+    const float gs = g[i] * scale;
+    c[k] = k < K ? make_float2(gs * a[i].x, gs * a[i].y) : make_float2(0.f, 0.f);
+  }
+  if (tid == 0) {
+    st->c_scale = scale;
+    const int i = step ? *step : 0;
+    if (loss_hist && i >= 0 && i < loss_cap) loss_hist[i] = (float)L;
   }
 }
 
-__global__ void step_increment_kernel(int* step) { *step += 1; }
+// One Adam update of n parameters (the published algorithm with torch's defaults for
+// the order of operations): t = *step + 1, m <- b1 m + (1 - b1) g,
+// v <- b2 v + (1 - b2) g^2, x <- x - lr / (1 - b1^t) m / (sqrt(v) / sqrt(1 - b2^t) + eps).
+// adam_prepare_kernel advances the step and forms the two bias corrections once (one
+// thread); adam_kernel applies the update, four parameters per thread when the
+// four arrays are 16-byte aligned.
+// 1 - b^t = -expm1(t log(b)), log(b) = log1p(-(1 - b)): accurate to a few FP32 ulps
+// relative also where b^t is close to 1 (b2 = 0.999 early on), where 1 - powf(b, t)
+// would cancel.  1 - b is exact in FP32 for b in [1/2, 1].
+__device__ __forceinline__ float one_minus_pow(float b, float t) {
+  return -expm1f(t * log1pf(-(1.f - b)));
+}
+
+__global__ void adam_prepare_kernel(int* __restrict__ step, OfaDevState* __restrict__ st,
+                                    float lr, float b1, float b2) {
+  const int t = *step + 1;
+  *step = t;
+  st->adam_step_size = lr / one_minus_pow(b1, (float)t);
+  st->adam_bc2_sqrt = sqrtf(one_minus_pow(b2, (float)t));
+}
+
+__device__ __forceinline__ void adam_one(float& x, float g, float& m, float& v, float b1,
+                                         float b2, float eps, float step_size,
+                                         float bc2_sqrt) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  x -= step_size * (m / (sqrtf(v) / bc2_sqrt + eps));
+}
+
+template <bool VEC>
+__global__ void adam_kernel(float* __restrict__ x, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v,
+                            const OfaDevState* __restrict__ st, size_t n, float b1, float b2,
+                            float eps) {
+  const float step_size = st->adam_step_size, bc2_sqrt = st->adam_bc2_sqrt;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (VEC) {
+    if (4 * i + 3 < n) {
+      float4 xv = reinterpret_cast<float4*>(x)[i];
+      const float4 gv = reinterpret_cast<const float4*>(g)[i];
+      float4 mv = reinterpret_cast<float4*>(m)[i];
+      float4 vv = reinterpret_cast<float4*>(v)[i];
+      adam_one(xv.x, gv.x, mv.x, vv.x, b1, b2, eps, step_size, bc2_sqrt);
+      adam_one(xv.y, gv.y, mv.y, vv.y, b1, b2, eps, step_size, bc2_sqrt);
+      adam_one(xv.z, gv.z, mv.z, vv.z, b1, b2, eps, step_size, bc2_sqrt);
+      adam_one(xv.w, gv.w, mv.w, vv.w, b1, b2, eps, step_size, bc2_sqrt);
+      reinterpret_cast<float4*>(x)[i] = xv;
+      reinterpret_cast<float4*>(m)[i] = mv;
+      reinterpret_cast<float4*>(v)[i] = vv;
+    } else {
+      for (size_t j = 4 * i; j < n; ++j) adam_one(x[j], g[j], m[j], v[j], b1, b2, eps,
+                                                   step_size, bc2_sqrt);
+    }
+  } else if (i < n) {
+    adam_one(x[i], g[i], m[i], v[i], b1, b2, eps, step_size, bc2_sqrt);
+  }
+}
 
 // P[n][2k..2k+1] = conj(Fy[k,n]) c_k in the operand format of the precision;
 // four foci per thread (kp is a multiple of 128): 16-byte loads and stores.
@@ -526,15 +647,29 @@ void launch_grad_c(const float2* theta, const float* g, int K, int kp, float in_
 void launch_loss_grad_c(const float2* theta, const float* t, int K, int kp, float2* c,
                         OfaDevState* st, float* loss_hist, int loss_cap, const int* step,
                         cudaStream_t s) {
-  loss_grad_c_kernel<<<1, FT, 0, s>>>(theta, t, K, kp, c, st, loss_hist, loss_cap, step);
+  if (K <= 2 * LT)
+    loss_grad_c_regs_kernel<2><<<1, LT, 0, s>>>(theta, t, K, kp, c, st, loss_hist, loss_cap,
+                                                step);
+  else if (K <= 16 * LT)
+    loss_grad_c_regs_kernel<16><<<1, LT, 0, s>>>(theta, t, K, kp, c, st, loss_hist, loss_cap,
+                                                 step);
+  else
+    loss_grad_c_kernel<<<1, FT, 0, s>>>(theta, t, K, kp, c, st, loss_hist, loss_cap, step);
 }
 
-void launch_adam(float* x, const float* g, float* m, float* v, int* step, size_t n, float lr,
-                 float b1, float b2, float eps, cudaStream_t s) {
-  size_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, g, m, v, step, n, lr, b1, b2, eps);
-  step_increment_kernel<<<1, 1, 0, s>>>(step);
+void launch_adam(float* x, const float* g, float* m, float* v, int* step, OfaDevState* st,
+                 size_t n, float lr, float b1, float b2, float eps, cudaStream_t s) {
+  adam_prepare_kernel<<<1, 1, 0, s>>>(step, st, lr, b1, b2);
+  const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(g) |
+                     reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+  if (vec) {
+    const size_t threads = (n + 3) / 4;
+    adam_kernel<true><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(x, g, m, v, st, n, b1,
+                                                                         b2, eps);
+  } else {
+    adam_kernel<false><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, g, m, v, st, n, b1, b2,
+                                                                    eps);
+  }
 }
 
 void launch_build_p(const float2* fyT, const float2* c, const int* done, int nyp, int kp,

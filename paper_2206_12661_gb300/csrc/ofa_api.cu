@@ -1337,7 +1337,8 @@ ofa_status ofa_adam_step(ofa_plan* p, float* phi, const float* grad_phi, float* 
       !(eps > 0.f))
     return ofa_fail(p, OFA_ERR_INVALID_ARG, "Adam needs lr > 0, 0 <= betas < 1, eps > 0");
   cudaSetDevice(p->device);
-  launch_adam(phi, grad_phi, m, v, step, (size_t)p->nx * p->ny, lr, beta1, beta2, eps, p->stream);
+  launch_adam(phi, grad_phi, m, v, step, p->st, (size_t)p->nx * p->ny, lr, beta1, beta2, eps,
+              p->stream);
   return ofa_cuda_check(p, cudaGetLastError(), "launching the Adam update");
 }
 

@@ -42,6 +42,8 @@ struct OfaDevState {
   double sum_i;
   double energy_fraction;
   float c_scale;      // power-of-two factor applied to c this iteration
+  float adam_step_size;   // lr / (1 - b1^t) of the latest ofa_adam_step
+  float adam_bc2_sqrt;    // sqrt(1 - b2^t) of the latest ofa_adam_step
   int pad_;
 };
 
@@ -272,9 +274,10 @@ void launch_build_p(const float2* fyT, const float2* c, const int* done, int nyp
 void launch_loss_grad_c(const float2* theta, const float* t, int K, int kp, float2* c,
                         OfaDevState* st, float* loss_hist, int loss_cap, const int* step,
                         cudaStream_t s);
-// Adam update of n parameters with the device step counter (then incremented).
-void launch_adam(float* x, const float* g, float* m, float* v, int* step, size_t n, float lr,
-                 float b1, float b2, float eps, cudaStream_t s);
+// Adam update of n parameters: the device step counter is advanced first and the
+// bias corrections for it are kept in st (adam_step_size, adam_bc2_sqrt).
+void launch_adam(float* x, const float* g, float* m, float* v, int* step, OfaDevState* st,
+                 size_t n, float lr, float b1, float b2, float eps, cudaStream_t s);
 
 // ---------------------------------------------------------------- kernels (k_umma.cu)
 cudaError_t tc_prepare(int prec);
