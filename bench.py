@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu --set full
 # capture of the kernel as it stands (cold caches, 1024^2 pupil, 1000 foci); an entry
 # is removed whenever that kernel changes.
-NCU_TRAFFIC_BYTES = {("f16x3", "forward"): 33638912, ("f16x3", "inverse"): 29413120}
+NCU_TRAFFIC_BYTES = {("f16x3", "forward"): 33632000, ("f16x3", "inverse"): 29405952}
 
 
 def load_peaks():
@@ -286,7 +286,8 @@ def bench_differentiation(ofa, I, torch, stream, flush, precision: str = "f16x3"
 def bench_batch(ofa, I, torch, stream, flush, n_iter: int = 50) -> dict:
     """256 holograms, pupils 512^2 / 768^2 / 1024^2, 16..4096 foci (log-uniform),
     jittered grids, 50 iterations: the grouped batch (f16x3), the same plans run
-    plan after plan, and the plain FP32 form plan after plan.  Unit: hologram
+    plan after plan, each hologram as one persistent fused-loop launch (plan after
+    plan), and the plain FP32 form plan after plan.  Unit: hologram
     iterations per second.  Timed with CUDA events on one stream after a warm-up."""
     ws = I.batch_workloads(count=256, n_iter=n_iter, seed=5)
     flop = sum(16.0 * w.nx * w.ny * w.n_foci for w in ws) * n_iter
@@ -321,6 +322,18 @@ def bench_batch(ofa, I, torch, stream, flush, n_iter: int = 50) -> dict:
     t = timed(lambda: [p.iterate(n_iter) for p in plans])
     out["plan_after_plan_f16x3"] = units / t
     for p in plans:
+        p.close()
+    # the persistent form: each hologram's iterations in one cooperative launch of the
+    # fused loop kernel (grid barriers between the phases), hologram after hologram
+    loops = [ofa.Plan.from_workload(w, precision="f16x3", stream=stream.cuda_stream,
+                                    autotune=False, fused_loop=1) for w in ws]
+    out["persistent_loop_holograms"] = sum(
+        ofa.ofa_plan_config(p.handle)["fused_loop"] == 1 for p in loops)
+    for p in loops:
+        p.iterate(1)
+    t = timed(lambda: [p.iterate(n_iter) for p in loops])
+    out["persistent_loop_plan_after_plan_f16x3"] = units / t
+    for p in loops:
         p.close()
     fp32 = [ofa.Plan.from_workload(w, precision="fp32", stream=stream.cuda_stream)
             for w in ws]
@@ -398,6 +411,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel-config", default=None,
+                    help="force the tensor-core tiles: fwd_bn,fwd_split,fwd_cg,inv_bn,inv_cg "
+                         "(as ofa_options.kernel_config; default: the plan's autotuner)")
+    ap.add_argument("--only", default=None,
+                    choices=["differentiation", "batch", "separable", "configs"],
+                    help="run one of the extra sections alone and print its JSON (for "
+                         "profiling runs; no timed loop, not a bench line)")
     ap.add_argument("--oracle-leg", default=None)
     ap.add_argument("--oracle-iters", type=int, default=1)
     args = ap.parse_args()
@@ -426,7 +446,21 @@ def main():
     w = I.named(WORKLOAD)
     n_iter = args.iters_per_step
     stream = torch.cuda.Stream()
-    plan = ofa.Plan.from_workload(w, precision=args.precision, stream=stream.cuda_stream)
+    if args.only:
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        sections = {
+            "differentiation": lambda: bench_differentiation(ofa, I, torch, stream, flush),
+            "batch": lambda: bench_batch(ofa, I, torch, stream, flush),
+            "separable": lambda: bench_separable(ofa, I, torch, stream, flush),
+            "configs": lambda: [bench_config(ofa, I, torch, stream, flush,
+                                             "pupil256_grid100_uniform", ("fp32", "f16x3"))]}
+        print(json.dumps({"section": args.only, args.only: sections[args.only]()}),
+              flush=True)
+        return 0
+    forced = ([int(x) for x in args.kernel_config.split(",")] if args.kernel_config
+              else None)
+    plan = ofa.Plan.from_workload(w, precision=args.precision, stream=stream.cuda_stream,
+                                  kernel_config=forced)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
