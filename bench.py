@@ -533,10 +533,11 @@ def main():
               "roofline": roofline, "clocks": clocks,
               "peaks": {"bf16_tflops": peaks["bf16_tflops"], "bf16_source": peak_src,
                         **{k: v for k, v in live.items()}}}
-    # fp32: forward, focal, inverse operand build, inverse; tensor-core forms: forward
-    # (+ fused focal step up to 4096 foci, else a separate focal kernel), inverse
-    # operand build, inverse
-    kernels_per_iter = 4 if (args.precision == "fp32" or w.n_foci > 4096) else 3
+    # forward (+ the focal step in its last block: up to 2048 foci in the FP32 form,
+    # 4096 in the tensor-core forms; else a separate focal kernel), inverse operand
+    # build, inverse
+    fused_limit = 2048 if args.precision == "fp32" else 4096
+    kernels_per_iter = 3 if w.n_foci <= fused_limit else 4
     result["gpu_launches"] = args.steps * (n_iter * kernels_per_iter + 1)
 
     if rank == 0 and not args.no_e2e:

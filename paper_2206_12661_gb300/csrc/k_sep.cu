@@ -124,7 +124,7 @@ template <int RT>
 __global__ void __launch_bounds__(FWD_THREADS, 1) sep_fwd_kernel(
     const float2* __restrict__ e32, const float2* __restrict__ fxu,
     const float2* __restrict__ fyu, const int2* __restrict__ ixy, int nx, int ny, int ux, int uy,
-    int K, int kp, int R, float2* __restrict__ part, const int* __restrict__ done, SepFocal f) {
+    int K, int kp, int R, float2* __restrict__ part, const int* __restrict__ done, FocalTail f) {
   pdl_launch_dependents();
   extern __shared__ float4 sep_smem4[];
   float2* ring = reinterpret_cast<float2*>(sep_smem4);
@@ -532,11 +532,11 @@ bool sep_fwd_fuses_focal(int ny, int K, int sms) {
 
 void launch_sep_fwd(const float2* e32, const float2* fxu, const float2* fyu, const int2* ixy,
                     int nx, int ny, int ux, int uy, int K, int kp, int sms, float2* part,
-                    const SepFocal& f, const int* done, cudaStream_t s) {
+                    const FocalTail& f, const int* done, cudaStream_t s) {
   const int R = sep_rows_per_block(ny, sms);
   const size_t smem = fwd_smem(R, ux, uy);
   const int blocks = sep_fwd_blocks(ny, sms);
-  SepFocal fk = f;
+  FocalTail fk = f;
   fk.on = f.on && sep_fwd_fuses_focal(ny, K, sms);
   visit_rt(R, [&](auto rc) {
     launch_pdl(sep_fwd_kernel<decltype(rc)::value>, dim3(blocks), FWD_THREADS, smem, s, e32, fxu,

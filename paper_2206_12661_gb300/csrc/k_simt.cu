@@ -31,6 +31,7 @@
 
 #include <algorithm>
 
+#include "ofa_focal.cuh"
 #include "ofa_internal.cuh"
 #include "ofa_math.cuh"
 
@@ -152,11 +153,15 @@ __device__ __forceinline__ int2 part_range(int len) {
 // Forward tile: rows n (E rows), columns k (foci), contraction m.
 // STORE: instead of the per-focus dot, write the product itself transposed,
 // gt[k][n] = G[n][k] (the separable grid form's first product).
+// With f.on (K <= 2048): the last row tile of each focus column to finish sums that
+// column's partial rows in order into row 0 (the order the focal kernel sums them), and
+// the last column to finish runs the focal step (f.counter: one counter per column
+// tile, then one for the columns).
 template <bool STORE>
 __global__ void __launch_bounds__(SIMT_THREADS, 4) fwd_simt_kernel(
     const float2* __restrict__ e32, const float2* __restrict__ fx, const float2* __restrict__ fy,
     int nx, int ny, int K, int kp, float2* __restrict__ part, const int* __restrict__ done,
-    float2* __restrict__ fws, unsigned* __restrict__ cnt) {
+    float2* __restrict__ fws, unsigned* __restrict__ cnt, FocalTail f) {
   if (done != nullptr && *done) return;
   __shared__ __align__(16) TileSmem sm;
   __shared__ float2 red[2][T64];
@@ -211,28 +216,82 @@ __global__ void __launch_bounds__(SIMT_THREADS, 4) fwd_simt_kernel(
     if (tid < T64) mine = make_float2(red[0][tid].x + red[1][tid].x, red[0][tid].y + red[1][tid].y);
     if (gridDim.z == 1) {
       if (tid < T64 && k < kp) part[(size_t)blockIdx.y * kp + k] = mine;
-      return;
-    }
-    // contraction parts: the last block of this tile sums them in order z = 0, 1, ...
-    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    float2* ws = fws + (size_t)tile * gridDim.z * T64;
-    if (tid < T64) ws[blockIdx.z * T64 + tid] = mine;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) last = atomicAdd(&cnt[tile], 1u) == gridDim.z - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (tid < T64) {
-      float2 a = make_float2(0.f, 0.f);
-      for (int z = 0; z < (int)gridDim.z; ++z) {
-        const float2 v = z == (int)blockIdx.z ? mine : __ldcg(&ws[z * T64 + tid]);
-        a.x += v.x;
-        a.y += v.y;
+    } else {
+      // contraction parts: the last block of this tile sums them in order z = 0, 1, ...
+      const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+      float2* ws = fws + (size_t)tile * gridDim.z * T64;
+      if (tid < T64) ws[blockIdx.z * T64 + tid] = mine;
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) last = atomicAdd(&cnt[tile], 1u) == gridDim.z - 1;
+      __syncthreads();
+      if (!last) return;
+      __threadfence();
+      if (tid < T64) {
+        float2 a = make_float2(0.f, 0.f);
+        for (int z = 0; z < (int)gridDim.z; ++z) {
+          const float2 v = z == (int)blockIdx.z ? mine : __ldcg(&ws[z * T64 + tid]);
+          a.x += v.x;
+          a.y += v.y;
+        }
+        if (k < kp) part[(size_t)blockIdx.y * kp + k] = a;
       }
-      if (k < kp) part[(size_t)blockIdx.y * kp + k] = a;
+      if (tid == 0) cnt[tile] = 0;
     }
-    if (tid == 0) cnt[tile] = 0;
+    if (!f.on) return;
+
+    // this focus column's partial rows (one per row tile) summed in order into row 0
+    __shared__ int tail_last;
+    __shared__ float focal_sh[4 * 33 + 4];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      tail_last = atomicAdd(&f.counter[blockIdx.x], 1u) == gridDim.y - 1;
+      if (tail_last) {
+        __threadfence();
+        f.counter[blockIdx.x] = 0u;
+      }
+    }
+    __syncthreads();
+    if (!tail_last) return;
+    if (tid < T64 && k < kp) {
+      constexpr int RB = 8;   // rows of loads in flight
+      float2 a = make_float2(0.f, 0.f);
+      for (int y0 = 0; y0 < (int)gridDim.y; y0 += RB) {
+        float2 v[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u)
+          v[u] = y0 + u < (int)gridDim.y ? __ldcg(part + (size_t)(y0 + u) * kp + k)
+                                         : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < RB; ++u)
+          if (y0 + u < (int)gridDim.y) {
+            a.x += v[u].x;
+            a.y += v[u].y;
+          }
+      }
+      part[k] = a;
+    }
+    // the last column runs the focal step on Theta
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      tail_last = atomicAdd(&f.counter[gridDim.x], 1u) == gridDim.x - 1;
+      if (tail_last) {
+        __threadfence();
+        f.counter[gridDim.x] = 0u;
+      }
+    }
+    __syncthreads();
+    if (!tail_last) return;
+    if (K <= SIMT_THREADS * 4)
+      ofa_focal::iterate_regs<SIMT_THREADS, 4>(part, 1, K, kp, f.t, f.w, f.c, f.hist, f.st,
+                                               f.weighting, focal_sh, tid,
+                                               ofa_focal::BarBlock());
+    else
+      ofa_focal::iterate_regs<SIMT_THREADS, 16>(part, 1, K, kp, f.t, f.w, f.c, f.hist, f.st,
+                                                f.weighting, focal_sh, tid,
+                                                ofa_focal::BarBlock());
   }
 }
 
@@ -451,7 +510,7 @@ SimtSizes simt_sizes(int nx, int ny, int K, int rows) {
   z.fxT = ldk * nx;
   z.fyT = ldk * ny;
   z.fws = (size_t)z.fwd_tiles * FWD_SPLIT * T64;
-  z.cnt = (size_t)z.fwd_tiles;
+  z.cnt = (size_t)z.fwd_tiles + tiles_of(K) + 1;   // tiles, focus columns, all columns
   return z;
 }
 
@@ -463,11 +522,19 @@ void launch_field_f32(const float* phi, const float* amp, int nx, int ny, float2
   field_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(phi, amp, n, e);
 }
 
+bool simt_fwd_fuses_focal(int K) { return K <= SIMT_THREADS * 16; }
+
 void launch_fwd_simt(const float2* e32, const float2* fx, const float2* fy, int nx, int ny, int K,
-                     int kp, float2* part, const int* done, const SimtWork& w, cudaStream_t s) {
+                     int kp, float2* part, const int* done, const SimtWork& w, cudaStream_t s,
+                     const FocalTail* f) {
   dim3 grid(tiles_of(K), tiles_of(ny), split_parts(nx, FWD_SPLIT));
+  FocalTail tail = {};
+  if (f && f->on && simt_fwd_fuses_focal(K)) {
+    tail = *f;
+    tail.counter = w.cnt + (size_t)tiles_of(K) * tiles_of(ny);   // after the tile counters
+  }
   fwd_simt_kernel<false><<<grid, SIMT_THREADS, 0, s>>>(e32, fx, fy, nx, ny, K, kp, part, done,
-                                                       w.fws, w.cnt);
+                                                       w.fws, w.cnt, tail);
 }
 
 int sep_parts(int nx, int ny, int ux, int sms) {
@@ -483,7 +550,7 @@ void launch_sep_forward(const float2* e32, const float2* fxu, int nx, int ny, in
                         float2* gt, cudaStream_t s) {
   dim3 grid((ux + T64 - 1) / T64, (ny + T64 - 1) / T64, parts);
   fwd_simt_kernel<true><<<grid, SIMT_THREADS, 0, s>>>(e32, fxu, nullptr, nx, ny, ux, ux, gt,
-                                                      nullptr, nullptr, nullptr);
+                                                      nullptr, nullptr, nullptr, FocalTail{});
 }
 
 void launch_sep_theta(float2* gt, const float2* fyu, const int2* ixy, int K, int ny, int ux,

@@ -300,7 +300,7 @@ void enqueue_sep_inverse(ofa_plan* p, const int* done, cudaStream_t s) {
 // Separable form, forward at the foci for the field e32: Theta in partial row 0.
 void enqueue_sep_forward(ofa_plan* p, const float2* e32, cudaStream_t s) {
   if (p->sep_fast) {
-    const SepFocal off = {};
+    const FocalTail off = {};
     launch_sep_fwd(e32, p->fxu, p->fyu, p->ixy, p->nx, p->ny, p->ux, p->uy, p->K, p->kp,
                    p->sm_count, p->part, off, nullptr, s);
     launch_sep_sum_focal(p->part, sep_fwd_blocks(p->ny, p->sm_count), p->K, p->kp, p->part, 0,
@@ -314,7 +314,7 @@ void enqueue_sep_forward(ofa_plan* p, const float2* e32, cudaStream_t s) {
 void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
   const int* done = done_ptr(p);
   if (p->sep && p->sep_fast) {
-    const SepFocal f = {p->t, p->w, p->c, p->hist, p->st, p->weighting, p->counters, 1};
+    const FocalTail f = {p->t, p->w, p->c, p->hist, p->st, p->weighting, p->counters, 1};
     launch_sep_fwd(p->e32, p->fxu, p->fyu, p->ixy, p->nx, p->ny, p->ux, p->uy, p->K, p->kp,
                    p->sm_count, p->part, f, done, s);
     if (!sep_fwd_fuses_focal(p->ny, p->K, p->sm_count))
@@ -327,9 +327,12 @@ void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
                  0, p->weighting, 1.f, p->amp_energy, s);
     enqueue_sep_inverse(p, done, s);
   } else if (!use_tc(p)) {
-    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, done, p->simt, s);
-    launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
-                 p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
+    const FocalTail f = {p->t, p->w, p->c, p->hist, p->st, p->weighting, nullptr, 1};
+    launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, done, p->simt, s,
+                    &f);
+    if (!simt_fwd_fuses_focal(p->K))
+      launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
+                   p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
     launch_bwd_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
                     done, p->simt, s);
   } else {

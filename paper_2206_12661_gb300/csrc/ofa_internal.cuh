@@ -79,7 +79,7 @@ struct SimtWork {
   float2* fxT = nullptr;      // [nx][ldk] conj(Fx)^T (separable: of the first inverse product)
   float2* fyT = nullptr;      // [ny][ldk] Fy^T (separable form: Fyu^T)
   float2* fws = nullptr;      // forward: [fwd_tiles][parts][64] partial per-focus dots
-  unsigned* cnt = nullptr;    // forward: [fwd_tiles] arrival counters
+  unsigned* cnt = nullptr;    // forward: [fwd_tiles + column tiles + 1] arrival counters
 };
 
 struct ofa_plan {
@@ -180,6 +180,19 @@ void launch_field_f32(const float* phi, const float* amp, int nx, int ny, float2
                       cudaStream_t s);
 // Element counts of the SimtWork buffers for a plan (rows = the longest inverse
 // contraction the plan runs, K or the separable form's uy).
+// The focal step's operands for a kernel that runs it in its last block (on != 0);
+// counter: the arrival counters that kernel uses (zero between launches).
+struct FocalTail {
+  const float* t;
+  float* w;
+  float2* c;
+  double* hist;
+  OfaDevState* st;
+  int weighting;
+  unsigned* counter;
+  int on;
+};
+
 struct SimtSizes {
   size_t p32, fxT, fyT, fws, cnt;
   int fwd_tiles;
@@ -187,8 +200,13 @@ struct SimtSizes {
 SimtSizes simt_sizes(int nx, int ny, int K, int rows);
 int simt_ldk(int K);   // row pitch of the transposed FP32 inverse operands
 
+// With f (f->on), the forward also sums the partial rows into Theta (row 0) and runs
+// the focal step in its last arriving block when simt_fwd_fuses_focal(K); otherwise
+// Theta is left as simt_fwd_tiles(ny) partial rows for launch_focal.
+bool simt_fwd_fuses_focal(int K);
 void launch_fwd_simt(const float2* e32, const float2* fx, const float2* fy, int nx, int ny, int K,
-                     int kp, float2* part, const int* done, const SimtWork& w, cudaStream_t s);
+                     int kp, float2* part, const int* done, const SimtWork& w, cudaStream_t s,
+                     const FocalTail* f = nullptr);
 int simt_fwd_tiles(int ny);   // partial Theta rows the forward writes
 // The inverse's left operand w.p32 = conj(fyT) c (the FP32 counterpart of build_p).
 void launch_scale_conj(const float2* c, const float2* fyT, int ny, int K, float2* pT,
@@ -225,23 +243,12 @@ size_t sep_inv_smem(int ux, int uy);
 bool sep_fast_shape(int nx, int uy);
 size_t sep_smem_limit();
 cudaError_t sep_prepare();
-// The focal step's operands for a kernel that runs it in its last block (on != 0).
-struct SepFocal {
-  const float* t;
-  float* w;
-  float2* c;
-  double* hist;
-  OfaDevState* st;
-  int weighting;
-  unsigned* counter;
-  int on;
-};
 // With f.on the forward runs the focal step itself when sep_fwd_fuses_focal (small
 // K); otherwise launch_sep_sum_focal follows it.
 bool sep_fwd_fuses_focal(int ny, int K, int sms);
 void launch_sep_fwd(const float2* e32, const float2* fxu, const float2* fyu, const int2* ixy,
                     int nx, int ny, int ux, int uy, int K, int kp, int sms, float2* part,
-                    const SepFocal& f, const int* done, cudaStream_t s);
+                    const FocalTail& f, const int* done, cudaStream_t s);
 void launch_sep_sum_focal(const float2* part, int nb, int K, int kp, float2* theta, int focal,
                           const float* t, float* w, float2* c, double* hist, OfaDevState* st,
                           int weighting, unsigned* counter, const int* done, cudaStream_t s);
