@@ -126,6 +126,16 @@ typedef struct ofa_options {
                                 pitch_y, and the default amplitude and phase are that pupil's
                                 rows.  Both 0 = the whole pupil (default).  Not with the
                                 separable form. */
+  int separable_loop;        /* separable form with K <= 512 foci: run each ofa_iterate call as
+                                one persistent cooperative launch (every block keeps its
+                                constant operands resident, computes the focal step itself
+                                and meets the others at grid barriers between the forward
+                                product, the partial-Theta sums and the inverse product).
+                                -1 = whenever the grid, its shared memory and the device
+                                allow it (default), 0 = never (two or three launches per
+                                iteration from CUDA graphs), 1 = always (OFA_ERR_UNSUPPORTED
+                                if it cannot run).  ofa_plan_config reports it as the fused
+                                loop. */
 } ofa_options;
 
 typedef struct ofa_stats {

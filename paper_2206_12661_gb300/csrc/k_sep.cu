@@ -116,64 +116,32 @@ __device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
 constexpr size_t FWD_SLOT = (size_t)4 * FWD_MT * FWD_GROUP;
 constexpr size_t FWD_RING = (size_t)FWD_STAGES * FWD_SLOT;
 
-// Block: pupil rows [n0, n0 + R), R <= 2 RT; thread (group g, t) holds E of rows
-// n0 + g RT + [0, RT) at the columns t + 256 j, j < 4.  With f.on, the block that
-// finishes last also sums the partial rows (staged in the idle ring) into Theta and
-// runs the focal step (K <= FWD_THREADS).
-template <int RT>
-__global__ void __launch_bounds__(FWD_THREADS, 1) sep_fwd_kernel(
-    const float2* __restrict__ e32, const float2* __restrict__ fxu,
-    const float2* __restrict__ fyu, const int2* __restrict__ ixy, int nx, int ny, int ux, int uy,
-    int K, int kp, int R, float2* __restrict__ part, const int* __restrict__ done, FocalTail f) {
-  pdl_launch_dependents();
-  extern __shared__ float4 sep_smem4[];
-  float2* ring = reinterpret_cast<float2*>(sep_smem4);
-  const int nquad = (ux + 3) >> 2;
-  float* red = reinterpret_cast<float*>(ring + FWD_RING);                         // [nquad][16][32]
-  float2* gs = reinterpret_cast<float2*>(red + (size_t)nquad * FWD_WARPS * 32);   // [R][ux]
-  float2* fs = gs + (size_t)R * ux;                                                // [uy][R]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = tid / FWD_GROUP, t = tid % FWD_GROUP;
-  const int n0 = blockIdx.x * R;
-  const int rows = min(R, ny - n0);
-  const int rows_g = max(0, min(RT, rows - g * RT));
-
-  // Fxu rows 4q .. 4q + 3 into ring slot q % FWD_STAGES, all columns: element
-  // (c, j, t) is Fxu[4q + c][t + 256 j]
-  auto issue = [&](int q) {
-    if (q < nquad) {
-      float2* dst = ring + (size_t)(q % FWD_STAGES) * FWD_SLOT;
+// Fxu rows 4q .. 4q + 3 into ring slot q % FWD_STAGES, all columns (element (c, j, t)
+// is Fxu[4q + c][t + 256 j]), as one cp.async group of the calling thread; past the
+// last quad the group is empty, which keeps the group count uniform.
+__device__ __forceinline__ void fwd_issue(float2* ring, const float2* __restrict__ fxu, int ux,
+                                          int nx, int q, int tid) {
+  if (q < ((ux + 3) >> 2)) {
+    float2* dst = ring + (size_t)(q % FWD_STAGES) * FWD_SLOT;
 #pragma unroll
-      for (int i = 0; i < (int)(FWD_SLOT / FWD_THREADS); ++i) {
-        const int idx = tid + i * FWD_THREADS;
-        const int c = idx / (FWD_MT * FWD_GROUP);
-        const int m = idx % (FWD_MT * FWD_GROUP);   // = t' + 256 j'
-        const int ix = 4 * q + c;
-        const bool ok = ix < ux && m < nx;
-        cp_async8(dst + idx, ok ? fxu + (size_t)ix * nx + m : fxu, ok);
-      }
+    for (int i = 0; i < (int)(FWD_SLOT / FWD_THREADS); ++i) {
+      const int idx = tid + i * FWD_THREADS;
+      const int c = idx / (FWD_MT * FWD_GROUP);
+      const int m = idx % (FWD_MT * FWD_GROUP);   // = t' + 256 j'
+      const int ix = 4 * q + c;
+      const bool ok = ix < ux && m < nx;
+      cp_async8(dst + idx, ok ? fxu + (size_t)ix * nx + m : fxu, ok);
     }
-    cp_async_commit();   // an empty group past the end keeps the group count uniform
-  };
-#pragma unroll
-  for (int q = 0; q < FWD_STAGES - 1; ++q) issue(q);
-  for (int i = tid; i < uy * R; i += FWD_THREADS) {
-    const int iy = i / R, r = i - iy * R;
-    fs[i] = r < rows ? __ldg(fyu + (size_t)iy * ny + n0 + r) : make_float2(0.f, 0.f);
   }
-  // grid indices of this thread's first foci
-  constexpr int KR = 4;
-  int2 xyr[KR];
-#pragma unroll
-  for (int i = 0; i < KR; ++i) {
-    const int k = tid + i * FWD_THREADS;
-    xyr[i] = k < K ? __ldg(ixy + k) : make_int2(0, 0);
-  }
+  cp_async_commit();
+}
 
-  pdl_wait();   // E and the stop flag come from the kernels before this one
-  const int stop = done != nullptr ? __ldcg(done) : 0;
-  // this thread's E values, all loads in flight together
-  float2 e[RT][FWD_MT];
+// E of this thread's pupil rows n0 + g RT + r at the columns t + 256 j (zero outside).
+template <int RT>
+__device__ __forceinline__ void fwd_load_e(float2 (&e)[RT][FWD_MT], const float2* __restrict__ e32,
+                                           int nx, int n0, int rows, int tid) {
+  const int g = tid / FWD_GROUP, t = tid % FWD_GROUP;
+  const int rows_g = max(0, min(RT, rows - g * RT));
 #pragma unroll
   for (int r = 0; r < RT; ++r)
 #pragma unroll
@@ -182,17 +150,24 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) sep_fwd_kernel(
       e[r][j] = (r < rows_g && m < nx) ? __ldcg(e32 + (size_t)(n0 + g * RT + r) * nx + m)
                                        : make_float2(0.f, 0.f);
     }
-  if (stop) {
-    cp_async_wait<0>();   // no copy may land after the block has left
-    return;
-  }
+}
 
+// G of the block's R pupil rows into gs [R][ux]: E in registers, Fxu streamed through
+// the ring (this thread has issued quads 0 .. FWD_STAGES - 2), each thread's
+// contributions summed by a warp reduce-scatter into red, then over the 8 warps of the
+// row's group in order.  Ends with a block barrier after gs is complete.
+template <int RT>
+__device__ __forceinline__ void fwd_g(const float2 (&e)[RT][FWD_MT], float2* ring, float* red,
+                                      float2* gs, const float2* __restrict__ fxu, int ux, int nx,
+                                      int R, int tid) {
+  const int lane = tid & 31, warp = tid >> 5, t = tid % FWD_GROUP;
+  const int nquad = (ux + 3) >> 2;
   for (int q = 0; q < nquad; ++q) {
     cp_async_wait<FWD_STAGES - 2>();   // this thread's copies of quad q have landed
     __syncthreads();                   // everyone's have; slot (q - 1) % S is free
-    issue(q + FWD_STAGES - 1);
+    fwd_issue(ring, fxu, ux, nx, q + FWD_STAGES - 1, tid);
     const float2* src = ring + (size_t)(q % FWD_STAGES) * FWD_SLOT;
-    // v[8 c + 2 r + {0, 1}]: this thread's part of G[n0 + g RT + r][4q + c]
+    // v[8 c + 2 r + {0, 1}]: this thread's part of G[g RT + r][4q + c]
     float v[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = 0.f;
@@ -212,21 +187,66 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) sep_fwd_kernel(
     red[((size_t)q * FWD_WARPS + warp) * 32 + lane] = reduce_scatter32(v, lane);
   }
   __syncthreads();
-  // G[r][ix] = sum over the 8 warps of the row's group, in order
   for (int i = tid; i < R * ux; i += FWD_THREADS) {
     const int r = i / ux, ix = i - r * ux;
     const int gr = r / RT, rr = r - gr * RT;
     const int el = (ix & 3) * 8 + 2 * rr;
-    const float* s = red + ((size_t)(ix >> 2) * FWD_WARPS + gr * (FWD_GROUP / 32)) * 32;
+    const float* sp = red + ((size_t)(ix >> 2) * FWD_WARPS + gr * (FWD_GROUP / 32)) * 32;
     float2 gv = make_float2(0.f, 0.f);
 #pragma unroll
     for (int w = 0; w < FWD_GROUP / 32; ++w) {
-      gv.x += s[w * 32 + el];
-      gv.y += s[w * 32 + el + 1];
+      gv.x += sp[w * 32 + el];
+      gv.y += sp[w * 32 + el + 1];
     }
     gs[i] = gv;
   }
   __syncthreads();
+}
+
+// Block: pupil rows [n0, n0 + R), R <= 2 RT; thread (group g, t) holds E of rows
+// n0 + g RT + [0, RT) at the columns t + 256 j, j < 4.  With f.on, the block that
+// finishes last also sums the partial rows (staged in the idle ring) into Theta and
+// runs the focal step (K <= FWD_THREADS).
+template <int RT>
+__global__ void __launch_bounds__(FWD_THREADS, 1) sep_fwd_kernel(
+    const float2* __restrict__ e32, const float2* __restrict__ fxu,
+    const float2* __restrict__ fyu, const int2* __restrict__ ixy, int nx, int ny, int ux, int uy,
+    int K, int kp, int R, float2* __restrict__ part, const int* __restrict__ done, FocalTail f) {
+  pdl_launch_dependents();
+  extern __shared__ float4 sep_smem4[];
+  float2* ring = reinterpret_cast<float2*>(sep_smem4);
+  const int nquad = (ux + 3) >> 2;
+  float* red = reinterpret_cast<float*>(ring + FWD_RING);                         // [nquad][16][32]
+  float2* gs = reinterpret_cast<float2*>(red + (size_t)nquad * FWD_WARPS * 32);   // [R][ux]
+  float2* fs = gs + (size_t)R * ux;                                                // [uy][R]
+  const int tid = threadIdx.x;
+  const int n0 = blockIdx.x * R;
+  const int rows = min(R, ny - n0);
+
+#pragma unroll
+  for (int q = 0; q < FWD_STAGES - 1; ++q) fwd_issue(ring, fxu, ux, nx, q, tid);
+  for (int i = tid; i < uy * R; i += FWD_THREADS) {
+    const int iy = i / R, r = i - iy * R;
+    fs[i] = r < rows ? __ldg(fyu + (size_t)iy * ny + n0 + r) : make_float2(0.f, 0.f);
+  }
+  // grid indices of this thread's first foci
+  constexpr int KR = 4;
+  int2 xyr[KR];
+#pragma unroll
+  for (int i = 0; i < KR; ++i) {
+    const int k = tid + i * FWD_THREADS;
+    xyr[i] = k < K ? __ldg(ixy + k) : make_int2(0, 0);
+  }
+
+  pdl_wait();   // E and the stop flag come from the kernels before this one
+  const int stop = done != nullptr ? __ldcg(done) : 0;
+  float2 e[RT][FWD_MT];
+  fwd_load_e<RT>(e, e32, nx, n0, rows, tid);   // all loads in flight together
+  if (stop) {
+    cp_async_wait<0>();   // no copy may land after the block has left
+    return;
+  }
+  fwd_g<RT>(e, ring, red, gs, fxu, ux, nx, R, tid);
   // this block's partial Theta: sum over its rows of Fyu[iy_k][n] G[n][ix_k]
   float2* dst = part + (size_t)blockIdx.x * kp;
 #pragma unroll
@@ -352,52 +372,18 @@ __global__ void __launch_bounds__(SEP_THREADS) sep_sum_focal_kernel(
                                     ofa_focal::BarBlock());
 }
 
-// Shared memory of the inverse: Fyu rows of the tile [uy][INV_ROWS] (first: 16-byte
-// aligned for its paired loads), C [uy][ux], Fxu columns of the tile [ux][INV_COLS],
-// T [uy][INV_COLS].
-__global__ void __launch_bounds__(INV_THREADS, 1) sep_inv_kernel(
-    const float2* __restrict__ c, const int* __restrict__ gridk, const float2* __restrict__ fxu,
-    const float2* __restrict__ fyu, const float* __restrict__ amp, int nx, int ny, int ux,
-    int uy, float* __restrict__ phi, float2* __restrict__ e32, const int* __restrict__ done) {
-  pdl_launch_dependents();
-  extern __shared__ float4 sep_smem4[];
-  float2* fys = reinterpret_cast<float2*>(sep_smem4);
-  float2* cs = fys + (size_t)uy * INV_ROWS;
-  float2* fxs = cs + (size_t)uy * ux;
-  float2* ts = fxs + (size_t)ux * INV_COLS;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m0 = blockIdx.x * INV_COLS, n0 = blockIdx.y * INV_ROWS;
+// T for a tile's 32 pixel columns, then E' over the warp's INV_RPW rows and the
+// projection.  fys: the tile's Fyu rows [uy][INV_ROWS] (16-byte aligned), fxs: its Fxu
+// columns [ux][INV_COLS], cs: C on the grid [uy][ux], all complete in shared memory;
+// ts: scratch [uy][INV_COLS]; av: this thread's amplitudes (rows n0 + 16 warp + i,
+// column m0 + lane).  Writes phi = arg E' and the next field A E'/|E'| (= A e^{i phi};
+// A where E' = 0).  Contains one block barrier.
+__device__ __forceinline__ void inv_tile(const float2* fys, const float2* fxs, const float2* cs,
+                                         float2* ts, const float (&av)[INV_RPW], int ux, int uy,
+                                         int nx, int ny, int m0, int n0, float* __restrict__ phi,
+                                         float2* __restrict__ e32, int tid) {
+  const int lane = tid & 31, warp = tid >> 5;
   const int nw0 = n0 + warp * INV_RPW;   // this warp's first row
-  // the tile's constant operands, asynchronously
-  for (int i = tid; i < uy * INV_ROWS; i += INV_THREADS) {
-    const int iy = i / INV_ROWS, n = n0 + (i - iy * INV_ROWS);
-    cp_async8(fys + i, n < ny ? fyu + (size_t)iy * ny + n : fyu, n < ny);
-  }
-  for (int i = tid; i < ux * INV_COLS; i += INV_THREADS) {
-    const int ix = i / INV_COLS, m = m0 + (i - ix * INV_COLS);
-    cp_async8(fxs + i, m < nx ? fxu + (size_t)ix * nx + m : fxu, m < nx);
-  }
-  cp_async_commit();
-  // the grid map (the focus index in the low word until c is known) and the
-  // amplitudes of this thread's pixels
-  for (int i = tid; i < uy * ux; i += INV_THREADS)
-    cs[i] = make_float2(__int_as_float(__ldg(gridk + i)), 0.f);
-  const int m = m0 + lane;
-  float av[INV_RPW];
-#pragma unroll
-  for (int i = 0; i < INV_RPW; ++i)
-    av[i] = (nw0 + i < ny && m < nx) ? __ldg(amp + (size_t)(nw0 + i) * nx + m) : 0.f;
-
-  pdl_wait();   // c and the stop flag come from the kernel before this one
-  const int stop = done != nullptr ? __ldcg(done) : 0;
-  // C on the grid: each thread fills the entries it mapped above
-  for (int i = tid; i < uy * ux; i += INV_THREADS) {
-    const int k = __float_as_int(cs[i].x);
-    cs[i] = k >= 0 ? __ldcg(c + k) : make_float2(0.f, 0.f);
-  }
-  cp_async_wait<0>();
-  if (stop) return;
-  __syncthreads();
   // T[iy][m0 + lane] for iy = warp, warp + 16, ...: sum over ix in order of
   // C[iy][ix] conj(Fxu[ix][m])
   {
@@ -435,21 +421,455 @@ __global__ void __launch_bounds__(INV_THREADS, 1) sep_inv_kernel(
       cmac_conj(acc[2 * i + 1], make_float2(q.z, q.w), tv);
     }
   }
+  const int m = m0 + lane;
   if (m >= nx) return;
-  // projection: phi = arg E' and the next field A exp(i phi) = A E' / |E'| (A at
-  // E' = 0); the pixels are independent, so their chains interleave
+  // projection; the pixels are independent, so their chains interleave
 #pragma unroll
   for (int i = 0; i < INV_RPW; ++i) {
     const float ph = ofa_arg(acc[i].y, acc[i].x);   // arg(0) = 0
     const float r2 = acc[i].x * acc[i].x + acc[i].y * acc[i].y;
-    const float s = r2 > 0.f ? av[i] * rsqrtf(r2) : 0.f;
-    const float2 ev = r2 > 0.f ? make_float2(s * acc[i].x, s * acc[i].y) : make_float2(av[i], 0.f);
+    const float sc = r2 > 0.f ? av[i] * rsqrtf(r2) : 0.f;
+    const float2 ev = r2 > 0.f ? make_float2(sc * acc[i].x, sc * acc[i].y) : make_float2(av[i], 0.f);
     if (nw0 + i < ny) {
       const size_t o = (size_t)(nw0 + i) * nx + m;
       phi[o] = ph;
       e32[o] = ev;
     }
   }
+}
+
+// The tile's constant operands into shared memory, asynchronously (one commit group).
+__device__ __forceinline__ void inv_stage_constants(float2* fys, float2* fxs,
+                                                    const float2* __restrict__ fyu,
+                                                    const float2* __restrict__ fxu, int ux,
+                                                    int uy, int nx, int ny, int m0, int n0,
+                                                    int tid, int nthreads) {
+  for (int i = tid; i < uy * INV_ROWS; i += nthreads) {
+    const int iy = i / INV_ROWS, n = n0 + (i - iy * INV_ROWS);
+    cp_async8(fys + i, n < ny ? fyu + (size_t)iy * ny + n : fyu, n < ny);
+  }
+  for (int i = tid; i < ux * INV_COLS; i += nthreads) {
+    const int ix = i / INV_COLS, m = m0 + (i - ix * INV_COLS);
+    cp_async8(fxs + i, m < nx ? fxu + (size_t)ix * nx + m : fxu, m < nx);
+  }
+  cp_async_commit();
+}
+
+// Shared memory of the inverse: Fyu rows of the tile [uy][INV_ROWS] (first: 16-byte
+// aligned for its paired loads), C [uy][ux], Fxu columns of the tile [ux][INV_COLS],
+// T [uy][INV_COLS].
+__global__ void __launch_bounds__(INV_THREADS, 1) sep_inv_kernel(
+    const float2* __restrict__ c, const int* __restrict__ gridk, const float2* __restrict__ fxu,
+    const float2* __restrict__ fyu, const float* __restrict__ amp, int nx, int ny, int ux,
+    int uy, float* __restrict__ phi, float2* __restrict__ e32, const int* __restrict__ done) {
+  pdl_launch_dependents();
+  extern __shared__ float4 sep_smem4[];
+  float2* fys = reinterpret_cast<float2*>(sep_smem4);
+  float2* cs = fys + (size_t)uy * INV_ROWS;
+  float2* fxs = cs + (size_t)uy * ux;
+  float2* ts = fxs + (size_t)ux * INV_COLS;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.x * INV_COLS, n0 = blockIdx.y * INV_ROWS;
+  const int nw0 = n0 + warp * INV_RPW;
+  inv_stage_constants(fys, fxs, fyu, fxu, ux, uy, nx, ny, m0, n0, tid, INV_THREADS);
+  // the grid map (the focus index in the low word until c is known) and the
+  // amplitudes of this thread's pixels
+  for (int i = tid; i < uy * ux; i += INV_THREADS)
+    cs[i] = make_float2(__int_as_float(__ldg(gridk + i)), 0.f);
+  const int m = m0 + lane;
+  float av[INV_RPW];
+#pragma unroll
+  for (int i = 0; i < INV_RPW; ++i)
+    av[i] = (nw0 + i < ny && m < nx) ? __ldg(amp + (size_t)(nw0 + i) * nx + m) : 0.f;
+
+  pdl_wait();   // c and the stop flag come from the kernel before this one
+  const int stop = done != nullptr ? __ldcg(done) : 0;
+  // C on the grid: each thread fills the entries it mapped above
+  for (int i = tid; i < uy * ux; i += INV_THREADS) {
+    const int k = __float_as_int(cs[i].x);
+    cs[i] = k >= 0 ? __ldcg(c + k) : make_float2(0.f, 0.f);
+  }
+  cp_async_wait<0>();
+  if (stop) return;
+  __syncthreads();
+  inv_tile(fys, fxs, cs, ts, av, ux, uy, nx, ny, m0, n0, phi, e32, tid);
+}
+
+// ---------------------------------------------------------------- persistent loop
+// All iterations of an ofa_iterate call in one cooperative launch.  Block b owns pupil
+// rows [b R, b R + R) for both products, and each thread keeps the pupil field E (and A)
+// of its pixels in registers across iterations:
+//   forward  the block's partial Theta row, as sep_fwd_kernel computes it;
+//   barrier; block b sums the partial rows of a slice of the foci (a warp per focus, in
+//   fixed order) into Theta; barrier;
+//   focal    every block runs the focal step on Theta identically (block 0 alone writes
+//            w, c, xi and the state);
+//   inverse  the adjoint restricted to the block's rows factors through
+//            U[n][ix] = sum_iy C[iy][ix] conj(Fyu[iy][n]) (R x U_x values per block):
+//            E'[n][m] = sum_ix U[n][ix] conj(Fxu[ix][m]), with Fxu streamed through the
+//            same ring as the forward and no cross-thread reduction; then the next
+//            E = A E'/|E'| in registers (phi = arg E' and the stored field are written
+//            on the last iteration, or on every one when a threshold can stop the loop).
+// Two grid barriers per iteration; every wait gives up after one second
+// (OFA_ERRBIT_TIMEOUT) and the block leaves.
+constexpr int LOOP_KPR = 5;                       // foci per thread: K <= 2560
+constexpr int LOOP_KMAX = LOOP_KPR * FWD_THREADS;
+
+struct LoopLayout {
+  size_t ring, red, gs, fs, us, cs, cl, wl, tl, gk, scr, total;
+};
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline LoopLayout loop_layout(int R, int ux, int uy) {
+  LoopLayout L;
+  const int uxp = (ux + 3) & ~3;   // U padded to whole quads of grid columns
+  size_t o = 0;
+  L.ring = o; o = align16(o + sizeof(float2) * FWD_RING);
+  L.red = o;  o = align16(o + sizeof(float) * (size_t)(uxp / 4) * FWD_WARPS * 32);
+  L.gs = o;   o = align16(o + sizeof(float2) * (size_t)R * ux);
+  L.fs = o;   o = align16(o + sizeof(float2) * (size_t)uy * R);
+  L.us = o;   o = align16(o + sizeof(float2) * (size_t)R * uxp);
+  L.cs = o;   o = align16(o + sizeof(float2) * (size_t)uy * ux);
+  L.cl = o;   o = align16(o + sizeof(float2) * LOOP_KMAX);
+  L.wl = o;   o = align16(o + sizeof(float) * LOOP_KMAX);
+  L.tl = o;   o = align16(o + sizeof(float) * LOOP_KMAX);
+  L.gk = o;   o = align16(o + sizeof(int) * (size_t)uy * ux);
+  L.scr = o;  o = align16(o + sizeof(float) * 4 * FWD_WARPS);
+  L.total = o;
+  return L;
+}
+
+struct SepLoopArgs {
+  const float2* fxu;
+  const float2* fyu;
+  const int2* ixy;
+  const int* gridk;
+  const float* amp;
+  float2* e32;
+  float* phi;
+  float2* part;
+  float2* theta;
+  float2* c;
+  const float* t;
+  float* w;
+  double* hist;
+  OfaDevState* st;
+  unsigned* bar;   // two counters, zero at launch
+  double threshold;
+  int nx, ny, ux, uy, K, kp, R, weighting, n_iter;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* q) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(q) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch: the block's writes are released by thread
+// 0 (CTA barrier, then a gpu-scope fence and a release add), and the wait for all
+// arrivals (the counter reaching target) is bounded.  Returns false when it gave up.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    int ok = 1;
+    if (ld_acquire_gpu(bar) < target) {
+      const uint64_t t0 = ofa_ptx::gtimer();
+      while (ld_acquire_gpu(bar) < target) {
+        __nanosleep(64);
+        if (ofa_ptx::gtimer() - t0 > ofa_ptx::WAIT_NS) {
+          ok = ld_acquire_gpu(bar) >= target;
+          break;
+        }
+      }
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// Sum of one value per thread over the block in a fixed order (warp butterfly, then the
+// warp partials in warp order); every thread receives the same bits.
+__device__ __forceinline__ float loop_block_sum(float v, float* scr, int tid) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((tid & 31) == 0) scr[tid >> 5] = v;
+  __syncthreads();
+  float r = scr[0];
+#pragma unroll
+  for (int w = 1; w < FWD_WARPS; ++w) r += scr[w];
+  return r;
+}
+
+// Two sums and a max of one value each per thread, in one round of the same fixed order.
+__device__ __forceinline__ void loop_block_reduce3(float& s0, float& s1, float& mx, float* scr,
+                                                   int tid) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  __syncthreads();
+  if ((tid & 31) == 0) {
+    scr[tid >> 5] = s0;
+    scr[FWD_WARPS + (tid >> 5)] = s1;
+    scr[2 * FWD_WARPS + (tid >> 5)] = mx;
+  }
+  __syncthreads();
+  s0 = scr[0];
+  s1 = scr[FWD_WARPS];
+  mx = scr[2 * FWD_WARPS];
+#pragma unroll
+  for (int w = 1; w < FWD_WARPS; ++w) {
+    s0 += scr[w];
+    s1 += scr[FWD_WARPS + w];
+    mx = fmaxf(mx, scr[2 * FWD_WARPS + w]);
+  }
+}
+
+template <int RT>
+__global__ void __launch_bounds__(FWD_THREADS, 1) sep_loop_kernel(SepLoopArgs a) {
+  extern __shared__ float4 sep_smem4[];
+  char* base = reinterpret_cast<char*>(sep_smem4);
+  const LoopLayout L = loop_layout(a.R, a.ux, a.uy);
+  float2* ring = reinterpret_cast<float2*>(base + L.ring);
+  float* red = reinterpret_cast<float*>(base + L.red);
+  float2* gs = reinterpret_cast<float2*>(base + L.gs);
+  float2* fs = reinterpret_cast<float2*>(base + L.fs);
+  float2* us = reinterpret_cast<float2*>(base + L.us);
+  float2* cs = reinterpret_cast<float2*>(base + L.cs);
+  float2* cl = reinterpret_cast<float2*>(base + L.cl);
+  float* wl = reinterpret_cast<float*>(base + L.wl);
+  float* tl = reinterpret_cast<float*>(base + L.tl);
+  int* gk = reinterpret_cast<int*>(base + L.gk);
+  float* scr = reinterpret_cast<float*>(base + L.scr);
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.x, G = gridDim.x;
+  const int nx = a.nx, ny = a.ny, ux = a.ux, uy = a.uy, K = a.K, R = a.R;
+  const int uxp = (ux + 3) & ~3, nquad = uxp >> 2;
+  if (tid == 0) s_ok = 1;
+  const int g = tid / FWD_GROUP, t = tid % FWD_GROUP;
+  const int n0 = b * R, rows = min(R, ny - n0);
+  const int rows_g = max(0, min(RT, rows - g * RT));
+  const bool writer = b == 0;
+
+  // ---- constants and state, once per launch
+#pragma unroll
+  for (int q = 0; q < FWD_STAGES - 1; ++q) fwd_issue(ring, a.fxu, ux, nx, q, tid);
+  for (int i = tid; i < uy * R; i += FWD_THREADS) {
+    const int iy = i / R, r = i - iy * R;
+    fs[i] = r < rows ? __ldg(a.fyu + (size_t)iy * ny + n0 + r) : make_float2(0.f, 0.f);
+  }
+  for (int i = tid; i < uy * ux; i += FWD_THREADS) gk[i] = __ldg(a.gridk + i);
+  for (int k = tid; k < LOOP_KMAX; k += FWD_THREADS) {
+    tl[k] = k < K ? __ldg(a.t + k) : 0.f;
+    wl[k] = k < K ? __ldcg(a.w + k) : 0.f;
+  }
+  int2 xy[LOOP_KPR];
+#pragma unroll
+  for (int i = 0; i < LOOP_KPR; ++i) {
+    const int k = tid + i * FWD_THREADS;
+    xy[i] = k < K ? __ldg(a.ixy + k) : make_int2(0, 0);
+  }
+  float2 e[RT][FWD_MT];
+  float av[RT][FWD_MT];
+  fwd_load_e<RT>(e, a.e32, nx, n0, rows, tid);
+#pragma unroll
+  for (int r = 0; r < RT; ++r)
+#pragma unroll
+    for (int j = 0; j < FWD_MT; ++j) {
+      const int m = t + j * FWD_GROUP;
+      av[r][j] = (r < rows_g && m < nx) ? __ldg(a.amp + (size_t)(n0 + g * RT + r) * nx + m)
+                                        : 0.f;
+    }
+  const int h0 = __ldcg(&a.st->hist_count), j0 = __ldcg(&a.st->j);
+  const int stop0 = __ldcg(&a.st->done);
+  __syncthreads();
+  if (stop0) {
+    cp_async_wait<0>();
+    return;
+  }
+  const bool thr_on = a.threshold > 0.0 && a.threshold < 1.0;
+  const int fpb = (K + G - 1) / G;   // foci whose partial rows this block sums
+
+  for (int it = 0; it < a.n_iter; ++it) {
+    const unsigned target = (unsigned)(it + 1) * (unsigned)G;
+    // ---- forward: this block's partial Theta row
+    fwd_g<RT>(e, ring, red, gs, a.fxu, ux, nx, R, tid);
+#pragma unroll
+    for (int i = 0; i < LOOP_KPR; ++i) {
+      const int k = tid + i * FWD_THREADS;
+      if (k < a.kp) {
+        float2 acc = make_float2(0.f, 0.f);
+        if (k < K)
+          for (int r = 0; r < R; ++r) cmac(acc, fs[xy[i].y * R + r], gs[r * ux + xy[i].x]);
+        a.part[(size_t)b * a.kp + k] = acc;
+      }
+    }
+    // the inverse pass streams the same Fxu quads again
+#pragma unroll
+    for (int q = 0; q < FWD_STAGES - 1; ++q) fwd_issue(ring, a.fxu, ux, nx, q, tid);
+    if (!grid_barrier(a.bar + 0, target, &s_ok)) break;
+    // ---- Theta_k for this block's foci: warp per focus, lanes over the rows in order
+    for (int kk = warp; kk < fpb; kk += FWD_WARPS) {
+      const int k = b * fpb + kk;
+      if (k >= K) break;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int p = lane; p < G; p += 32) {
+        const float2 v = __ldcg(a.part + (size_t)p * a.kp + k);
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) a.theta[k] = acc;
+    }
+    if (!grid_barrier(a.bar + 1, target, &s_ok)) break;
+    // ---- focal step (Algorithm 1), identical in every block
+    float2 th[LOOP_KPR];
+    float ik[LOOP_KPR], s_part = 0.f;
+#pragma unroll
+    for (int i = 0; i < LOOP_KPR; ++i) {
+      const int k = tid + i * FWD_THREADS;
+      th[i] = k < K ? __ldcg(a.theta + k) : make_float2(0.f, 0.f);
+      ik[i] = th[i].x * th[i].x + th[i].y * th[i].y;
+      s_part += ik[i];
+    }
+    const float S = loop_block_sum(s_part, scr, tid);
+    if (!(S > 0.f) || !isfinite(S)) {
+      if (writer && tid == 0) {
+        atomicOr(&a.st->err, OFA_ERRBIT_NUMERIC);
+        a.st->done = 1;
+      }
+      break;
+    }
+    const float inv_s = 1.f / S;
+    float wk[LOOP_KPR], sq[LOOP_KPR], r0 = 0.f, r1 = 0.f, mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < LOOP_KPR; ++i) {
+      const int k = tid + i * FWD_THREADS;
+      sq[i] = sqrtf(tl[k < LOOP_KMAX ? k : 0]);
+      wk[i] = wl[k < LOOP_KMAX ? k : 0];
+      if (k >= K) continue;
+      const float ih = ik[i] * inv_s, d = tl[k] - ih;
+      r0 += d * d;
+      r1 += ih * ih;
+      if (a.weighting) wk[i] *= sq[i] * rsqrtf(fmaxf(ih, 1e-30f));   // w sqrt(t / Ihat)
+      mx = fmaxf(mx, wk[i] * sq[i]);
+    }
+    loop_block_reduce3(r0, r1, mx, scr, tid);
+    const float xi = 1.f - sqrtf(r0 / r1);
+    if (writer && tid == 0) {
+      a.hist[(h0 + it) % OFA_HIST_CAP] = (double)xi;
+      a.st->hist_count = h0 + it + 1;
+      a.st->xi = (double)xi;
+    }
+    if (thr_on && (double)xi > a.threshold) {
+      if (writer && tid == 0) a.st->done = 1;
+      break;
+    }
+    int ex = 0;
+    frexpf(mx, &ex);
+    const float scale = mx > 0.f ? exp2f((float)-ex) : 1.f;
+#pragma unroll
+    for (int i = 0; i < LOOP_KPR; ++i) {
+      const int k = tid + i * FWD_THREADS;
+      if (k >= K) continue;
+      const float mag = wk[i] * sq[i] * scale;
+      float2 ck;
+      if (ik[i] > 0.f) {
+        const float inv = rsqrtf(ik[i]);
+        ck = make_float2(mag * th[i].x * inv, mag * th[i].y * inv);
+      } else {
+        ck = make_float2(mag, 0.f);   // arg(0) = 0
+      }
+      cl[k] = ck;
+      if (a.weighting) wl[k] = wk[i];
+      if (writer) {
+        if (a.weighting) a.w[k] = wk[i];
+        a.c[k] = ck;
+      }
+    }
+    if (writer && tid == 0) {
+      a.st->j = j0 + it + 1;
+      a.st->c_scale = scale;
+    }
+    __syncthreads();
+    // ---- inverse for the block's rows: U = (C on the grid) conj(Fyu) restricted to them
+    for (int i = tid; i < uy * ux; i += FWD_THREADS) {
+      const int k = gk[i];
+      cs[i] = k >= 0 ? cl[k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int i = tid; i < R * uxp; i += FWD_THREADS) {
+      const int r = i / uxp, ix = i - r * uxp;
+      float2 u = make_float2(0.f, 0.f);
+      if (ix < ux)
+        for (int iy = 0; iy < uy; ++iy) cmac_conj(u, fs[iy * R + r], cs[iy * ux + ix]);
+      us[i] = u;   // U[r][ix] = sum_iy C[iy][ix] conj(Fyu[iy][n0 + r])
+    }
+    // E'[r][j] = sum_ix U[g RT + r][ix] conj(Fxu[ix][t + 256 j]), quads through the ring
+    float2 acc[RT][FWD_MT];
+#pragma unroll
+    for (int r = 0; r < RT; ++r)
+#pragma unroll
+      for (int j = 0; j < FWD_MT; ++j) acc[r][j] = make_float2(0.f, 0.f);
+    for (int q = 0; q < nquad; ++q) {
+      cp_async_wait<FWD_STAGES - 2>();
+      __syncthreads();   // quad q landed for everyone (and, at q = 0, U is complete)
+      fwd_issue(ring, a.fxu, ux, nx, q + FWD_STAGES - 1, tid);
+      const float2* src = ring + (size_t)(q % FWD_STAGES) * FWD_SLOT;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float2 uv[RT];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+          const int row = g * RT + r;   // rows past R (the group's padding) stay zero
+          uv[r] = row < R ? us[row * uxp + 4 * q + c] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < FWD_MT; ++j) {
+          const float2 fv = src[(c * FWD_MT + j) * FWD_GROUP + t];
+#pragma unroll
+          for (int r = 0; r < RT; ++r) cmac_conj(acc[r][j], fv, uv[r]);   // U conj(Fxu)
+        }
+      }
+    }
+    // the next field E = A E'/|E'| (A at E' = 0); phi and the stored field when the
+    // loop may end here
+    const bool store = it == a.n_iter - 1 || thr_on;
+#pragma unroll
+    for (int r = 0; r < RT; ++r)
+#pragma unroll
+      for (int j = 0; j < FWD_MT; ++j) {
+        const float2 z = acc[r][j];
+        const float r2 = z.x * z.x + z.y * z.y;
+        const float sc = r2 > 0.f ? av[r][j] * rsqrtf(r2) : 0.f;
+        e[r][j] = r2 > 0.f ? make_float2(sc * z.x, sc * z.y) : make_float2(av[r][j], 0.f);
+        const int m = t + j * FWD_GROUP;
+        if (store && r < rows_g && m < nx) {
+          const size_t o = (size_t)(n0 + g * RT + r) * nx + m;
+          a.phi[o] = ofa_arg(z.y, z.x);   // arg(0) = 0
+          a.e32[o] = e[r][j];
+        }
+      }
+    // the next forward's first quads, once every thread is done with the ring
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < FWD_STAGES - 1; ++q) fwd_issue(ring, a.fxu, ux, nx, q, tid);
+  }
+  if (!s_ok && tid == 0) {
+    atomicOr(&a.st->err, OFA_ERRBIT_TIMEOUT);
+    a.st->done = 1;
+  }
+  cp_async_wait<0>();
 }
 
 size_t fwd_smem(int R, int ux, int uy) {
@@ -557,4 +977,74 @@ void launch_sep_inverse(const float2* c, const int* gridk, const float2* fxu, co
   dim3 grid((nx + INV_COLS - 1) / INV_COLS, (ny + INV_ROWS - 1) / INV_ROWS);
   launch_pdl(sep_inv_kernel, grid, INV_THREADS, sep_inv_smem(ux, uy), s, c, gridk, fxu, fyu, amp,
              nx, ny, ux, uy, phi, e32, done);
+}
+
+// ---------------------------------------------------------------- persistent loop host
+constexpr size_t SEP_LOOP_SMEM_LIMIT = 220 * 1024;
+
+bool sep_loop_shape(int nx, int ny, int ux, int uy, int K, int sms, size_t* smem, int* grid) {
+  const int R = sep_rows_per_block(ny, sms);
+  const int G = sep_fwd_blocks(ny, sms);
+  const size_t bytes = loop_layout(R, ux, uy).total;
+  if (!sep_fast_shape(nx, uy) || K > LOOP_KMAX || G > sms || bytes > SEP_LOOP_SMEM_LIMIT)
+    return false;
+  if (smem) *smem = bytes;
+  if (grid) *grid = G;
+  return true;
+}
+
+cudaError_t sep_loop_prepare(int ny, int sms, int* resident) {
+  cudaError_t e = cudaSuccess;
+  int per_sm = 0;
+  visit_rt(sep_rows_per_block(ny, sms), [&](auto rc) {
+    auto kern = sep_loop_kernel<decltype(rc)::value>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SEP_LOOP_SMEM_LIMIT);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FWD_THREADS,
+                                                        SEP_LOOP_SMEM_LIMIT);
+  });
+  if (resident) *resident = e == cudaSuccess ? per_sm : 0;
+  return e;
+}
+
+cudaError_t launch_sep_loop(ofa_plan* p, int n_iter, double threshold, cudaStream_t s) {
+  if (n_iter <= 0) return cudaSuccess;
+  constexpr int CHUNK = 1 << 20;   // a barrier counter reaches iterations x blocks
+  if (n_iter > CHUNK) {
+    for (int left = n_iter; left > 0; left -= CHUNK) {
+      cudaError_t e = launch_sep_loop(p, left < CHUNK ? left : CHUNK, threshold, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  size_t smem = 0;
+  int G = 0;
+  if (!sep_loop_shape(p->nx, p->ny, p->ux, p->uy, p->K, p->sm_count, &smem, &G))
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(p->loop_bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  SepLoopArgs a;
+  a.fxu = p->fxu; a.fyu = p->fyu; a.ixy = p->ixy; a.gridk = p->sep_gridk; a.amp = p->amp;
+  a.e32 = p->e32; a.phi = p->phi; a.part = p->part; a.theta = p->theta; a.c = p->c;
+  a.t = p->t; a.w = p->w; a.hist = p->hist; a.st = p->st; a.bar = p->loop_bar;
+  a.threshold = threshold;
+  a.nx = p->nx; a.ny = p->ny; a.ux = p->ux; a.uy = p->uy; a.K = p->K; a.kp = p->kp;
+  a.R = sep_rows_per_block(p->ny, p->sm_count);
+  a.weighting = p->weighting;
+  a.n_iter = n_iter;
+  visit_rt(a.R, [&](auto rc) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(FWD_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, sep_loop_kernel<decltype(rc)::value>, a);
+  });
+  return e;
 }

@@ -468,6 +468,7 @@ ofa_status ofa_options_default(ofa_options* o) {
   o->focus_z = nullptr;
   o->separable = -1;
   o->fused_loop = 0;
+  o->separable_loop = -1;
   return OFA_OK;
 }
 
@@ -521,6 +522,10 @@ ofa_status ofa_check_foci(int n_foci, const double* xy, double px, double py, do
 ofa_status ofa_plan_config(const ofa_plan* p, int* c) {
   if (!p || !c) return ofa_fail(nullptr, OFA_ERR_INVALID_ARG, "NULL argument");
   for (int i = 0; i < 12; ++i) c[i] = 0;
+  if (p->sep_loop) {
+    c[8] = 1; c[11] = p->sep_loop_grid;
+    return OFA_OK;
+  }
   if (!use_tc(p)) return OFA_OK;
   const TcOperands& t = p->tc;
   c[0] = t.fwd_bn; c[1] = t.fwd_split; c[2] = t.fwd_cg; c[3] = t.bwd_bn; c[4] = t.bwd_cg;
@@ -871,6 +876,21 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
                   sep_fwd_smem(ny, p->ux, p->uy, sm_count) <= limit &&
                   sep_inv_smem(p->ux, p->uy) <= limit && sep_prepare() == cudaSuccess;
     cudaGetLastError();
+    // the persistent loop: the shape fits, and one block per SM can be resident
+    if (opt.separable_loop != 0) {
+      int grid = 0, resident = 0;
+      const bool ok = p->sep_fast &&
+                      sep_loop_shape(nx, ny, p->ux, p->uy, n_foci, sm_count, nullptr, &grid) &&
+                      sep_loop_prepare(ny, sm_count, &resident) == cudaSuccess && resident >= 1;
+      cudaGetLastError();
+      if (!ok && opt.separable_loop == 1) {
+        p->last_error = "the separable loop needs the fast separable kernels, K <= 2560 and "
+                        "one pupil-row block per SM";
+        return fail(OFA_ERR_UNSUPPORTED);
+      }
+      p->sep_loop = ok;
+      p->sep_loop_grid = ok ? grid : 0;
+    }
   }
 
   // Small inputs.
@@ -1009,6 +1029,30 @@ ofa_status ofa_iterate(ofa_plan* p, int n_iter, double threshold, int* iters_don
     return ofa_fail(p, OFA_ERR_INVALID_ARG, "n_iter must be >= 0 and threshold finite");
   cudaSetDevice(p->device);
   const bool use_thr = threshold > 0.0 && threshold < 1.0;
+  if (p->sep_loop) {
+    // one persistent launch runs the n_iter iterations (and stops at the threshold)
+    launch_control(p->st, use_thr ? threshold : 0.0, 1, p->stream);
+    int j0 = -1;
+    const bool need_sync = iters_done || xi;
+    if (need_sync) {
+      ofa_status s = sync_and_check(p);
+      if (s != OFA_OK) return s;
+      j0 = p->st_host->j;
+    }
+    cudaError_t e = launch_sep_loop(p, n_iter, use_thr ? threshold : 0.0, p->stream);
+    if (e != cudaSuccess) return ofa_cuda_check(p, e, "launching the separable loop");
+    if (!need_sync && !use_thr) return OFA_OK;
+    ofa_status s = sync_and_check(p);
+    if (s != OFA_OK) return s;
+    if (iters_done) *iters_done = p->st_host->j - j0;
+    if (xi) {
+      enqueue_forward_current(p, p->stream);
+      s = sync_and_check(p);
+      if (s != OFA_OK) return s;
+      *xi = p->st_host->xi;
+    }
+    return OFA_OK;
+  }
   if (p->loop.ready) {
     // one persistent launch runs the n_iter iterations (and stops at the threshold)
     launch_control(p->st, use_thr ? threshold : 0.0, 1, p->stream);

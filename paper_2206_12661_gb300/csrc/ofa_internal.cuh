@@ -127,6 +127,8 @@ struct ofa_plan {
   float2* ones = nullptr;              // [uy] unit weights of the second inverse product
   int2* ixy = nullptr;                 // [K] (ix, iy) of each focus
   bool sep_fast = false;               // the three-launch separable iteration (k_sep.cu)
+  bool sep_loop = false;               // the separable form's persistent loop (k_sep.cu)
+  int sep_loop_grid = 0;               // its blocks
   int sm_count = 0;
   int* row_ptr = nullptr;              // [uy + 1] foci of each grid row ...
   int* row_foci = nullptr;             // [K] ... in increasing ix order
@@ -255,6 +257,13 @@ void launch_sep_sum_focal(const float2* part, int nb, int K, int kp, float2* the
 void launch_sep_inverse(const float2* c, const int* gridk, const float2* fxu, const float2* fyu,
                         const float* amp, int nx, int ny, int ux, int uy, float* phi,
                         float2* e32, const int* done, cudaStream_t s);
+// The persistent separable loop (K <= 2560): whether the shape fits (shared memory,
+// one block per SM for the forward's row blocks; grid and smem on output), the kernel
+// attributes and the blocks per SM that can be resident, and n_iter iterations in
+// cooperative launches on s (threshold as in ofa_iterate).
+bool sep_loop_shape(int nx, int ny, int ux, int uy, int K, int sms, size_t* smem, int* grid);
+cudaError_t sep_loop_prepare(int ny, int sms, int* resident);
+cudaError_t launch_sep_loop(ofa_plan* p, int n_iter, double threshold, cudaStream_t s);
 void launch_grad_simt(const float2* c, const float2* fxT, const float2* fyT, int nx, int ny, int K,
                       const float* phi, const float* amp, float amp_factor,
                       const OfaDevState* st, float* grad, const SimtWork& w, cudaStream_t s);

@@ -60,7 +60,8 @@ WORKLOADS = {"ragged333x250_300": ragged, "pupil1024_poisson1000":
              lambda: I.named("pupil1024_poisson1000"),
              "pupil1920x1152_grid2500": lambda: I.named("pupil1920x1152_grid2500"),
              "table1_grid9x9": lambda: I.named("table1_grid9x9"),
-             "table1_grid45x47": lambda: I.named("table1_grid45x47")}
+             "table1_grid45x47": lambda: I.named("table1_grid45x47"),
+             "table1_grid20x20": lambda: I.table1_workload(20, 20, seed=9)}
 
 
 @functools.lru_cache(maxsize=None)
@@ -166,9 +167,20 @@ def test_one_step_full_size(ofa, dev, prec, name):
 @pytest.mark.parametrize("name", ["table1_grid9x9", "table1_grid45x47"])
 def test_separable_one_step(ofa, dev, name, j):
     """The separable grid form (FP32): forward amplitudes and one iteration from the
-    oracle's iterate j, at the start and in the steep climb of xi (iteration 5)."""
+    oracle's iterate j, at the start and in the steep climb of xi (iteration 5), in the
+    plan's default execution (the persistent loop)."""
     cfg = check_plan(ofa, name, "fp32", j=j, separable=1)
-    assert cfg["fused_loop"] == 0
+    assert cfg["fused_loop"] == 1
+
+
+@pytest.mark.parametrize("loop", [0, 1])
+@pytest.mark.parametrize("name", ["table1_grid9x9", "table1_grid20x20", "table1_grid45x47"])
+def test_separable_loop_one_step(ofa, dev, name, loop):
+    """The separable form's persistent loop and its multi-launch form, one step from the
+    oracle's iterate 5, on grids with 1 to 15 foci per block in the loop's Theta sums and
+    1 to 5 per thread in its focal step (81, 400 and 2115 foci)."""
+    cfg = check_plan(ofa, name, "fp32", j=5, separable=1, separable_loop=loop)
+    assert cfg["fused_loop"] == loop
 
 
 @pytest.mark.parametrize("prec", ["f16x3", "tf32"])

@@ -667,6 +667,39 @@ def test_separable_plans_of_different_grids_coexist(ofa, dev):
     assert np.array_equal(h_alone, h_both), (h_alone, h_both)
 
 
+def test_separable_loop_agrees_with_launches_and_resumes(ofa, dev):
+    """The persistent separable loop against the two-launch iteration over the Table 1
+    9 x 9 replay (the same operator, associated differently: the loop's inverse sums
+    U conj(Fxu) with U = C conj(Fyu) over the block's rows, the launches conj(Fyu) T;
+    so the first xi agree to the 1e-5 the replay allows against FP64 and the history
+    to its 2e-3), bitwise resume across calls, and the threshold stop."""
+    w = I.named("table1_grid9x9")
+    hs = []
+    for loop in (1, 0):
+        plan = ofa.Plan.from_workload(w, precision="fp32", separable=1, separable_loop=loop)
+        assert ofa.ofa_plan_config(plan.handle)["fused_loop"] == loop
+        plan.iterate(w.n_iter)
+        hs.append(plan.xi_history())
+        plan.close()
+    assert np.max(np.abs(hs[0][:3] - hs[1][:3])) < 1e-5, hs
+    assert np.max(np.abs(hs[0] - hs[1])) < 2e-3, hs
+    # 10 iterations in one call and as 4 + 6: the same phase, bit for bit
+    phases = []
+    for parts in ((10,), (4, 6)):
+        plan = ofa.Plan.from_workload(w, precision="fp32", separable=1, separable_loop=1)
+        for n in parts:
+            plan.iterate(n)
+        phases.append(plan.phase())
+        plan.close()
+    assert np.array_equal(phases[0], phases[1])
+    # threshold: the loop stops after the first iteration whose xi exceeds it
+    plan = ofa.Plan.from_workload(w, precision="fp32", separable=1, separable_loop=1)
+    done, _ = plan.iterate(200, threshold=0.95, want_stats=True)
+    h = plan.xi_history()
+    plan.close()
+    assert done == len(h) - 1 and h[-1] > 0.95 and np.all(h[:-1] <= 0.95), (done, h)
+
+
 def test_separable_refused_for_3d(ofa, dev):
     w = I.named("table1_grid9x9")
     with pytest.raises(ofa.OfaError) as e:
