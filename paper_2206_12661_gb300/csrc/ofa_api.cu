@@ -1679,7 +1679,8 @@ ofa_status ofa_batch_iterate(ofa_batch* b, int n_iter) {
     for (int it = 0; it < n_iter; ++it) {
       if (b->tc) tc_batch_enqueue_iteration(b->tc, b->cap_stream);
       else
-        for (ofa_plan* p : b->plans) enqueue_iteration(p, b->cap_stream);
+        for (ofa_plan* p : b->plans)
+          if (!p->sep_loop && !p->loop.ready) enqueue_iteration(p, b->cap_stream);
     }
     e = cudaStreamEndCapture(b->cap_stream, &g);
     if (e != cudaSuccess) return ofa_fail(nullptr, OFA_ERR_CUDA, "batch capture end");
@@ -1691,6 +1692,14 @@ ofa_status ofa_batch_iterate(ofa_batch* b, int n_iter) {
   // The plans' own streams must see the batch's work in order.
   cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
   if (e != cudaSuccess) return ofa_fail(nullptr, OFA_ERR_CUDA, "batch graph launch");
+  // plans whose own iterations run as one persistent launch run it here too, so that a
+  // batch of plans run one after another gives each plan's own results bit for bit
+  if (!b->tc)
+    for (ofa_plan* p : b->plans) {
+      if (p->sep_loop) e = launch_sep_loop(p, n_iter, 0.0, b->stream);
+      else if (p->loop.ready) e = launch_loop(p, n_iter, 0.0, b->stream);
+      if (e != cudaSuccess) return ofa_fail(nullptr, OFA_ERR_CUDA, "batch persistent launch");
+    }
   return OFA_OK;
 }
 
