@@ -185,6 +185,32 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
   else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
+  // The B operand (Fx or conj(Fx) in block form, written once per plan) of the first
+  // stages is fetched before the wait for the previous kernel.  Its bytes are
+  // registered on the stage's full barrier without an arrival, so a stage cannot
+  // complete before its A tile (the previous kernel's output) is loaded and arrived for.
+  const int npre = nkb < C::STAGES ? nkb : C::STAGES;
+  if (warp == WARP_TMA && lane == 0) {
+    for (int kb = 0; kb < npre; ++kb) {
+      const uint32_t st = base_u32 + kb * C::STAGE_BYTES;
+      const int x = (kb0 + kb) * C::BK;
+      if (PAIR) {
+        if (leader) mbar_expect_tx_only(bar_full + 8 * kb, 2 * C::PLANES * C::B_BYTES);
+        const uint32_t fb =
+            leader ? bar_full + 8 * kb : mapa_shared(bar_full + 8 * kb, crank & ~1);
+        const int brow = n_tile * BN + (crank & 1) * (BN / 2);
+        tma_load_2d_pair(st + C::PLANES * C::A_BYTES, tmb_hi, fb, x, brow);
+        if (NPASS == 3)
+          tma_load_2d_pair(st + C::PLANES * C::A_BYTES + C::B_BYTES, tmb_lo, fb, x, brow);
+      } else {
+        mbar_expect_tx_only(bar_full + 8 * kb, C::PLANES * C::B_BYTES);
+        tma_load_2d(st + C::PLANES * C::A_BYTES, tmb_hi, bar_full + 8 * kb, x, n_tile * BN);
+        if (NPASS == 3)
+          tma_load_2d(st + C::PLANES * C::A_BYTES + C::B_BYTES, tmb_lo, bar_full + 8 * kb, x,
+                      n_tile * BN);
+      }
+    }
+  }
   // Everything above is independent of the previous kernel; from here on its
   // outputs (the dynamic operand, the loop flags) are read.
   pdl_wait();
@@ -192,7 +218,16 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
   const bool skip = (done != nullptr && *done) || (*ep.err & OFA_ERRBIT_TIMEOUT);
 
   if (skip) {
-    // nothing to compute; fall through to the teardown
+    // nothing to compute: the prefetched B copies must land before the CTA may leave
+    // (the odd CTA of a pair waits at the teardown's cluster barrier)
+    if (warp == WARP_TMA && lane == 0 && leader)
+      for (int kb = 0; kb < npre; ++kb) {
+        mbar_arrive(bar_full + 8 * kb);
+        if (!mbar_wait(bar_full + 8 * kb, 0)) {
+          atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
+          break;
+        }
+      }
   } else if (warp == WARP_TMA) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
@@ -208,25 +243,31 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
         }
         const uint32_t st = base_u32 + s * C::STAGE_BYTES;
         const int x = (kb0 + kb) * C::BK;
+        const bool pre = kb < npre;   // B already in flight (registered above)
         if (PAIR) {
           // both CTAs' halves land on the leader's barrier, which expects them all
-          if (leader) mbar_expect_tx(bar_full + 8 * s, 2 * C::STAGE_BYTES);
+          if (leader)
+            mbar_expect_tx(bar_full + 8 * s,
+                           pre ? 2 * C::PLANES * C::A_BYTES : 2 * C::STAGE_BYTES);
           const uint32_t fb = leader ? bar_full + 8 * s : mapa_shared(bar_full + 8 * s, crank & ~1);
           const int brow = n_tile * BN + (crank & 1) * (BN / 2);
           tma_load_2d_pair(st, tma_hi, fb, x, m_tile * BM);
-          tma_load_2d_pair(st + C::PLANES * C::A_BYTES, tmb_hi, fb, x, brow);
+          if (!pre) tma_load_2d_pair(st + C::PLANES * C::A_BYTES, tmb_hi, fb, x, brow);
           if (NPASS == 3) {
             tma_load_2d_pair(st + C::A_BYTES, tma_lo, fb, x, m_tile * BM);
-            tma_load_2d_pair(st + C::PLANES * C::A_BYTES + C::B_BYTES, tmb_lo, fb, x, brow);
+            if (!pre)
+              tma_load_2d_pair(st + C::PLANES * C::A_BYTES + C::B_BYTES, tmb_lo, fb, x, brow);
           }
         } else {
-          mbar_expect_tx(bar_full + 8 * s, C::STAGE_BYTES);
+          mbar_expect_tx(bar_full + 8 * s, pre ? C::PLANES * C::A_BYTES : C::STAGE_BYTES);
           tma_load_2d(st, tma_hi, bar_full + 8 * s, x, m_tile * BM);
-          tma_load_2d(st + C::PLANES * C::A_BYTES, tmb_hi, bar_full + 8 * s, x, n_tile * BN);
+          if (!pre)
+            tma_load_2d(st + C::PLANES * C::A_BYTES, tmb_hi, bar_full + 8 * s, x, n_tile * BN);
           if (NPASS == 3) {
             tma_load_2d(st + C::A_BYTES, tma_lo, bar_full + 8 * s, x, m_tile * BM);
-            tma_load_2d(st + C::PLANES * C::A_BYTES + C::B_BYTES, tmb_lo, bar_full + 8 * s, x,
-                        n_tile * BN);
+            if (!pre)
+              tma_load_2d(st + C::PLANES * C::A_BYTES + C::B_BYTES, tmb_lo, bar_full + 8 * s,
+                          x, n_tile * BN);
           }
         }
         ++issued;
