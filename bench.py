@@ -217,11 +217,12 @@ def bench_config(ofa, I, torch, stream, flush, name: str, precisions, reps: int 
 
 
 def bench_separable(ofa, I, torch, stream, flush, reps: int = 3) -> dict:
-    """Table 1 geometry (1000^2 pupil) with regular 9 x 9 and 45 x 47 grids: the
-    separable grid form (products through the distinct focus coordinates, FP32)
-    against the general tensor-core form (F16X3), iterations/s."""
+    """Table 1 geometry (1000^2 pupil) with regular 9 x 9 and 45 x 47 grids and the
+    paper's 66 random spots on a 45 x 47 sampling grid: the separable grid form
+    (products through the distinct focus coordinates, FP32) against the general
+    tensor-core form (F16X3), iterations/s."""
     out = {}
-    for name in ("table1_grid9x9", "table1_grid45x47"):
+    for name in ("table1_grid9x9", "table1_grid45x47", "table1_random66"):
         w = I.named(name)
         rec = {"n_foci": w.n_foci}
         for label, kw in (("separable_fp32", {"separable": 1, "precision": "fp32"}),

@@ -233,6 +233,47 @@ def table1_workload(cols: int = 9, rows: int = 9, n_iter: int = 40, seed: int = 
                     meta={"layout": "regular grid", "gap_m": gap, "seed": seed})
 
 
+def table1_random_workload(n_spots: int = 66, ux: int = 45, uy: int = 47, lattice: int = 61,
+                           step_px: int = 12, n_iter: int = 40, seed: int = 10,
+                           name: str | None = None) -> Workload:
+    """Table 1 geometry with the paper's second simulated OFA: n_spots foci at random
+    positions with random intensities U[0.5, 1], sampled on the camera grid (3.45 um
+    pixels) so that they take exactly ux distinct x and uy distinct y values (the
+    45 x 47 MTP sampling grid of the Fig. 2 discussion).  Positions are cells of a
+    lattice x lattice lattice of step_px camera pixels centred on the axis (12 px =
+    41 um, about 2.6 diffraction-limited spots of this pupil): ux columns and uy rows
+    are drawn, every row gets one spot in a column chosen so that every column is used,
+    and the remaining spots take distinct random free cells of those rows and columns."""
+    if not (max(ux, uy) <= n_spots <= ux * uy and ux <= lattice and uy <= lattice):
+        raise ValueError("need max(ux, uy) <= n_spots <= ux * uy within the lattice")
+    rng = np.random.default_rng(seed)
+    n, pitch, lam, f = 1000, 12.5e-6, 785e-9, 0.25
+    step = step_px * 3.45e-6
+    cols = np.sort(rng.choice(lattice, ux, replace=False))
+    rows = np.sort(rng.choice(lattice, uy, replace=False))
+    # one spot per row, covering every column, then distinct extra cells
+    if uy >= ux:
+        col_of_row = np.concatenate([rng.permutation(ux), rng.integers(0, ux, uy - ux)])
+        cells = {(int(r), int(c)) for r, c in zip(range(uy), rng.permutation(col_of_row))}
+    else:
+        row_of_col = np.concatenate([rng.permutation(uy), rng.integers(0, uy, ux - uy)])
+        cells = {(int(r), int(c)) for c, r in zip(range(ux), rng.permutation(row_of_col))}
+    while len(cells) < n_spots:
+        cells.add((int(rng.integers(uy)), int(rng.integers(ux))))
+    cells = sorted(cells)
+    centre = (lattice - 1) / 2.0
+    foci = np.array([[(cols[c] - centre) * step, (rows[r] - centre) * step] for r, c in cells])
+    t = rng.uniform(0.5, 1.0, n_spots)
+    return Workload(name=name or f"table1_random{n_spots}", nx=n, ny=n, pitch_x=pitch,
+                    pitch_y=pitch, wavelength=lam, focal_length=f,
+                    focus_xy=np.ascontiguousarray(foci, dtype=np.float64),
+                    target=np.ascontiguousarray(t, dtype=np.float32),
+                    amplitude=gaussian_amplitude(n, n, pitch, pitch),
+                    phi0=uniform_phase(rng, n, n), n_iter=n_iter,
+                    meta={"layout": "random cells of a camera-pixel lattice",
+                          "step_m": step, "distinct_x": ux, "distinct_y": uy, "seed": seed})
+
+
 def batch_workloads(count: int = 256, sizes=(512, 768, 1024), k_min: int = 16, k_max: int = 4096,
                     n_iter: int = 50, seed: int = 5) -> list[Workload]:
     """Uneven batch: N drawn from sizes, K log-uniform in [k_min, k_max], jittered grid foci."""
@@ -262,6 +303,8 @@ NAMED = {
     "table1_grid9x9": lambda: table1_workload(9, 9, n_iter=40, seed=7, name="table1_grid9x9"),
     "table1_grid45x47": lambda: table1_workload(45, 47, n_iter=40, seed=8,
                                                 name="table1_grid45x47"),
+    "table1_random66": lambda: table1_random_workload(66, 45, 47, n_iter=40, seed=10,
+                                                      name="table1_random66"),
     "pupil1024_grid400_adam": lambda: grid_workload(1024, 20, 20, n_iter=200, seed=4,
                                                     uniform_targets=False,
                                                     name="pupil1024_grid400_adam"),

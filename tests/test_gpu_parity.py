@@ -648,6 +648,30 @@ def test_separable_45x47_forward_and_gradient(ofa, dev):
     assert rel < 1e-4, rel
 
 
+@pytest.mark.parametrize("sep", [1, 0])
+def test_table1_random66_replay(ofa, dev, sep):
+    """The paper's second Table 1 OFA (66 random spots on a 45 x 47 sampling grid): the
+    separable form (FP32, forced) and the general form (F16X3, the default here) follow
+    the FP64 oracle's loop: the first xi to 1e-5, the history to 2e-3, the final xi to
+    1e-3 and the final uniformity to 2e-3 (the replay tolerances of the 9 x 9 OFA)."""
+    w = I.named("table1_random66")
+    fx, fy = oracle_mats(w)
+    ref = O.gsw(w.amplitude, w.phi0, fx, fy, w.target, w.n_iter)
+    plan = ofa.Plan.from_workload(w, precision="fp32" if sep else "f16x3", separable=sep)
+    form = ofa.ofa_plan_form(plan.handle)
+    it, xi = plan.iterate(w.n_iter, want_stats=True)
+    st = plan.stats()
+    hist = plan.xi_history()
+    plan.close()
+    if sep:
+        assert form == {"separable": True, "ux": 45, "uy": 47}
+    else:
+        assert form["separable"] is False
+    assert np.max(np.abs(hist[:3] - ref["xi_hist"][:3])) < 1e-5
+    assert np.max(np.abs(hist - ref["xi_hist"])) < 2e-3
+    assert abs(xi - ref["xi"]) < 1e-3 and abs(st.uniformity - ref["uniformity"]) < 2e-3
+
+
 def test_separable_plans_of_different_grids_coexist(ofa, dev):
     """A plan with a small grid created after one with a large grid leaves the large
     one's launches intact (kernel attributes are shared by every plan of a process):

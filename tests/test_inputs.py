@@ -93,3 +93,22 @@ def test_volume_layers_and_table1_grid():
     assert (t.nx, t.pitch_x, t.wavelength, t.focal_length) == (1000, 12.5e-6, 785e-9, 0.25)
     xs = np.unique(np.round(t.focus_xy[:, 0], 12))
     assert len(xs) == 9 and np.allclose(np.diff(xs), 20 * 3.45e-6)
+
+
+def test_table1_random66_recipe():
+    """The paper's second simulated OFA: 66 spots at random cells of a camera-pixel
+    lattice, with exactly 45 distinct x and 47 distinct y (its 45 x 47 MTP grid)."""
+    w = I.named("table1_random66")
+    step = 12 * 3.45e-6
+    assert w.n_foci == 66 and (w.nx, w.ny) == (1000, 1000)
+    xs = np.unique(np.round(w.focus_xy[:, 0], 12))
+    ys = np.unique(np.round(w.focus_xy[:, 1], 12))
+    assert (len(xs), len(ys)) == (45, 47)
+    # on the lattice (centred, 12-pixel step), no two spots in one cell
+    assert np.allclose(np.round(w.focus_xy / step * 2) / 2, w.focus_xy / step, atol=1e-9)
+    assert len({(round(x, 12), round(y, 12)) for x, y in w.focus_xy}) == 66
+    d = np.sqrt(((w.focus_xy[:, None] - w.focus_xy[None]) ** 2).sum(-1)) + np.eye(66)
+    assert d.min() >= step - 1e-12
+    assert alias_free(w)
+    assert np.all((w.target >= 0.5) & (w.target <= 1.0))
+    assert np.array_equal(w.focus_xy, I.named("table1_random66").focus_xy)
