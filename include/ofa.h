@@ -69,7 +69,12 @@ typedef struct ofa_options {
   void* cuda_stream;         /* cudaStream_t the plan runs on; NULL = a non-blocking stream the
                                 plan creates and owns */
   const float* amplitude;    /* [ny][nx] pupil amplitude A >= 0, or NULL for the default
-                                Gaussian exp(-(u^2/wx^2 + v^2/wy^2)), w = waist_frac * n * p */
+                                Gaussian exp(-(u^2/wx^2 + v^2/wy^2)), w = waist_frac * n * p.
+                                Checked on the device: a negative, infinite or NaN value, or
+                                A = 0 everywhere, fails creation with OFA_ERR_INVALID_ARG.
+                                The plan stores A 2^-e, the power of two e putting max A 2^-e
+                                in (1/2, 1], so amplitudes that differ by a power of two give
+                                the same phases bit for bit. */
   double waist_frac;         /* default 0.4 */
   const float* phi0;         /* [ny][nx] initial guess phi_0 (radians), or NULL for
                                 2*pi*(splitmix64 stream of seed >> 11)/2^53 - pi per pixel */
@@ -166,7 +171,8 @@ ofa_status ofa_options_default(ofa_options* opt);
  *                          loop uses I~ / sum I~), sum > 0
  *   opt                    NULL = defaults
  * Builds the DFT rows Fx[k][m] = exp(-i 2 pi x_k u_m / (lambda f)) and Fy likewise
- * (phase arguments reduced in FP64), sets E_0 = A exp(i phi_0), w_0 = 1, j = 0.
+ * (phase arguments reduced modulo one turn exactly, in 64-bit fixed point, before the
+ * FP32 sincos), sets E_0 = A exp(i phi_0), w_0 = 1, j = 0.
  * The plan owns every device buffer it allocates.  *out is NULL on failure.
  */
 ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, double pitch_y,
@@ -211,14 +217,15 @@ ofa_status ofa_get_phase(const ofa_plan* plan, float* phi_out, int out_mem_space
 
 /* Release every resource of the plan.  NULL-safe.  The plan's device buffers live
  * in one allocation; the library keeps the last one released on each device (the
- * larger, if it already holds one), and the pinned state mirror, for the next plan
- * of similar size to reuse, so a create/destroy loop allocates once.  ofa_trim
- * frees what is kept. */
+ * larger, if it already holds one), the pinned state mirror and up to eight idle
+ * streams for the next plan of similar size to reuse, so a create/destroy loop
+ * allocates once.  ofa_trim frees what is kept. */
 ofa_status ofa_destroy(ofa_plan* plan);
 
-/* Free the device and pinned host memory that destroyed plans left for reuse on the
- * current device (at most one plan arena and one state mirror).  Plans still alive
- * are not affected.  OFA_OK, or OFA_ERR_CUDA if a free fails. */
+/* Free the device memory, pinned host memory and streams that destroyed plans left
+ * for reuse on the current device (at most one plan arena, one state mirror and
+ * eight streams).  Plans still alive are not affected.  OFA_OK, or OFA_ERR_CUDA if a
+ * free fails. */
 ofa_status ofa_trim(void);
 
 /* Statistics of one forward at the current phase (runs that forward; host output). */

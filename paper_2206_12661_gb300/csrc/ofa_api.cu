@@ -15,9 +15,9 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
-#include "ofa_host.h"
 #include "ofa_internal.cuh"
 
 namespace {
@@ -61,9 +61,10 @@ cudaError_t dalloc(T** p, size_t count) {
 
 // Per-device reuse of what plan creation and destruction cost most on the host:
 // the device attributes, the kernels' shared-memory opt-in (once per precision),
-// one plan arena and one pinned state mirror.  A process that creates and
-// destroys plans in a loop then calls cudaMalloc / cudaMallocHost once; ofa_trim
-// releases the cached memory.
+// one plan arena, one pinned state mirror and a few idle streams.  A process that
+// creates and destroys plans in a loop then calls cudaMalloc / cudaMallocHost /
+// cudaStreamCreate once; ofa_trim releases what is cached.
+constexpr int OFA_CACHED_STREAMS = 8;
 struct DeviceCache {
   bool attrs = false;
   int cc = 0, sms = 0;
@@ -71,6 +72,8 @@ struct DeviceCache {
   void* arena = nullptr;
   size_t arena_bytes = 0;
   OfaDevState* st_host = nullptr;
+  cudaStream_t streams[OFA_CACHED_STREAMS] = {};
+  int n_streams = 0;
 };
 constexpr int OFA_MAX_DEVICES = 64;
 std::mutex g_cache_mu;
@@ -143,6 +146,33 @@ void give_back_arena(int dev, void* arena, size_t bytes) {
   if (drop) cudaFree(drop);
 }
 
+// An idle non-blocking stream of the device: a cached one, else a new one.
+cudaError_t take_stream(int dev, cudaStream_t* s) {
+  if (dev >= 0 && dev < OFA_MAX_DEVICES) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    DeviceCache& c = g_cache[dev];
+    if (c.n_streams > 0) {
+      *s = c.streams[--c.n_streams];
+      return cudaSuccess;
+    }
+  }
+  return cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+}
+
+// Keep a stream with no work pending for the next plan, or destroy it.
+void give_back_stream(int dev, cudaStream_t s) {
+  if (!s) return;
+  if (dev >= 0 && dev < OFA_MAX_DEVICES) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    DeviceCache& c = g_cache[dev];
+    if (c.n_streams < OFA_CACHED_STREAMS) {
+      c.streams[c.n_streams++] = s;
+      return;
+    }
+  }
+  cudaStreamDestroy(s);
+}
+
 OfaDevState* take_cached_st_host(int dev) {
   if (dev < 0 || dev >= OFA_MAX_DEVICES) return nullptr;
   std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -180,14 +210,12 @@ cudaError_t arena_commit(ofa_plan* p, const std::vector<ArenaReq>& reqs) {
   }
   p->arena = base;
   p->arena_bytes = bytes;
-  cudaError_t e = cudaSuccess;
   for (size_t i = 0; i < reqs.size(); ++i) {
     *reqs[i].slot = static_cast<uint8_t*>(base) + off[i];
     p->arena_slots.push_back(reqs[i].slot);
   }
-  e = cudaMemsetAsync(base, 0, total, p->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
-  return e;
+  // every later set-up copy and kernel runs on the plan's stream, after the fill
+  return cudaMemsetAsync(base, 0, total, p->stream);
 }
 
 void dfree(void* p) {
@@ -311,6 +339,8 @@ void enqueue_sep_forward(ofa_plan* p, const float2* e32, cudaStream_t s) {
   launch_sep_theta(p->gt, p->fyu, p->ixy, p->K, p->ny, p->ux, p->sep_parts, p->part, s);
 }
 
+// The iteration takes no amplitude statistic (the energy enters only the statistics
+// of mode 1), so plan creation captures it before the statistics are read back.
 void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
   const int* done = done_ptr(p);
   if (p->sep && p->sep_fast) {
@@ -324,7 +354,7 @@ void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
   } else if (p->sep) {
     enqueue_sep_forward(p, p->e32, s);
     launch_focal(p->part, 1, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist, p->st,
-                 0, p->weighting, 1.f, p->amp_energy, s);
+                 0, p->weighting, 1.f, 0.0, s);
     enqueue_sep_inverse(p, done, s);
   } else if (!use_tc(p)) {
     const FocalTail f = {p->t, p->w, p->c, p->hist, p->st, p->weighting, nullptr, 1};
@@ -332,7 +362,7 @@ void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
                     &f);
     if (!simt_fwd_fuses_focal(p->K))
       launch_focal(p->part, simt_fwd_tiles(p->ny), p->kp, p->K, p->t, p->w, p->theta, p->inten,
-                   p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
+                   p->c, p->hist, p->st, 0, p->weighting, 1.f, 0.0, s);
     launch_bwd_simt(p->c, p->simt.fxT, p->simt.fyT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
                     done, p->simt, s);
   } else {
@@ -341,7 +371,7 @@ void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
     launch_fwd_tc(p, p->tc, done, s, fuse);
     if (!fuse)
       launch_focal(p->part, fwd_n_part(p->nyp, p->tc), p->kp, p->K, p->t, p->w, p->theta,
-                   p->inten, p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
+                   p->inten, p->c, p->hist, p->st, 0, p->weighting, 1.f, 0.0, s);
     launch_build_p(p->fyT, p->c, done, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
     launch_bwd_tc(p, p->tc, done, s);
   }
@@ -578,8 +608,8 @@ ofa_status ofa_destroy(ofa_plan* p) {
     dfree(p->tc_aux.e_hi);
     dfree(p->tc_aux.e_lo);
   }
-  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  give_back_stream(p->device, p->cap_stream);
+  if (p->own_stream) give_back_stream(p->device, p->stream);
   if (prev >= 0) cudaSetDevice(prev);
   delete p;
   return OFA_OK;
@@ -703,24 +733,40 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   // Fyu E Fxu^T), costing nx ny (ux + uy) complex products instead of 2 nx ny K.
   std::vector<double> xs, ys;
   if (opt.separable != 0 && !opt.focus_z && !shard) {
-    for (int k = 0; k < n_foci; ++k) {
-      xs.push_back(xy[2 * k]);
-      ys.push_back(xy[2 * k + 1]);
-    }
-    std::sort(xs.begin(), xs.end());
-    xs.erase(std::unique(xs.begin(), xs.end()), xs.end());
-    std::sort(ys.begin(), ys.end());
-    ys.erase(std::unique(ys.begin(), ys.end()), ys.end());
-    const double c_sep = (double)nx * ny * ((double)xs.size() + (double)ys.size()) +
-                         (double)n_foci * (nx + ny);
-    const double c_gen = 2.0 * nx * ny * (double)round_up(n_foci, 128);
-    // the grid form runs on the CUDA cores: against a tensor-core form it must save
-    // about twenty times the work to be faster (measured: 1000^2 pupil, 9 x 9 grid
-    // 23 k vs 42 k it/s, 45 x 47 grid 17 k vs 11.5 k it/s)
+    // The grid form runs on the CUDA cores: by default it is taken where its work,
+    // nx ny (U_x + U_y) + K (nx + ny), is under 1/20 of the tensor-core forms'
+    // 2 nx ny K_p (1/2 of the FP32 form's), where it was always the faster in
+    // measurements (1000^2 pupil, 45 x 47 grid: 22 k vs 11 k it/s).  Smaller savings
+    // can win too (9 x 9 grid, 14x less work: 60 k vs 41 k it/s): separable = 1.
+    // The distinct values are counted only up to the bound this puts on U_x + U_y,
+    // so a plan of scattered foci stops early.
+    const double npix_d = (double)nx * ny;
+    const double c_gen = 2.0 * npix_d * (double)round_up(n_foci, 128);
     const double gain = prec_is_tc(opt.precision) ? 20.0 : 2.0;
-    p->sep = opt.separable == 1 || c_sep * gain < c_gen;
-    p->ux = (int)xs.size();
-    p->uy = (int)ys.size();
+    const double bound = (c_gen / gain - (double)n_foci * (nx + ny)) / npix_d;
+    const size_t limit = opt.separable == 1 ? (size_t)n_foci
+                         : bound < 1.0 ? 0 : (size_t)std::min(bound, (double)n_foci);
+    auto distinct = [&](int c, size_t lim, std::vector<double>& out) {
+      std::unordered_set<double> seen;  // -0.0 == 0.0: one value
+      seen.reserve(std::min((size_t)n_foci, lim + 1));
+      for (int k = 0; k < n_foci; ++k) {
+        seen.insert(xy[2 * (size_t)k + c]);
+        if (seen.size() > lim) return false;
+      }
+      out.assign(seen.begin(), seen.end());
+      std::sort(out.begin(), out.end());
+      return true;
+    };
+    bool fits = distinct(0, limit, xs);
+    if (fits) fits = distinct(1, opt.separable == 1 ? limit : limit - xs.size(), ys);
+    if (fits && opt.separable != 1) {
+      const double c_sep = npix_d * ((double)xs.size() + (double)ys.size()) +
+                           (double)n_foci * (nx + ny);
+      fits = c_sep * gain < c_gen;
+    }
+    p->sep = fits;
+    p->ux = fits ? (int)xs.size() : 0;
+    p->uy = fits ? (int)ys.size() : 0;
   }
   if (opt.separable == 1 && !p->sep) {
     delete p;
@@ -747,11 +793,10 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   if (opt.cuda_stream) {
     p->stream = static_cast<cudaStream_t>(opt.cuda_stream);
   } else {
-    OFA_TRY(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking), "creating stream");
+    OFA_TRY(take_stream(dev, &p->stream), "creating stream");
     p->own_stream = true;
   }
-  OFA_TRY(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking),
-          "creating capture stream");
+  OFA_TRY(take_stream(dev, &p->cap_stream), "creating capture stream");
 
   const bool tc = use_tc(p);
   const int n_part_max = tc ? (p->nyp / 128) * 8
@@ -778,6 +823,8 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     R(dalloc(&p->counters, p->kp / 64 + 1));
     R(dalloc(&p->loop_bar, 4));
     R(dalloc(&p->meas, n_foci));
+    R(dalloc(&p->amp_part, 3 * (size_t)AMP_STAT_BLOCKS));
+    R(dalloc(&p->amp_count, 1));
     if (p->sep) {
       R(dalloc(&p->fxu, (size_t)p->ux * nx));
       R(dalloc(&p->fyu, (size_t)p->uy * ny));
@@ -844,21 +891,20 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     for (int i = 0; i < p->ux; ++i) ux2[2 * i] = xs[i];
     for (int i = 0; i < p->uy; ++i) uy2[2 * i + 1] = ys[i];
     double* dcoord = p->sep_coord;
-    cudaError_t ce = cudaMemcpy(dcoord, ux2.data(), ux2.size() * 8, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess)
-      ce = cudaMemcpy(dcoord + ux2.size(), uy2.data(), uy2.size() * 8, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess)
-      ce = cudaMemcpy(p->ixy, ixy.data(), ixy.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess)
-      ce = cudaMemcpy(p->row_ptr, count.data(), count.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess)
-      ce = cudaMemcpy(p->row_foci, order.data(), order.size() * sizeof(int),
-                      cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess)
-      ce = cudaMemcpy(p->ones, ones.data(), ones.size() * sizeof(float2), cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess)
-      ce = cudaMemcpy(p->sep_gridk, gridk.data(), gridk.size() * sizeof(int),
-                      cudaMemcpyHostToDevice);
+    // stream-ordered copies; the synchronisation below keeps the host vectors alive
+    // until they are consumed
+    cudaError_t ce = cudaSuccess;
+    auto h2d = [&](void* dst, const void* src, size_t bytes) {
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, p->stream);
+    };
+    h2d(dcoord, ux2.data(), ux2.size() * sizeof(double));
+    h2d(dcoord + ux2.size(), uy2.data(), uy2.size() * sizeof(double));
+    h2d(p->ixy, ixy.data(), ixy.size() * sizeof(int2));
+    h2d(p->row_ptr, count.data(), count.size() * sizeof(int));
+    h2d(p->row_foci, order.data(), order.size() * sizeof(int));
+    h2d(p->ones, ones.data(), ones.size() * sizeof(float2));
+    h2d(p->sep_gridk, gridk.data(), gridk.size() * sizeof(int));
     if (ce == cudaSuccess) {
       const double lf = wavelength * focal_length;
       launch_dft_rows(dcoord, nullptr, 0, p->ux, nx, pitch_x, 0.5 * (nx - 1), lf, lf * focal_length,
@@ -893,17 +939,22 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     }
   }
 
-  // Small inputs.
+  // Small inputs: stream-ordered copies from host vectors that live until the
+  // synchronisation at the end of set-up.
   std::vector<float> tn(n_foci), ones(n_foci, 1.f);
   for (int k = 0; k < n_foci; ++k) tn[k] = (float)(tgt[k] / tsum);
-  OFA_TRY(cudaMemcpy(p->focus_xy, xy.data(), xy.size() * sizeof(double), cudaMemcpyHostToDevice),
+  OFA_TRY(cudaMemcpyAsync(p->focus_xy, xy.data(), xy.size() * sizeof(double),
+                          cudaMemcpyHostToDevice, p->stream),
           "copy foci");
   if (opt.focus_z)
-    OFA_TRY(cudaMemcpy(p->focus_z, zz.data(), zz.size() * sizeof(double), cudaMemcpyHostToDevice),
+    OFA_TRY(cudaMemcpyAsync(p->focus_z, zz.data(), zz.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, p->stream),
             "copy axial offsets");
-  OFA_TRY(cudaMemcpy(p->t, tn.data(), tn.size() * sizeof(float), cudaMemcpyHostToDevice),
+  OFA_TRY(cudaMemcpyAsync(p->t, tn.data(), tn.size() * sizeof(float), cudaMemcpyHostToDevice,
+                          p->stream),
           "copy targets");
-  OFA_TRY(cudaMemcpy(p->w, ones.data(), ones.size() * sizeof(float), cudaMemcpyHostToDevice),
+  OFA_TRY(cudaMemcpyAsync(p->w, ones.data(), ones.size() * sizeof(float),
+                          cudaMemcpyHostToDevice, p->stream),
           "init weights");
 
   // Amplitude: copy or default, then scale by a power of two to max in (1/2, 1].
@@ -915,31 +966,10 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     launch_default_amplitude(p->amp, nx, ny, row0, ny_total, pitch_x, pitch_y, opt.waist_frac,
                              p->stream);
   }
-  std::vector<float> ah;
-  const float* av = opt.amplitude;
-  if (!opt.amplitude || opt.mem_space == OFA_MEM_DEVICE) {
-    ah.resize(npix);
-    OFA_TRY(cudaMemcpyAsync(ah.data(), p->amp, npix * sizeof(float), cudaMemcpyDeviceToHost,
-                            p->stream),
-            "read amplitude");
-    OFA_TRY(cudaStreamSynchronize(p->stream), "sync");
-    av = ah.data();
-  }
-  double amax = 0.0, energy = 0.0;
-  if (!ofa_host::amplitude_stats(av, npix, &amax, &energy)) {
-    p->last_error = "amplitude must be finite and >= 0";
-    return fail(OFA_ERR_INVALID_ARG);
-  }
-  if (!(amax > 0.0)) {
-    p->last_error = "amplitude is zero everywhere";
-    return fail(OFA_ERR_INVALID_ARG);
-  }
-  int ex = 0;
-  std::frexp(amax, &ex);           // amax = f 2^ex, f in [1/2, 1)
-  if (amax == std::ldexp(1.0, ex - 1)) ex -= 1;  // exact power of two stays at 1
-  p->amp_exp = ex;
-  p->amp_energy = energy;
-  if (ex != 0) launch_scale(p->amp, npix, std::ldexp(1.0f, -ex), p->stream);
+  // its peak, energy and validity are reduced on the device and read back with the
+  // state mirror at the end of set-up; the scale by 2^-amp_exp follows on the stream
+  launch_amp_stats(p->amp, npix, p->amp_part, p->amp_count, p->st, p->stream);
+  launch_scale_pow2(p->amp, npix, p->st, p->stream);
 
   if (opt.phi0) {
     OFA_TRY(cudaMemcpyAsync(p->phi, opt.phi0, npix * sizeof(float), kind_from(opt.mem_space),
@@ -981,7 +1011,6 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
       p->tc.fwd_bn = kc[0]; p->tc.fwd_split = kc[1]; p->tc.fwd_cg = kc[2];
       p->tc.bwd_bn = kc[3]; p->tc.bwd_cg = kc[4];
     } else if (opt.autotune) {
-      OFA_TRY(cudaStreamSynchronize(p->stream), "plan set-up");
       if (!tc_autotune(p, p->tc, err)) {
         p->last_error = err;
         return fail(OFA_ERR_CUDA);
@@ -1016,7 +1045,27 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   launch_set_j(p->st, 0, 1, p->stream);
   launch_control(p->st, 0.0, 1, p->stream);
   OFA_TRY(cudaGetLastError(), "launching set-up kernels");
-  OFA_TRY(cudaStreamSynchronize(p->stream), "plan set-up");
+  // the iteration graphs are captured on the host while the set-up runs on the device
+  if (!p->loop.ready && !p->sep_loop) {
+    ofa_status gs = build_graph(p, p->chunk_iters, &p->chunk_exec);
+    if (gs == OFA_OK) gs = build_graph(p, 1, &p->one_exec);
+    if (gs != OFA_OK) return fail(gs);
+  }
+  {
+    const ofa_status ss = sync_and_check(p);
+    if (ss != OFA_OK) return fail(ss);
+  }
+  const OfaDevState& sh = *p->st_host;
+  if (sh.amp_bad) {
+    p->last_error = "amplitude must be finite and >= 0";
+    return fail(OFA_ERR_INVALID_ARG);
+  }
+  if (!(sh.amp_max > 0.0)) {
+    p->last_error = "amplitude is zero everywhere";
+    return fail(OFA_ERR_INVALID_ARG);
+  }
+  p->amp_exp = sh.amp_exp;
+  p->amp_energy = sh.amp_energy;
   g_fault_alloc_countdown = 0;
 #undef OFA_TRY
   *out = p;
@@ -1621,17 +1670,27 @@ ofa_status ofa_trim(void) {
   if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "cudaGetDevice");
   void* arena = nullptr;
   OfaDevState* h = nullptr;
+  cudaStream_t streams[OFA_CACHED_STREAMS];
+  int n_streams = 0;
   if (dev >= 0 && dev < OFA_MAX_DEVICES) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
-    arena = g_cache[dev].arena;
-    h = g_cache[dev].st_host;
-    g_cache[dev].arena = nullptr;
-    g_cache[dev].arena_bytes = 0;
-    g_cache[dev].st_host = nullptr;
+    DeviceCache& c = g_cache[dev];
+    arena = c.arena;
+    h = c.st_host;
+    c.arena = nullptr;
+    c.arena_bytes = 0;
+    c.st_host = nullptr;
+    n_streams = c.n_streams;
+    for (int i = 0; i < n_streams; ++i) streams[i] = c.streams[i];
+    c.n_streams = 0;
   }
   if (arena) e = cudaFree(arena);
   if (h) {
     const cudaError_t e2 = cudaFreeHost(h);
+    if (e == cudaSuccess) e = e2;
+  }
+  for (int i = 0; i < n_streams; ++i) {
+    const cudaError_t e2 = cudaStreamDestroy(streams[i]);
     if (e == cudaSuccess) e = e2;
   }
   if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "releasing cached memory");

@@ -44,6 +44,10 @@ struct OfaDevState {
   float c_scale;      // power-of-two factor applied to c this iteration
   float adam_step_size;   // lr / (1 - b1^t) of the latest ofa_adam_step
   float adam_bc2_sqrt;    // sqrt(1 - b2^t) of the latest ofa_adam_step
+  int amp_exp;            // plan set-up: the amplitude is stored scaled by 2^-amp_exp
+  double amp_max;         // plan set-up: peak and energy of the amplitude as given
+  double amp_energy;
+  int amp_bad;            // plan set-up: a value was negative, infinite or NaN
   int pad_;
 };
 
@@ -148,6 +152,8 @@ struct ofa_plan {
   size_t arena_bytes = 0;
   std::vector<void**> arena_slots;     // the pointers carved out of it
   double* sep_coord = nullptr;         // separable form: distinct coordinates (set-up)
+  double* amp_part = nullptr;          // [3 AMP_STAT_BLOCKS] amplitude statistics (set-up)
+  unsigned* amp_count = nullptr;       // their arrival counter
 
   std::string last_error;
 };
@@ -159,7 +165,8 @@ void ofa_set_thread_error(const std::string& msg);
 
 // ---------------------------------------------------------------- kernels (k_gen.cu)
 // origin: index of the optical axis along the sampled coordinate ((n - 1) / 2 for a
-// whole pupil; a row shard passes the whole pupil's axis relative to its first row).
+// whole pupil; a row shard passes the whole pupil's axis relative to its first row);
+// 2 origin must be an integer.
 void launch_dft_rows(const double* focus_xy, const double* focus_z, int coord, int K, int n,
                      double pitch, double origin, double lam_f, double lam_f2, float2* out,
                      cudaStream_t s);
@@ -167,7 +174,13 @@ void launch_dft_rows(const double* focus_xy, const double* focus_z, int coord, i
 void launch_default_amplitude(float* amp, int nx, int ny, int row0, int ny_total, double px,
                               double py, double waist_frac, cudaStream_t s);
 void launch_default_phase(float* phi, int nx, int ny, int row0, uint64_t seed, cudaStream_t s);
-void launch_scale(float* x, size_t n, float f, cudaStream_t s);
+// Amplitude statistics of plan set-up: peak, energy, validity and the power-of-two
+// exponent of the peak into st (amp_*); part holds 3 AMP_STAT_BLOCKS doubles, count
+// one zeroed word (left zero).  launch_scale_pow2 then scales by 2^-amp_exp.
+constexpr int AMP_STAT_BLOCKS = 1024;
+void launch_amp_stats(const float* amp, size_t n, double* part, unsigned* count,
+                      OfaDevState* st, cudaStream_t s);
+void launch_scale_pow2(float* x, size_t n, const OfaDevState* st, cudaStream_t s);
 // dst [nyp][kp] = src [K][ny] transposed (conjugated when conj), zero padded
 void launch_transpose_fy(const float2* fy, int K, int ny, int kp, int nyp, float2* fyT,
                          cudaStream_t s, bool conj = false);

@@ -444,6 +444,70 @@ def test_create_errors_on_gpu(ofa, dev):
     assert e.value.status == ofa.OFA_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("bad", [-1e-30, -1.0, np.nan, np.inf, -np.inf])
+@pytest.mark.parametrize("where", [0, 40001, 300 * 260 - 1])
+def test_amplitude_checked_on_device(ofa, dev, bad, where):
+    """A negative, infinite or NaN amplitude value anywhere in the pupil (first pixel,
+    one inside, last pixel of a pupil larger than the statistics grid) fails creation."""
+    nx, ny = 300, 260
+    a = np.ones((ny, nx), np.float32)
+    a.flat[where] = bad
+    with pytest.raises(ofa.OfaError) as e:
+        ofa.Plan(nx, ny, 8e-6, 8e-6, 532e-9, 0.2, np.zeros((1, 2)), np.ones(1), amplitude=a)
+    assert e.value.status == ofa.OFA_ERR_INVALID_ARG
+    assert "finite" in str(e.value)
+
+
+def test_amplitude_edge_values_accepted(ofa, dev):
+    """-0.0 is a valid amplitude and the largest FP32 value scales without overflow."""
+    nx, ny = 300, 260
+    a = np.full((ny, nx), np.finfo(np.float32).max, np.float32)
+    a[0, 0] = -0.0
+    p = ofa.Plan(nx, ny, 8e-6, 8e-6, 532e-9, 0.2, np.array([[1e-3, -2e-3]]), np.ones(1),
+                 amplitude=a, precision="fp32")
+    p.iterate(2)
+    assert np.all(np.isfinite(p.phase()))
+    p.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_power_of_two_amplitude_scale_is_bitwise(ofa, dev, prec):
+    """Algorithm 1 does not depend on the amplitude's scale (Theta scales with A, the
+    weights see normalised intensities, the phase is an argument).  The plan stores A
+    divided by a power of two putting its peak in (1/2, 1], so 2^e A gives the very
+    same phases and statistics, for a subnormal peak (e = -140) and one near the FP32
+    maximum (e = 100) too.  A sits on a 2^-8 lattice, exact at every scale used."""
+    w = custom(64, 48, 20, seed=9, targets="random")
+    A = (np.round(w.amplitude.astype(np.float64) * 256) / 256).astype(np.float32)
+    runs = []
+    for e in (0, -140, 100):
+        a = (A.astype(np.float64) * 2.0 ** e).astype(np.float32)
+        assert np.array_equal(a.astype(np.float64) * 2.0 ** -e, A.astype(np.float64))
+        p = ofa.Plan(w.nx, w.ny, w.pitch_x, w.pitch_y, w.wavelength, w.focal_length,
+                     w.focus_xy, w.target, precision=prec, amplitude=a, phi0=w.phi0)
+        p.iterate(4)
+        st = p.stats()
+        runs.append((p.phase(), st.xi, st.energy_fraction))
+        p.close()
+    for phi, xi, ef in runs[1:]:
+        assert np.array_equal(phi, runs[0][0])
+        assert xi == runs[0][1] and ef == runs[0][2]
+
+
+def test_energy_fraction_is_the_parseval_share(ofa, dev):
+    """energy_fraction = sum_k |Theta_k|^2 / (nx ny sum A^2), the pupil energy's share
+    at the foci (Parseval), against the oracle's forward at the initial phase."""
+    w = custom(300, 260, 41, seed=3, targets="random")
+    p = ofa.Plan.from_workload(w, precision="fp32")
+    st = p.stats()
+    p.close()
+    fx, fy = oracle_mats(w)
+    ref = O.forward(O.pupil_field(w.amplitude, w.phi0), fx, fy)
+    A = w.amplitude.astype(np.float64)
+    share = float(np.sum(np.abs(ref) ** 2) / (w.nx * w.ny * np.sum(A * A)))
+    assert st.energy_fraction == pytest.approx(share, rel=1e-5)
+
+
 def run_batch(ofa, ws, prec, n_iter, autotune=False):
     plans = [ofa.Plan.from_workload(w, precision=prec, autotune=autotune) for w in ws]
     stream = torch.cuda.Stream()
