@@ -219,13 +219,16 @@ def bench_config(ofa, I, torch, stream, flush, name: str, precisions, reps: int 
 def bench_separable(ofa, I, torch, stream, flush, reps: int = 3) -> dict:
     """Table 1 geometry (1000^2 pupil) with regular 9 x 9 and 45 x 47 grids and the
     paper's 66 random spots on a 45 x 47 sampling grid: the separable grid form
-    (products through the distinct focus coordinates, FP32) against the general
-    tensor-core form (F16X3), iterations/s."""
+    (products through the distinct focus coordinates) with FP32 products on the CUDA
+    cores and with F16X3 products on the tensor cores, against the general tensor-core
+    form (F16X3), iterations/s."""
     out = {}
     for name in ("table1_grid9x9", "table1_grid45x47", "table1_random66"):
         w = I.named(name)
         rec = {"n_foci": w.n_foci}
         for label, kw in (("separable_fp32", {"separable": 1, "precision": "fp32"}),
+                          ("separable_f16x3_tc", {"separable": 1, "precision": "f16x3",
+                                                  "separable_tc": 1}),
                           ("general_f16x3", {"separable": 0, "precision": "f16x3"})):
             with torch.cuda.stream(stream):
                 p = ofa.Plan.from_workload(w, stream=stream.cuda_stream, **kw)

@@ -141,6 +141,17 @@ typedef struct ofa_options {
                                 iteration from CUDA graphs), 1 = always (OFA_ERR_UNSUPPORTED
                                 if it cannot run).  ofa_plan_config reports it as the fused
                                 loop. */
+  int separable_tc;          /* separable form with a tensor-core precision, U_x, U_y <= 128,
+                                K <= 4096 and at most one focus per grid point: run the
+                                iteration's products on the tensor cores in the plan's
+                                precision -- G = E Fx_u^T per contraction part, Theta from G,
+                                the focal step with U = conj(Fy_u)^T C, then the inverse
+                                E' = U conj(Fx_u) --
+                                instead of FP32 on the CUDA cores (the persistent loop is
+                                then not used).  -1 = when U_x + U_y > 48 (default), 0 = never,
+                                1 = always (OFA_ERR_UNSUPPORTED if it cannot run).  Statistics,
+                                ofa_forward and the gradient entry points keep the FP32
+                                products.  ofa_plan_config reports its tile configuration. */
 } ofa_options;
 
 typedef struct ofa_stats {
@@ -327,7 +338,9 @@ ofa_status ofa_adam_step(ofa_plan* plan, float* phi, const float* grad_phi, floa
  *   ms_out[2] inverse left-operand build (P = conj(Fy)^T diag(c): the split operand
  *   planes of the tensor-core forms, the FP32 conj(Fy)^T c of OFA_PREC_FP32; the
  *   separable form's first inverse product), ms_out[3] inverse product (+ phase
- *   projection).
+ *   projection).  The separable form on the tensor cores reports its forward product
+ *   with the Theta sums in ms_out[0] and its focal step with U in ms_out[2] (0 in
+ *   ms_out[1]).
  * The loop state (phi, w, j, xi history) is saved before and restored after, so
  * the call does not change the result of later iterations.  Synchronises.
  */
@@ -355,7 +368,8 @@ ofa_status ofa_profile_loop(ofa_plan* plan, int n_iter, int reps, double* ms_per
  * step runs in the forward kernel's last CTA, forward and inverse operand row width per
  * pipeline stage (bytes of K); then the fused loop: 1 if ofa_iterate runs it, its CTA
  * group, its forward split and its CTAs per launch.  The FP32 and separable forms report
- * zeros. */
+ * zeros, except the separable form on the tensor cores (ofa_options.separable_tc), which
+ * reports its tiles, and the separable persistent loop, reported as the fused loop. */
 ofa_status ofa_plan_config(const ofa_plan* plan, int* config_out);
 
 /* Form of a plan: *separable = 1 with the U_x and U_y distinct focus coordinates it

@@ -672,6 +672,212 @@ void launch_adam(float* x, const float* g, float* m, float* v, int* step, OfaDev
   }
 }
 
+namespace {
+
+// Separable grid form on the tensor cores: the focal step of the loop and the inverse's
+// left operand in one launch.  Every block runs the focal step on Theta (the same
+// fixed-order reductions over the same inputs, so every block holds the same bits; the
+// weights are read from wprev, a copy taken before this launch, because block 0 alone
+// writes the new w, c, the xi history and the loop state), places c_k at the grid
+// point of focus k in shared memory (C, zero where no focus sits), and forms
+// U[n][ix] = sum over the grid rows iy (in order) of conj(Fyu[iy][n]) C[iy][ix] for its
+// eight rows n (one per warp; lane + 32 r = column ix, ux <= 128) into the operand
+// planes [nyp][2 kpad] (columns ix >= ux and rows n >= ny are never written and stay
+// zero).  The focal arithmetic is that of ofa_focal::iterate_regs.
+constexpr int SEP_U_THREADS = 256, SEP_U_ROWS = 8, SEP_U_MAXY = 128;
+constexpr size_t SEP_U_SMEM_MAX = 96 * 1024;   // the C grid, [uy][pitch] complex
+template <int KPR>
+__global__ void __launch_bounds__(SEP_U_THREADS) sep_focal_u_kernel(
+    const float2* __restrict__ theta, const float* __restrict__ t,
+    const float* __restrict__ wprev, float* __restrict__ w, float2* __restrict__ c,
+    double* __restrict__ hist, OfaDevState* __restrict__ st, int weighting,
+    const int2* __restrict__ ixy, int K, const float2* __restrict__ fyu,
+    const int* __restrict__ done, int ny, int ux, int uy, int pitch, int kpad, int prec,
+    void* hi, void* lo) {
+  constexpr int NT = SEP_U_THREADS;
+  extern __shared__ float2 cg[];                  // [uy][pitch]
+  __shared__ float2 fy[SEP_U_MAXY][SEP_U_ROWS];   // conj(Fyu) of the block's rows
+  __shared__ float sh[4 * 33 + 4];
+  __shared__ int skip;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n0 = blockIdx.x * SEP_U_ROWS;
+  const bool writer = blockIdx.x == 0;
+  // what does not change over the loop, before the wait: the block's conj(Fyu), the
+  // focus positions and targets, and the zero grid
+  for (int e = tid; e < uy * SEP_U_ROWS; e += NT) {
+    const int i = e / SEP_U_ROWS, r = e % SEP_U_ROWS, n = n0 + r;
+    float2 v = make_float2(0.f, 0.f);
+    if (n < ny) {
+      const float2 f = __ldg(fyu + (size_t)i * ny + n);
+      v = make_float2(f.x, -f.y);
+    }
+    fy[i][r] = v;
+  }
+  int2 q[KPR];
+  float tk[KPR];
+  bool in[KPR];
+#pragma unroll
+  for (int i = 0; i < KPR; ++i) {
+    const int k = tid + i * NT;
+    in[i] = k < K;
+    q[i] = in[i] ? __ldg(ixy + k) : make_int2(0, 0);
+    tk[i] = in[i] ? __ldg(t + k) : 0.f;
+  }
+  for (int e = tid; e < uy * pitch; e += NT) cg[e] = make_float2(0.f, 0.f);
+  // programmatic dependent launch: schedule the inverse product now, then wait for
+  // Theta and the weights' copy
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (tid == 0) skip = done != nullptr && __ldcg(done);   // one decision per block
+  __syncthreads();
+  if (skip) return;
+  const double thr = st->threshold;
+  float2 th[KPR];
+  float wk[KPR], ik[KPR];
+#pragma unroll
+  for (int i = 0; i < KPR; ++i) {
+    const int k = tid + i * NT;
+    th[i] = in[i] ? __ldcg(theta + k) : make_float2(0.f, 0.f);
+    wk[i] = in[i] ? __ldcg(wprev + k) : 0.f;
+  }
+  float r1[1] = {0.f};
+#pragma unroll
+  for (int i = 0; i < KPR; ++i) {
+    ik[i] = th[i].x * th[i].x + th[i].y * th[i].y;
+    r1[0] += ik[i];
+  }
+  ofa_focal::block_sum<NT>(r1, sh, tid, ofa_focal::BarBlock());
+  const float S = r1[0];
+  if (!(S > 0.f) || !isfinite(S)) {
+    if (writer && tid == 0) {
+      atomicOr(&st->err, OFA_ERRBIT_NUMERIC);
+      st->done = 1;
+    }
+    return;
+  }
+  const float inv_s = 1.f / S;
+  float r2[2] = {0.f, 0.f};
+  float mx = 0.f;
+  float sq[KPR];
+#pragma unroll
+  for (int i = 0; i < KPR; ++i) {
+    sq[i] = sqrtf(tk[i]);
+    if (!in[i]) continue;
+    const float ih = ik[i] * inv_s;
+    const float d = tk[i] - ih;
+    r2[0] += d * d;
+    r2[1] += ih * ih;
+    if (weighting) wk[i] *= sq[i] * rsqrtf(fmaxf(ih, 1e-30f));  // w_j = w_{j-1} sqrt(t / Ihat)
+    mx = fmaxf(mx, wk[i] * sq[i]);
+  }
+  ofa_focal::block_sum2_max<NT>(r2, mx, sh + 33, tid, ofa_focal::BarBlock());
+  const float xi = 1.f - sqrtf(r2[0] / r2[1]);
+  if (writer && tid == 0) {
+    const int hcount = st->hist_count;
+    hist[hcount % OFA_HIST_CAP] = (double)xi;
+    st->hist_count = hcount + 1;
+    st->xi = (double)xi;
+  }
+  if (thr > 0.0 && thr < 1.0 && (double)xi > thr) {
+    if (writer && tid == 0) st->done = 1;
+    return;
+  }
+  int e2 = 0;
+  frexpf(mx, &e2);
+  const float scale = mx > 0.f ? exp2f((float)-e2) : 1.f;
+#pragma unroll
+  for (int i = 0; i < KPR; ++i) {
+    if (!in[i]) continue;
+    const int k = tid + i * NT;
+    const float mag = wk[i] * sq[i] * scale;
+    float2 ck;
+    if (ik[i] > 0.f) {
+      const float inv = rsqrtf(ik[i]);
+      ck = make_float2(mag * th[i].x * inv, mag * th[i].y * inv);
+    } else {
+      ck = make_float2(mag, 0.f);  // arg(0) = 0
+    }
+    cg[q[i].y * pitch + q[i].x] = ck;
+    if (writer) {
+      if (weighting) w[k] = wk[i];
+      c[k] = ck;
+    }
+  }
+  if (writer && tid == 0) {
+    st->j = st->j + 1;
+    st->c_scale = scale;
+  }
+  __syncthreads();
+  float2 acc[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) acc[r] = make_float2(0.f, 0.f);
+  const int R = pitch / 32;
+  for (int iy = 0; iy < uy; ++iy) {
+    const float2 g = fy[iy][warp];
+    const float2* row = cg + iy * pitch + lane;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (r >= R) break;
+      const float2 v = row[32 * r];
+      acc[r].x = fmaf(g.x, v.x, acc[r].x);
+      acc[r].x = fmaf(-g.y, v.y, acc[r].x);
+      acc[r].y = fmaf(g.x, v.y, acc[r].y);
+      acc[r].y = fmaf(g.y, v.x, acc[r].y);
+    }
+  }
+  const int n = n0 + warp;
+  if (n >= ny) return;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int ix = lane + 32 * r;
+    if (ix < ux) split_store2(prec, hi, lo, ((size_t)n * kpad + ix) * 2, acc[r].x, acc[r].y);
+  }
+}
+
+}  // namespace
+
+size_t sep_focal_u_smem(int ux, int uy) {
+  return (size_t)uy * (size_t)((ux + 31) / 32 * 32) * sizeof(float2);
+}
+
+cudaError_t sep_focal_u_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(sep_focal_u_kernel<4>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SEP_U_SMEM_MAX);
+  const cudaError_t e2 = cudaFuncSetAttribute(sep_focal_u_kernel<16>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)SEP_U_SMEM_MAX);
+  return e != cudaSuccess ? e : e2;
+}
+
+bool sep_focal_u_fits(int ux, int uy, int K) {
+  return ux <= 128 && uy <= SEP_U_MAXY && K <= 16 * SEP_U_THREADS &&
+         sep_focal_u_smem(ux, uy) <= SEP_U_SMEM_MAX;
+}
+
+void launch_sep_focal_u(const float2* theta, const float* t, const float* wprev, float* w,
+                        float2* c, double* hist, OfaDevState* st, int weighting, const int2* ixy,
+                        int K, const float2* fyu, const int* done, int ny, int ux, int uy,
+                        int kpad, int prec, void* hi, void* lo, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((ny + SEP_U_ROWS - 1) / SEP_U_ROWS));
+  cfg.blockDim = dim3(SEP_U_THREADS);
+  cfg.dynamicSmemBytes = sep_focal_u_smem(ux, uy);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int pitch = (ux + 31) / 32 * 32;
+  if (K <= 4 * SEP_U_THREADS)
+    cudaLaunchKernelEx(&cfg, sep_focal_u_kernel<4>, theta, t, wprev, w, c, hist, st, weighting,
+                       ixy, K, fyu, done, ny, ux, uy, pitch, kpad, prec, hi, lo);
+  else
+    cudaLaunchKernelEx(&cfg, sep_focal_u_kernel<16>, theta, t, wprev, w, c, hist, st, weighting,
+                       ixy, K, fyu, done, ny, ux, uy, pitch, kpad, prec, hi, lo);
+}
+
 void launch_build_p(const float2* fyT, const float2* c, const int* done, int nyp, int kp,
                     int prec, void* hi, void* lo, cudaStream_t s) {
   const size_t total = (size_t)nyp * kp / 4;

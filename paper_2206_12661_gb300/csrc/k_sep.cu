@@ -372,6 +372,81 @@ __global__ void __launch_bounds__(SEP_THREADS) sep_sum_focal_kernel(
                                     ofa_focal::BarBlock());
 }
 
+// Separable form on the tensor cores, Theta from the forward's product G (contraction
+// parts [parts][ux][ny], parts <= TCT_MAX_PARTS): block (ix, g) sums the parts of
+// column ix in fixed order into shared memory (chunks of TCT_CHUNK rows; all parts of a
+// row loaded before any is added), warp w forms T[iy][ix] = sum_n Fyu[iy][n] G[n][ix]
+// for the grid row iy = 16 g + w (lanes strided over n, eight loads in flight, fixed
+// shuffle tree) and writes Theta_k = T at the focus of that grid point (every focus
+// sits on one).  The blocks also copy the weights to wprev, which the focal step reads
+// while it writes the new ones.
+constexpr int TCT_THREADS = 512, TCT_WARPS = TCT_THREADS / 32, TCT_CHUNK = 2048;
+constexpr int TCT_MAX_PARTS = 32;
+__global__ void __launch_bounds__(TCT_THREADS) sep_tc_theta_kernel(
+    const float2* __restrict__ gt, int parts, const float2* __restrict__ fyu,
+    const int* __restrict__ gridk, int ny, int ux, int uy, int K, float2* __restrict__ theta,
+    const float* __restrict__ w, float* __restrict__ wprev, const int* __restrict__ done) {
+  pdl_launch_dependents();
+  __shared__ float2 g[TCT_CHUNK];
+  __shared__ int skip;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ix = blockIdx.x;
+  const int iy = blockIdx.y * TCT_WARPS + warp;
+  pdl_wait();
+  if (tid == 0) skip = done != nullptr && __ldcg(done);
+  __syncthreads();
+  if (skip) return;
+  if (wprev != nullptr) {
+    const int b = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+    for (int k = b * TCT_THREADS + tid; k < K; k += nb * TCT_THREADS) wprev[k] = __ldcg(w + k);
+  }
+  const size_t slice = (size_t)ux * ny;
+  const float2* col = gt + (size_t)ix * ny;
+  const float2* fr = fyu + (size_t)min(iy, uy - 1) * ny;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int n0 = 0; n0 < ny; n0 += TCT_CHUNK) {
+    const int nn = min(TCT_CHUNK, ny - n0);
+    __syncthreads();  // the previous chunk is consumed
+    for (int i = tid; i < nn; i += TCT_THREADS) {
+      float2 v[TCT_MAX_PARTS];
+#pragma unroll
+      for (int z = 0; z < TCT_MAX_PARTS; ++z)
+        v[z] = z < parts ? __ldcg(col + z * slice + n0 + i) : make_float2(0.f, 0.f);
+      float2 a = v[0];
+#pragma unroll
+      for (int z = 1; z < TCT_MAX_PARTS; ++z)
+        if (z < parts) {
+          a.x += v[z].x;
+          a.y += v[z].y;
+        }
+      g[i] = a;
+    }
+    __syncthreads();
+    if (iy < uy)
+      for (int i0 = 0; i0 < nn; i0 += 8 * 32) {
+        float2 fv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * 32 + lane;
+          fv[u] = i < nn ? __ldg(fr + n0 + i) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * 32 + lane;
+          if (i < nn) cmac(acc, fv[u], g[i]);
+        }
+      }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (iy < uy && lane == 0) {
+    const int k = gridk[(size_t)iy * ux + ix];
+    if (k >= 0) theta[k] = acc;
+  }
+}
+
 // T for a tile's 32 pixel columns, then E' over the warp's INV_RPW rows and the
 // projection.  fys: the tile's Fyu rows [uy][INV_ROWS] (16-byte aligned), fxs: its Fxu
 // columns [ux][INV_COLS], cs: C on the grid [uy][ux], all complete in shared memory;
@@ -969,6 +1044,14 @@ void launch_sep_sum_focal(const float2* part, int nb, int K, int kp, float2* the
                           int weighting, unsigned* counter, const int* done, cudaStream_t s) {
   launch_pdl(sep_sum_focal_kernel, dim3((K + 31) / 32), SEP_THREADS, 0, s, part, nb, K, kp, theta,
              focal, t, w, c, hist, st, weighting, counter, done);
+}
+
+void launch_sep_tc_theta(const float2* gt, int parts, const float2* fyu, const int* gridk, int ny,
+                         int ux, int uy, int K, float2* theta, const float* w, float* wprev,
+                         const int* done, cudaStream_t s) {
+  const dim3 grid((unsigned)ux, (unsigned)((uy + TCT_WARPS - 1) / TCT_WARPS));
+  launch_pdl(sep_tc_theta_kernel, grid, TCT_THREADS, 0, s, gt, parts, fyu, gridk, ny, ux, uy, K,
+             theta, w, wprev, done);
 }
 
 void launch_sep_inverse(const float2* c, const int* gridk, const float2* fxu, const float2* fyu,

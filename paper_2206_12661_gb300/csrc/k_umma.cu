@@ -48,11 +48,13 @@ using namespace ofa_ptx;
 namespace {
 
 constexpr int BM = 128;
-// Epilogue warps: 8 (two per TMEM lane quarter) for the forward, 16 (four per
-// quarter) for the inverse, whose per-pixel epilogue needs more latency hiding.
+enum { EPI_FWD = 0, EPI_BWD = 1, EPI_GRAD = 2, EPI_STORE = 3 };
+
+// Epilogue warps: 8 (two per TMEM lane quarter) for the forward products, 16 (four
+// per quarter) for the inverse, whose per-pixel epilogue needs more latency hiding.
 // The two warps after them are the TMA producer and the MMA issuer.
 template <int EPI> struct Warps {
-  static constexpr int EPI_THREADS = EPI == 0 ? 256 : 512;
+  static constexpr int EPI_THREADS = EPI == EPI_FWD || EPI == EPI_STORE ? 256 : 512;
   static constexpr int TMA = EPI_THREADS / 32;
   static constexpr int MMA = TMA + 1;
   static constexpr int THREADS = EPI_THREADS + 64;
@@ -60,8 +62,6 @@ template <int EPI> struct Warps {
 constexpr int NUM_EPI_THREADS = 256;  // forward epilogue (the fused focal step runs on these)
 // Operand rows per stage are RB = 128 or 64 bytes of K (128B or 64B swizzle).
 constexpr int SMEM_BUDGET = 200 * 1024;   // operand stages
-
-enum { EPI_FWD = 0, EPI_BWD = 1, EPI_GRAD = 2 };
 
 
 struct EpiArgs {
@@ -81,6 +81,9 @@ struct EpiArgs {
   float amp_factor;
   const OfaDevState* st;
   int* err;
+  // separable grid form (EPI_STORE): the product itself, per contraction part,
+  // gt[split][j][n] = G[n][j] for the ep.K columns j and ep.ny rows n
+  float2* gt;
   // forward with the focal step fused into its last CTA (fuse != 0)
   int fuse;
   unsigned int* counters;  // [n_tiles + 1], zero between launches
@@ -118,7 +121,9 @@ struct Cfg {
   static constexpr int STAGE_BYTES = PLANES * (A_BYTES + B_BYTES);
   static constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES > 12 ? 12 : SMEM_BUDGET / STAGE_BYTES;
   // the inverse epilogue stages its output through 4 x 3 x 32 x 65 words of the freed stages
-  static_assert(EPI == 0 || STAGES * STAGE_BYTES >= 4 * 3 * 32 * 65 * 4, "epilogue staging");
+  static_assert(EPI == EPI_FWD || EPI == EPI_STORE ||
+                    STAGES * STAGE_BYTES >= 4 * 3 * 32 * 65 * 4,
+                "epilogue staging");
   static constexpr int UMMA_K_STEPS = RB / 32;            // 32 bytes of K per MMA
   static constexpr int RED_BYTES = EPI == EPI_FWD ? 4 * BN * 4 : 0;
   static constexpr int BAR_OFF = STAGES * STAGE_BYTES + RED_BYTES;
@@ -397,6 +402,34 @@ __device__ __forceinline__ void umma_tile(const CUtensorMap* tma_hi, const CUten
                                                          focal_sh, t, BarEpi());
         }
       }
+    } else if (EPI == EPI_STORE) {
+      // The product tile itself: lane = pupil row n, accumulator column pairs
+      // (Re, Im) = complex column j; each warp store covers 32 consecutive rows of
+      // one column of this contraction part's slice.
+      const bool ready = mbar_wait_sleep(bar_accum, 0);
+      tc_fence_after();
+      if (!ready) atomicOr(ep.err, OFA_ERRBIT_TIMEOUT);
+      const bool valid = ready && nkb > 0;
+      float2* g = ep.gt + (size_t)split * ep.K * ep.ny;
+#pragma unroll
+      for (int c = 0; c < CPW; ++c) {
+        const int ch = half * CPW + c;
+        uint32_t v[32];
+        if (valid) {
+          tmem_ld32(tw + ch * 32, v);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = 0u;
+        }
+        const int j0 = (n_tile * BN + ch * 32) >> 1;
+        if (n < ep.ny) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (j0 + q < ep.K)
+              g[(size_t)(j0 + q) * ep.ny + n] =
+                  make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
+        }
+      }
     } else {
       // Per-pixel work (thread = row).  Inputs are prefetched into registers while
       // the mainloop runs.  Warp `half` of a lane quarter takes accumulator chunks
@@ -667,12 +700,16 @@ void launch_gemm(int prec, int bn, int rb, int cg, const CUtensorMap& a_hi,
                  dim3 grid, int kbps, int kbt, const EpiArgs& ep, const int* done,
                  cudaStream_t s) {
   visit_variant(prec, bn, rb, cg, [&](auto kind, auto npass, auto bnc, auto rbc, auto cgc) {
-    OFA_VARIANT_TYPES;
-    const dim3 g = CG_ == 2 ? dim3(grid.y, grid.x, grid.z) : grid;  // pairs: rows on x
-    cudaLaunchAttribute attr[2];
-    cudaLaunchConfig_t cfg = make_cfg(g, Warps<EPI>::THREADS, C::SMEM, s, attr, CG_);
-    cudaLaunchKernelEx(&cfg, umma_gemm_kernel<K_, NP_, BN_, EPI, RB_, CG_>, a_hi, a_lo, b_hi,
-                       b_lo, kbps, kbt, ep, done);
+    if constexpr (EPI == EPI_STORE && decltype(cgc)::value == 2) {
+      return;  // the store epilogue runs on single CTAs only
+    } else {
+      OFA_VARIANT_TYPES;
+      const dim3 g = CG_ == 2 ? dim3(grid.y, grid.x, grid.z) : grid;  // pairs: rows on x
+      cudaLaunchAttribute attr[2];
+      cudaLaunchConfig_t cfg = make_cfg(g, Warps<EPI>::THREADS, C::SMEM, s, attr, CG_);
+      cudaLaunchKernelEx(&cfg, umma_gemm_kernel<K_, NP_, BN_, EPI, RB_, CG_>, a_hi, a_lo, b_hi,
+                         b_lo, kbps, kbt, ep, done);
+    }
   });
 }
 
@@ -682,10 +719,13 @@ cudaError_t set_attr_epi(int prec) {
   for (int bn : {128, 256})
     for (int cg : {1, 2})
       visit_variant(prec, bn, 128, cg, [&](auto kind, auto npass, auto bnc, auto rbc, auto cgc) {
-        OFA_VARIANT_TYPES;
-        cudaError_t r = cudaFuncSetAttribute(umma_gemm_kernel<K_, NP_, BN_, EPI, RB_, CG_>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        if (r != cudaSuccess) e = r;
+        if constexpr (!(EPI == EPI_STORE && decltype(cgc)::value == 2)) {
+          OFA_VARIANT_TYPES;
+          cudaError_t r = cudaFuncSetAttribute(umma_gemm_kernel<K_, NP_, BN_, EPI, RB_, CG_>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               C::SMEM);
+          if (r != cudaSuccess) e = r;
+        }
       });
   return e;
 }
@@ -714,10 +754,11 @@ EpiArgs base_args(ofa_plan* p) {
 // Opt every kernel variant of a precision into its dynamic shared memory (done
 // once per plan, outside any stream capture; the attribute is per device).
 cudaError_t tc_prepare(int prec) {
-  cudaError_t e = set_attr_epi<EPI_FWD>(prec);
-  cudaError_t e2 = set_attr_epi<EPI_BWD>(prec);
-  cudaError_t e3 = set_attr_epi<EPI_GRAD>(prec);
-  return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3);
+  const cudaError_t es[4] = {set_attr_epi<EPI_FWD>(prec), set_attr_epi<EPI_BWD>(prec),
+                             set_attr_epi<EPI_GRAD>(prec), set_attr_epi<EPI_STORE>(prec)};
+  for (cudaError_t e : es)
+    if (e != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err);
@@ -751,7 +792,7 @@ bool tc_config_valid(const ofa_plan* p, const TcOperands& t, int fwd_bn, int fwd
   if (bwd_cg != 1 && bwd_cg != 2) return false;
   // a 2-SM pair covers two row tiles
   if ((fwd_cg == 2 || bwd_cg == 2) && tiles_m % 2 != 0) return false;
-  return (2 * p->kp) % fwd_bn == 0 && (2 * p->nxp) % bwd_bn == 0;
+  return (2 * t.kp) % fwd_bn == 0 && (2 * p->nxp) % bwd_bn == 0;
 }
 
 bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
@@ -854,19 +895,19 @@ bool tc_autotune(ofa_plan* p, TcOperands& t, std::string& err) {
 
 bool tc_encode_maps(ofa_plan* p, TcOperands& t, std::string& err) {
   const int eb = t.elem_bytes;
-  const uint64_t e_cols = 2 * (uint64_t)p->nxp, k_cols = 2 * (uint64_t)p->kp;
+  const uint64_t e_cols = 2 * (uint64_t)p->nxp, k_cols = 2 * (uint64_t)t.kp;
   bool ok = true;
   // boxes are whole tiles; a 2-SM pair loads half of the B tile per CTA
   const uint32_t e_box = BM, bx_box = t.fwd_bn / t.fwd_cg;
   const uint32_t p_box = BM, q_box = t.bwd_bn / t.bwd_cg;
   const int fr = t.fwd_rb, br = t.bwd_rb;
   ok = ok && encode(&t.tm_e_hi, t.e_hi, eb, e_cols, p->nyp, e_box, fr, err);
-  ok = ok && encode(&t.tm_bx_hi, t.bx_hi, eb, e_cols, 2 * (uint64_t)p->kp, bx_box, fr, err);
+  ok = ok && encode(&t.tm_bx_hi, t.bx_hi, eb, e_cols, 2 * (uint64_t)t.kp, bx_box, fr, err);
   ok = ok && encode(&t.tm_p_hi, t.p_hi, eb, k_cols, p->nyp, p_box, br, err);
   ok = ok && encode(&t.tm_q_hi, t.q_hi, eb, k_cols, 2 * (uint64_t)p->nxp, q_box, br, err);
   if (t.npass == 3) {
     ok = ok && encode(&t.tm_e_lo, t.e_lo, eb, e_cols, p->nyp, e_box, fr, err);
-    ok = ok && encode(&t.tm_bx_lo, t.bx_lo, eb, e_cols, 2 * (uint64_t)p->kp, bx_box, fr, err);
+    ok = ok && encode(&t.tm_bx_lo, t.bx_lo, eb, e_cols, 2 * (uint64_t)t.kp, bx_box, fr, err);
     ok = ok && encode(&t.tm_p_lo, t.p_lo, eb, k_cols, p->nyp, p_box, br, err);
     ok = ok && encode(&t.tm_q_lo, t.q_lo, eb, k_cols, 2 * (uint64_t)p->nxp, q_box, br, err);
   } else {
@@ -882,7 +923,7 @@ void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream
                    bool fuse_focal) {
   const int kb_total = (2 * p->nxp * t.elem_bytes) / t.fwd_rb;
   const int kbps = (kb_total + t.fwd_split - 1) / t.fwd_split;
-  dim3 grid((2 * p->kp) / t.fwd_bn, p->nyp / BM, t.fwd_split);
+  dim3 grid((2 * t.kp) / t.fwd_bn, p->nyp / BM, t.fwd_split);
   EpiArgs ep = base_args(p);
   if (fuse_focal) {
     ep.fuse = 1;
@@ -902,8 +943,21 @@ void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream
                        t.tm_e_lo, t.tm_bx_hi, t.tm_bx_lo, grid, kbps, kb_total, ep, done, s);
 }
 
+// Separable grid form: G = E Fxu^T on the tensor cores, each contraction part's
+// product into its slice of p->gt ([split][ux][ny]).
+void launch_fwd_sep_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s) {
+  const int kb_total = (2 * p->nxp * t.elem_bytes) / t.fwd_rb;
+  const int kbps = (kb_total + t.fwd_split - 1) / t.fwd_split;
+  dim3 grid((2 * t.kp) / t.fwd_bn, p->nyp / BM, t.fwd_split);
+  EpiArgs ep = base_args(p);
+  ep.gt = p->gt;
+  ep.K = p->ux;
+  launch_gemm<EPI_STORE>(p->precision, t.fwd_bn, t.fwd_rb, 1, t.tm_e_hi, t.tm_e_lo, t.tm_bx_hi,
+                         t.tm_bx_lo, grid, kbps, kb_total, ep, done, s);
+}
+
 void launch_bwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s) {
-  const int kb_total = (2 * p->kp * t.elem_bytes) / t.bwd_rb;
+  const int kb_total = (2 * t.kp * t.elem_bytes) / t.bwd_rb;
   dim3 grid((2 * p->nxp) / t.bwd_bn, p->nyp / BM, 1);
   EpiArgs ep = base_args(p);
   ep.out = p->phi;
@@ -916,7 +970,7 @@ void launch_bwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream
 void launch_grad_tc(ofa_plan* p, const TcOperands& t, const float* phi, float scale_unused,
                     float* grad, cudaStream_t s) {
   (void)scale_unused;
-  const int kb_total = (2 * p->kp * t.elem_bytes) / t.bwd_rb;
+  const int kb_total = (2 * t.kp * t.elem_bytes) / t.bwd_rb;
   dim3 grid((2 * p->nxp) / t.bwd_bn, p->nyp / BM, 1);
   EpiArgs ep = base_args(p);
   ep.out = grad;

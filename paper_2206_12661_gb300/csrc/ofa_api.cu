@@ -250,10 +250,10 @@ void choose_tiles(ofa_plan* p, TcOperands& t, int sms) {
   for (int bn : {256, 128}) {
     for (int split = 1; split <= 8; split *= 2) {
       if (kb_fwd / split < 4) break;
-      const long ctas = (long)tiles_m * (2 * p->kp / bn) * split;
+      const long ctas = (long)tiles_m * (2 * t.kp / bn) * split;
       const long waves = (ctas + sms - 1) / sms;
       const double cost = (double)waves * ((double)kb_fwd / split) * bn * t.npass +
-                          0.02 * split * tiles_m * 2.0 * p->kp;
+                          0.02 * split * tiles_m * 2.0 * t.kp;
       if (cost < best - 1e-9) {
         best = cost;
         t.fwd_bn = bn;
@@ -273,13 +273,25 @@ void choose_tiles(ofa_plan* p, TcOperands& t, int sms) {
   }
 }
 
+// Separable form on the tensor cores: the forward's tiles and contraction parts (about
+// one CTA per SM, at least two k-blocks per part), the inverse as choose_tiles has it.
+int sep_tc_split(const ofa_plan* p, const TcOperands& t, int sms) {
+  const int tiles = (p->nyp / 128) * (2 * t.kp / t.fwd_bn);
+  const int kb_fwd = (2 * p->nxp * t.elem_bytes) / t.fwd_rb;
+  int split = 1;
+  while (split < 32 && tiles * split * 2 <= sms && kb_fwd / (split * 2) >= 2) split *= 2;
+  return split;
+}
+
 ofa_status alloc_tc(ofa_plan* p, TcOperands& t, bool with_static) {
   const int eb = prec_elem_bytes(p->precision);
   t.elem_bytes = eb;
   t.npass = prec_npass(p->precision);
+  // the planes' focus dimension: the foci, or the separable form's distinct x
+  t.kp = p->sep_tc ? round_up(p->ux, 64) : p->kp;
   const size_t e_n = (size_t)p->nyp * 2 * p->nxp;
-  const size_t bx_n = (size_t)2 * p->kp * 2 * p->nxp;
-  const size_t pp_n = (size_t)p->nyp * 2 * p->kp;
+  const size_t bx_n = (size_t)2 * t.kp * 2 * p->nxp;
+  const size_t pp_n = (size_t)p->nyp * 2 * t.kp;
   // reserve or allocate straight into the operand's own slot (an arena commit
   // writes the final address there later)
   auto A = [&](void** ptr, size_t n) -> bool {
@@ -343,7 +355,17 @@ void enqueue_sep_forward(ofa_plan* p, const float2* e32, cudaStream_t s) {
 // of mode 1), so plan creation captures it before the statistics are read back.
 void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
   const int* done = done_ptr(p);
-  if (p->sep && p->sep_fast) {
+  if (p->sep_tc) {
+    // separable form on the tensor cores: G per contraction part, Theta from G, the
+    // focal step with U = conj(Fy_u)^T C, then E' = U conj(Fx_u) with the phase projection
+    launch_fwd_sep_tc(p, p->tc, done, s);
+    launch_sep_tc_theta(p->gt, p->tc.fwd_split, p->fyu, p->sep_gridk, p->ny, p->ux, p->uy, p->K,
+                        p->part, p->w, p->sep_wprev, done, s);
+    launch_sep_focal_u(p->part, p->t, p->sep_wprev, p->w, p->c, p->hist, p->st, p->weighting,
+                       p->ixy, p->K, p->fyu, done, p->ny, p->ux, p->uy, p->tc.kp, p->precision,
+                       p->tc.p_hi, p->tc.p_lo, s);
+    launch_bwd_tc(p, p->tc, done, s);
+  } else if (p->sep && p->sep_fast) {
     const FocalTail f = {p->t, p->w, p->c, p->hist, p->st, p->weighting, p->counters, 1};
     launch_sep_fwd(p->e32, p->fxu, p->fyu, p->ixy, p->nx, p->ny, p->ux, p->uy, p->K, p->kp,
                    p->sm_count, p->part, f, done, s);
@@ -377,9 +399,23 @@ void enqueue_iteration(ofa_plan* p, cudaStream_t s) {
   }
 }
 
+// The separable form on the tensor cores iterates on the operand planes; its FP32
+// entry points take the field of the current phase from this.
+void sep_tc_refresh_e32(ofa_plan* p, cudaStream_t s) {
+  if (p->sep_tc) launch_field_f32(p->phi, p->amp, p->nx, p->ny, p->e32, s);
+}
+
+// ... and after an FP32 step has moved the phase, the iteration's planes follow it.
+void sep_tc_refresh_planes(ofa_plan* p, cudaStream_t s) {
+  if (p->sep_tc)
+    launch_field_planes(p->phi, p->amp, p->nx, p->ny, p->nxp, p->precision, p->tc.e_hi,
+                        p->tc.e_lo, s);
+}
+
 // Forward at the loop's current phase + statistics (mode 1) or output (mode 2).
 void enqueue_forward_current(ofa_plan* p, cudaStream_t s) {
   if (p->sep) {
+    sep_tc_refresh_e32(p, s);
     enqueue_sep_forward(p, p->e32, s);
     launch_focal(p->part, 1, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist, p->st,
                  1, p->weighting, ldexpf(1.f, p->amp_exp), p->amp_energy, s);
@@ -499,6 +535,7 @@ ofa_status ofa_options_default(ofa_options* o) {
   o->separable = -1;
   o->fused_loop = 0;
   o->separable_loop = -1;
+  o->separable_tc = -1;
   return OFA_OK;
 }
 
@@ -556,10 +593,10 @@ ofa_status ofa_plan_config(const ofa_plan* p, int* c) {
     c[8] = 1; c[11] = p->sep_loop_grid;
     return OFA_OK;
   }
-  if (!use_tc(p)) return OFA_OK;
+  if (!use_tc(p) && !p->sep_tc) return OFA_OK;
   const TcOperands& t = p->tc;
   c[0] = t.fwd_bn; c[1] = t.fwd_split; c[2] = t.fwd_cg; c[3] = t.bwd_bn; c[4] = t.bwd_cg;
-  c[5] = p->K <= 4096 ? 1 : 0; c[6] = t.fwd_rb; c[7] = t.bwd_rb;
+  c[5] = p->K <= 4096 && !p->sep_tc ? 1 : 0; c[6] = t.fwd_rb; c[7] = t.bwd_rb;
   if (p->loop.ready) {
     c[8] = 1; c[9] = p->loop.cg; c[10] = p->loop.split; c[11] = p->loop.grid;
   }
@@ -772,6 +809,43 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     delete p;
     return ofa_fail(nullptr, OFA_ERR_UNSUPPORTED, "the separable form needs 2D foci");
   }
+  if (opt.separable_tc < -1 || opt.separable_tc > 1) {
+    delete p;
+    return ofa_fail(nullptr, OFA_ERR_UNSUPPORTED, "separable_tc must be -1, 0 or 1");
+  }
+  // The separable iteration on the tensor cores: a tensor-core precision, at most
+  // SEP_TC_MAX_UX distinct x (one MMA tile of columns) and one focus per grid point.
+  if (p->sep && opt.separable_tc != 0) {
+    bool ok = prec_is_tc(opt.precision) && p->ux <= SEP_TC_MAX_UX && p->uy <= SEP_TC_MAX_UY &&
+              sep_focal_u_fits(p->ux, p->uy, n_foci);
+    if (ok) {
+      std::vector<std::pair<double, double>> pts(n_foci);
+      for (int k = 0; k < n_foci; ++k) pts[k] = {xy[2 * (size_t)k], xy[2 * (size_t)k + 1]};
+      std::sort(pts.begin(), pts.end());
+      ok = std::adjacent_find(pts.begin(), pts.end()) == pts.end();
+    }
+    if (!ok && opt.separable_tc == 1) {
+      delete p;
+      return ofa_fail(nullptr, OFA_ERR_UNSUPPORTED,
+                      "the separable form on the tensor cores needs a tensor-core precision, "
+                      "at most 128 distinct x and y, 4096 foci and one focus per grid point");
+    }
+    if (ok && opt.separable_tc == 1 && opt.separable_loop == 1) {
+      delete p;
+      return ofa_fail(nullptr, OFA_ERR_UNSUPPORTED,
+                      "separable_tc = 1 and separable_loop = 1 exclude each other");
+    }
+    p->sep_tc = ok && (opt.separable_tc == 1 || p->ux + p->uy > 48);
+    if (p->sep_tc) {
+      // the forward's configuration (the contraction parts size p->gt)
+      p->tc.elem_bytes = prec_elem_bytes(opt.precision);
+      p->tc.npass = prec_npass(opt.precision);
+      p->tc.kp = round_up(p->ux, 64);
+      p->tc.fwd_bn = 128;
+      p->tc.fwd_cg = 1;
+      p->tc.fwd_split = sep_tc_split(p, p->tc, sm_count);
+    }
+  }
 
   auto fail = [&](ofa_status s) {
     g_thread_error = p->last_error;
@@ -829,13 +903,15 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
       R(dalloc(&p->fxu, (size_t)p->ux * nx));
       R(dalloc(&p->fyu, (size_t)p->uy * ny));
       p->sep_parts = sep_parts(nx, ny, p->ux, sm_count);
-      R(dalloc(&p->gt, (size_t)p->sep_parts * p->ux * ny));
+      const int gt_parts = std::max(p->sep_parts, p->sep_tc ? p->tc.fwd_split : 1);
+      R(dalloc(&p->gt, (size_t)gt_parts * p->ux * ny));
       R(dalloc(&p->tconj, (size_t)p->uy * nx));
       R(dalloc(&p->ones, (size_t)p->uy));
       R(dalloc(&p->ixy, (size_t)n_foci));
       R(dalloc(&p->row_ptr, (size_t)p->uy + 1));
       R(dalloc(&p->row_foci, (size_t)n_foci));
       R(dalloc(&p->sep_gridk, (size_t)p->ux * p->uy));
+      if (p->sep_tc) R(dalloc(&p->sep_wprev, (size_t)n_foci));
       R(dalloc(&p->sep_coord, 2 * ((size_t)p->ux + p->uy)));
     }
     R(dalloc(&p->st, 1));
@@ -848,6 +924,10 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
       R(dalloc(&p->simt.fyT, z.fyT));
       R(dalloc(&p->simt.fws, z.fws));
       R(dalloc(&p->simt.cnt, z.cnt));
+      // the separable form on the tensor cores keeps the FP32 buffers for its other
+      // entry points
+      if (p->sep_tc && e == cudaSuccess && alloc_tc(p, p->tc, true) != OFA_OK)
+        e = cudaErrorMemoryAllocation;
     } else {
       R(dalloc(&p->fyT, (size_t)p->nyp * p->kp));
       if (e == cudaSuccess && alloc_tc(p, p->tc, true) != OFA_OK) e = cudaErrorMemoryAllocation;
@@ -923,7 +1003,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
                   sep_inv_smem(p->ux, p->uy) <= limit && sep_prepare() == cudaSuccess;
     cudaGetLastError();
     // the persistent loop: the shape fits, and one block per SM can be resident
-    if (opt.separable_loop != 0) {
+    if (opt.separable_loop != 0 && !p->sep_tc) {
       int grid = 0, resident = 0;
       const bool ok = p->sep_fast &&
                       sep_loop_shape(nx, ny, p->ux, p->uy, n_foci, sm_count, nullptr, &grid) &&
@@ -1041,6 +1121,29 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
       launch_transpose_fy(p->fy, n_foci, ny, simt_ldk(n_foci), ny, p->simt.fyT, p->stream);
     }
     launch_field_f32(p->phi, p->amp, nx, ny, p->e32, p->stream);
+    if (p->sep_tc) {
+      // tensor-core operands of the separable iteration: Fx_u in the forward's and the
+      // inverse's block forms, and the pupil field planes
+      TcOperands& t = p->tc;
+      launch_pack_fx(p->fxu, p->ux, nx, t.kp, p->nxp, 0, p->precision, t.bx_hi, t.bx_lo,
+                     p->stream);
+      launch_pack_fx(p->fxu, p->ux, nx, t.kp, p->nxp, 1, p->precision, t.q_hi, t.q_lo,
+                     p->stream);
+      launch_field_planes(p->phi, p->amp, nx, ny, p->nxp, p->precision, t.e_hi, t.e_lo,
+                          p->stream);
+      OFA_TRY(prepare_precision(dev, p->precision), "setting kernel shared-memory attributes");
+      OFA_TRY(sep_focal_u_prepare(), "setting kernel shared-memory attributes");
+      choose_tiles(p, t, sm_count);   // the inverse's tile width
+      t.fwd_bn = 128;
+      t.fwd_cg = 1;
+      t.bwd_cg = 1;
+      t.fwd_split = sep_tc_split(p, t, sm_count);
+      std::string err;
+      if (!tc_encode_maps(p, t, err)) {
+        p->last_error = err;
+        return fail(OFA_ERR_CUDA);
+      }
+    }
   }
   launch_set_j(p->st, 0, 1, p->stream);
   launch_control(p->st, 0.0, 1, p->stream);
@@ -1191,6 +1294,7 @@ ofa_status ofa_iterate_measured(ofa_plan* p, const float* measured, int mem_spac
   launch_control(p->st, 0.0, 1, s);
   // forward (partials only), focal step on the captured intensities, inverse
   const int n_part = p->sep ? 1 : use_tc(p) ? fwd_n_part(p->nyp, p->tc) : simt_fwd_tiles(p->ny);
+  sep_tc_refresh_e32(p, s);
   if (p->sep) enqueue_sep_forward(p, p->e32, s);
   else if (use_tc(p)) launch_fwd_tc(p, p->tc, nullptr, s, false);
   else
@@ -1200,6 +1304,7 @@ ofa_status ofa_iterate_measured(ofa_plan* p, const float* measured, int mem_spac
                         p->weighting, p->meas, s);
   if (p->sep) {
     enqueue_sep_inverse(p, nullptr, s);
+    sep_tc_refresh_planes(p, s);
   } else if (use_tc(p)) {
     launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
     launch_bwd_tc(p, p->tc, nullptr, s);
@@ -1297,6 +1402,7 @@ ofa_status ofa_set_state(ofa_plan* p, const float* phi, const float* w, int j, i
                         p->tc.e_lo, p->stream);
   else
     launch_field_f32(p->phi, p->amp, p->nx, p->ny, p->e32, p->stream);
+  sep_tc_refresh_planes(p, p->stream);
   launch_set_j(p->st, j, 1, p->stream);
   return sync_and_check(p);
 }
@@ -1364,6 +1470,7 @@ ofa_status ofa_shard_update(ofa_plan* p, const float* theta_total) {
                p->theta, p->inten, p->c, p->hist, p->st, 0, p->weighting, 1.f, p->amp_energy, s);
   if (p->sep) {
     enqueue_sep_inverse(p, nullptr, s);
+    sep_tc_refresh_planes(p, s);
   } else if (use_tc(p)) {
     launch_build_p(p->fyT, p->c, nullptr, p->nyp, p->kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
     launch_bwd_tc(p, p->tc, nullptr, s);
@@ -1453,8 +1560,9 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   cudaError_t e = cudaMalloc(&phi_s, npix * 4);
   if (e == cudaSuccess) e = cudaMalloc(&w_s, (size_t)p->K * 4);
   if (e == cudaSuccess) e = cudaMalloc(&st_s, sizeof(OfaDevState));
-  if (e == cudaSuccess && tc) e = cudaMalloc(&e_s[0], e_bytes);
-  if (e == cudaSuccess && tc && p->tc.npass == 3) e = cudaMalloc(&e_s[1], e_bytes);
+  const bool planes = tc || p->sep_tc;   // operand planes to save and restore
+  if (e == cudaSuccess && planes) e = cudaMalloc(&e_s[0], e_bytes);
+  if (e == cudaSuccess && planes && p->tc.npass == 3) e = cudaMalloc(&e_s[1], e_bytes);
   auto cleanup = [&]() {
     dfree(phi_s);
     dfree(w_s);
@@ -1470,7 +1578,7 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   cudaMemcpyAsync(phi_s, p->phi, npix * 4, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(w_s, p->w, (size_t)p->K * 4, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(st_s, p->st, sizeof(OfaDevState), cudaMemcpyDeviceToDevice, s);
-  if (tc) cudaMemcpyAsync(e_s[0], p->tc.e_hi, e_bytes, cudaMemcpyDeviceToDevice, s);
+  if (planes) cudaMemcpyAsync(e_s[0], p->tc.e_hi, e_bytes, cudaMemcpyDeviceToDevice, s);
   if (e_s[1]) cudaMemcpyAsync(e_s[1], p->tc.e_lo, e_bytes, cudaMemcpyDeviceToDevice, s);
   launch_control(p->st, 0.0, 1, s);
 
@@ -1478,19 +1586,32 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   auto run = [&](int which) {
     switch (which) {
       case 0:
-        if (p->sep) enqueue_sep_forward(p, p->e32, s);
-        else if (tc) launch_fwd_tc(p, p->tc, nullptr, s, p->K <= 4096);  // + fused focal step
-        else launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr,
-                             p->simt, s);
+        if (p->sep_tc) {
+          launch_fwd_sep_tc(p, p->tc, nullptr, s);
+          launch_sep_tc_theta(p->gt, p->tc.fwd_split, p->fyu, p->sep_gridk, p->ny, p->ux, p->uy,
+                              p->K, p->part, p->w, p->sep_wprev, nullptr, s);
+        } else if (p->sep) {
+          enqueue_sep_forward(p, p->e32, s);
+        } else if (tc) {
+          launch_fwd_tc(p, p->tc, nullptr, s, p->K <= 4096);  // + fused focal step
+        } else {
+          launch_fwd_simt(p->e32, p->fx, p->fy, p->nx, p->ny, p->K, p->kp, p->part, nullptr,
+                          p->simt, s);
+        }
         break;
       case 1:
-        if (tc && p->K <= 4096) break;  // fused into the forward kernel
+        if ((tc && p->K <= 4096) || p->sep_tc) break;  // fused into another kernel
         launch_control(p->st, 0.0, 1, s);
         launch_focal(p->part, n_part, p->kp, p->K, p->t, p->w, p->theta, p->inten, p->c, p->hist,
                      p->st, 0, p->weighting, 1.f, p->amp_energy, s);
         break;
       case 2:
-        if (p->sep) {
+        if (p->sep_tc) {
+          // the focal step and U in one launch (reported here; nothing in ms_out[1])
+          launch_sep_focal_u(p->part, p->t, p->sep_wprev, p->w, p->c, p->hist, p->st,
+                             p->weighting, p->ixy, p->K, p->fyu, nullptr, p->ny, p->ux, p->uy,
+                             p->tc.kp, p->precision, p->tc.p_hi, p->tc.p_lo, s);
+        } else if (p->sep) {
           // the three-launch separable form builds T inside the inverse (reported there)
           if (!p->sep_fast)
             launch_sep_t(p->c, p->fxu, p->ixy, p->row_ptr, p->row_foci, p->uy, p->nx, p->tconj,
@@ -1500,7 +1621,8 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
         else launch_scale_conj(p->c, p->simt.fyT, p->ny, p->K, p->simt.p32, nullptr, s);
         break;
       default:
-        if (p->sep) enqueue_sep_inverse(p, nullptr, s);
+        if (p->sep_tc) launch_bwd_tc(p, p->tc, nullptr, s);
+        else if (p->sep) enqueue_sep_inverse(p, nullptr, s);
         else if (tc) launch_bwd_tc(p, p->tc, nullptr, s);
         else launch_bwd_simt_product(p->simt.fxT, p->nx, p->ny, p->K, p->amp, p->phi, p->e32,
                                      nullptr, p->simt, s);
@@ -1511,7 +1633,7 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
   for (int which = 0; which < 4; ++which) {
-    if (which == 1 && tc && p->K <= 4096) {
+    if (which == 1 && ((tc && p->K <= 4096) || p->sep_tc)) {
       ms_out[which] = 0.0;
       continue;
     }
@@ -1529,7 +1651,7 @@ ofa_status ofa_profile_kernels(ofa_plan* p, int reps, double* ms_out) {
   cudaMemcpyAsync(p->phi, phi_s, npix * 4, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(p->w, w_s, (size_t)p->K * 4, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(p->st, st_s, sizeof(OfaDevState), cudaMemcpyDeviceToDevice, s);
-  if (tc) cudaMemcpyAsync(p->tc.e_hi, e_s[0], e_bytes, cudaMemcpyDeviceToDevice, s);
+  if (planes) cudaMemcpyAsync(p->tc.e_hi, e_s[0], e_bytes, cudaMemcpyDeviceToDevice, s);
   if (e_s[1]) cudaMemcpyAsync(p->tc.e_lo, e_s[1], e_bytes, cudaMemcpyDeviceToDevice, s);
   if (!tc) launch_field_f32(p->phi, p->amp, p->nx, p->ny, p->e32, s);  // field of the restored phi
   ofa_status st = sync_and_check(p);

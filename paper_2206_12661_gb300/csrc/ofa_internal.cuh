@@ -62,6 +62,7 @@ struct TcOperands {
   int fwd_bn = 256, fwd_split = 1, bwd_bn = 256;
   int fwd_rb = 128, bwd_rb = 128;                          // operand row bytes per stage
   int fwd_cg = 1, bwd_cg = 1;                              // 2 = 2-SM MMA pairs
+  int kp = 0;   // padded focus dimension of the planes: K_p, or U_x rounded up (separable)
 };
 
 // Fused loop kernel (all of an iteration in one persistent cooperative launch):
@@ -132,11 +133,13 @@ struct ofa_plan {
   int2* ixy = nullptr;                 // [K] (ix, iy) of each focus
   bool sep_fast = false;               // the three-launch separable iteration (k_sep.cu)
   bool sep_loop = false;               // the separable form's persistent loop (k_sep.cu)
+  bool sep_tc = false;                 // the separable form's iteration on the tensor cores
   int sep_loop_grid = 0;               // its blocks
   int sm_count = 0;
   int* row_ptr = nullptr;              // [uy + 1] foci of each grid row ...
   int* row_foci = nullptr;             // [K] ... in increasing ix order
   int* sep_gridk = nullptr;            // [uy][ux] focus at each grid point, or -1
+  float* sep_wprev = nullptr;          // [K] weights before the focal step (tensor-core form)
   TcOperands tc;
   TcOperands tc_aux;                   // E planes of an external phase (forward/adjoint)
   LoopOperands loop;                   // fused loop kernel (tensor-core forms, K <= 4096)
@@ -297,6 +300,26 @@ void launch_grad_c(const float2* theta, const float* g, int K, int kp, float in_
                    float2* c, OfaDevState* st, cudaStream_t s);
 void launch_build_p(const float2* fyT, const float2* c, const int* done, int nyp, int kp,
                     int prec, void* hi, void* lo, cudaStream_t s);
+// Separable grid form on the tensor cores: the focal step of the loop on theta [K]
+// (the weights read from wprev, the new ones written to w) and the inverse's left
+// operand U[n][ix] = sum_iy conj(Fyu[iy][n]) C[iy][ix], C the grid of the new c_k, into
+// operand planes [nyp][2 kpad], in one launch; sep_focal_u_fits: the grid and the foci
+// this launch covers, sep_focal_u_prepare: its shared-memory opt-in (once per process).
+bool sep_focal_u_fits(int ux, int uy, int K);
+cudaError_t sep_focal_u_prepare();
+void launch_sep_focal_u(const float2* theta, const float* t, const float* wprev, float* w,
+                        float2* c, double* hist, OfaDevState* st, int weighting, const int2* ixy,
+                        int K, const float2* fyu, const int* done, int ny, int ux, int uy,
+                        int kpad, int prec, void* hi, void* lo, cudaStream_t s);
+constexpr int SEP_TC_MAX_UX = 128, SEP_TC_MAX_UY = 128, SEP_TC_MAX_PARTS = 32;
+// Separable form on the tensor cores: Theta_k = T[iy_k][ix_k] with T = Fyu G from the
+// forward's contraction parts gt [parts][ux][ny] (parts <= 32, summed in fixed order),
+// into theta [K]; the blocks also copy w [K] to wprev (nullable) for the focal step.
+void launch_sep_tc_theta(const float2* gt, int parts, const float2* fyu, const int* gridk, int ny,
+                         int ux, int uy, int K, float2* theta, const float* w, float* wprev,
+                         const int* done, cudaStream_t s);
+void launch_sep_u_planes(const float2* cgrid, const float2* fyu, const int* done, int ny, int ux,
+                         int uy, int kpad, int prec, void* hi, void* lo, cudaStream_t s);
 // Intensity loss sum (I/S - t)^2 of Theta, its gradient g = dL/dI folded into
 // c = g Theta (scaled; st->c_scale), loss_hist[*step] = L when the index lies in
 // [0, loss_cap) (step, loss_hist nullable).
@@ -324,6 +347,8 @@ void launch_selftest_wait(OfaDevState* st, cudaStream_t s);
 // fuse_focal: the last CTA runs the focal step of the loop (mode 0) on the final Theta.
 void launch_fwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s,
                    bool fuse_focal);
+// Separable grid form: G = E Fxu^T per contraction part into p->gt [split][ux][ny].
+void launch_fwd_sep_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s);
 void launch_bwd_tc(ofa_plan* p, const TcOperands& t, const int* done, cudaStream_t s);
 void launch_grad_tc(ofa_plan* p, const TcOperands& t, const float* phi, float scale,
                     float* grad, cudaStream_t s);

@@ -46,7 +46,8 @@ class ofa_options(C.Structure):
                 ("focus_z", C.c_void_p), ("separable", C.c_int),
                 ("kernel_config", C.c_int * 5), ("fused_loop", C.c_int),
                 ("loop_config", C.c_int * 2), ("shard_row0", C.c_int),
-                ("shard_ny_total", C.c_int), ("separable_loop", C.c_int)]
+                ("shard_ny_total", C.c_int), ("separable_loop", C.c_int),
+                ("separable_tc", C.c_int)]
 
 
 class ofa_stats(C.Structure):
@@ -356,7 +357,7 @@ class Plan:
                  precision="f16x3", amplitude=None, phi0=None, seed=0, weighting=True,
                  stream=None, waist_frac=0.4, mem_space=OFA_MEM_HOST, autotune=True,
                  focus_z=None, separable=-1, kernel_config=None, fused_loop=None,
-                 loop_config=None, shard=None, separable_loop=None):
+                 loop_config=None, shard=None, separable_loop=None, separable_tc=None):
         opt = ofa_options_default()
         opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opt.seed = int(seed)
@@ -370,6 +371,8 @@ class Plan:
             opt.fused_loop = int(fused_loop)
         if separable_loop is not None:
             opt.separable_loop = int(separable_loop)
+        if separable_tc is not None:
+            opt.separable_tc = int(separable_tc)
         if loop_config is not None:
             opt.loop_config[0], opt.loop_config[1] = int(loop_config[0]), int(loop_config[1])
         if kernel_config is not None:

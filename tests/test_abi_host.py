@@ -44,6 +44,7 @@ def test_options_default(ofa):
     assert o.weighting == 1
     assert o.autotune == 1
     assert o.separable == -1 and not o.focus_z
+    assert o.separable_loop == -1 and o.separable_tc == -1
     assert not o.amplitude and not o.phi0 and not o.cuda_stream
 
 

@@ -56,7 +56,21 @@ def ragged(nx=333, ny=250, K=300, seed=21):
                       I.gaussian_amplitude(nx, ny), I.uniform_phase(rng, nx, ny), 3)
 
 
-WORKLOADS = {"ragged333x250_300": ragged, "pupil1024_poisson1000":
+def ragged_grid(nx=333, ny=250, cols=13, rows=41, seed=23):
+    """A regular cols x rows grid on a ragged pupil (row and column padding of every
+    operand plane), targets U[0.5, 1]."""
+    rng = np.random.default_rng(seed)
+    half = 532e-9 * 0.2 / (2 * 8e-6)
+    xx, yy = np.meshgrid(np.linspace(-0.8 * half, 0.8 * half, cols),
+                         np.linspace(-0.8 * half, 0.8 * half, rows))
+    xy = np.stack([xx.ravel(), yy.ravel()], 1)
+    t = rng.uniform(0.5, 1.0, xy.shape[0]).astype(np.float32)
+    return I.Workload(f"grid{cols}x{rows}_{nx}x{ny}", nx, ny, 8e-6, 8e-6, 532e-9, 0.2, xy, t,
+                      I.gaussian_amplitude(nx, ny), I.uniform_phase(rng, nx, ny), 3)
+
+
+WORKLOADS = {"ragged333x250_300": ragged, "grid13x41_333x250": ragged_grid,
+             "pupil1024_poisson1000":
              lambda: I.named("pupil1024_poisson1000"),
              "pupil1920x1152_grid2500": lambda: I.named("pupil1920x1152_grid2500"),
              "table1_grid9x9": lambda: I.named("table1_grid9x9"),
@@ -181,6 +195,18 @@ def test_separable_loop_one_step(ofa, dev, name, loop):
     1 to 5 per thread in its focal step (81, 400 and 2115 foci)."""
     cfg = check_plan(ofa, name, "fp32", j=5, separable=1, separable_loop=loop)
     assert cfg["fused_loop"] == loop
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+@pytest.mark.parametrize("name", ["grid13x41_333x250", "table1_grid9x9", "table1_grid20x20",
+                                  "table1_grid45x47"])
+def test_separable_tc_one_step(ofa, dev, name, prec):
+    """The separable form's iteration on the tensor cores (forced), one step from the
+    oracle's iterate 5: G = E Fx_u^T per contraction part, Theta and the new weights from
+    it, U = conj(Fy_u)^T C and the inverse product with the phase projection, within the
+    form's tolerances; on a ragged pupil and on grids of 9 to 47 distinct coordinates."""
+    cfg = check_plan(ofa, name, prec, j=5, separable=1, separable_tc=1)
+    assert cfg["fwd_bn"] == 128 and cfg["fused_loop"] == 0, cfg
 
 
 @pytest.mark.parametrize("prec", ["f16x3", "tf32"])
