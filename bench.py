@@ -216,14 +216,17 @@ def bench_config(ofa, I, torch, stream, flush, name: str, precisions, reps: int 
     return out
 
 
-def bench_separable(ofa, I, torch, stream, flush, reps: int = 3) -> dict:
+SEPARABLE_GRIDS = ("table1_grid9x9", "table1_grid45x47", "table1_random66")
+
+
+def bench_separable(ofa, I, torch, stream, flush, reps: int = 3, grids=SEPARABLE_GRIDS) -> dict:
     """Table 1 geometry (1000^2 pupil) with regular 9 x 9 and 45 x 47 grids and the
     paper's 66 random spots on a 45 x 47 sampling grid: the separable grid form
     (products through the distinct focus coordinates) with FP32 products on the CUDA
     cores and with F16X3 products on the tensor cores, against the general tensor-core
     form (F16X3), iterations/s."""
     out = {}
-    for name in ("table1_grid9x9", "table1_grid45x47", "table1_random66"):
+    for name in grids:
         w = I.named(name)
         rec = {"n_foci": w.n_foci}
         for label, kw in (("separable_fp32", {"separable": 1, "precision": "fp32"}),
@@ -418,6 +421,8 @@ def main():
     ap.add_argument("--kernel-config", default=None,
                     help="force the tensor-core tiles: fwd_bn,fwd_split,fwd_cg,inv_bn,inv_cg "
                          "(as ofa_options.kernel_config; default: the plan's autotuner)")
+    ap.add_argument("--separable-grid", default=None, choices=list(SEPARABLE_GRIDS),
+                    help="with --only separable: time this Table 1 grid alone")
     ap.add_argument("--only", default=None,
                     choices=["differentiation", "batch", "separable", "configs"],
                     help="run one of the extra sections alone and print its JSON (for "
@@ -455,7 +460,9 @@ def main():
         sections = {
             "differentiation": lambda: bench_differentiation(ofa, I, torch, stream, flush),
             "batch": lambda: bench_batch(ofa, I, torch, stream, flush),
-            "separable": lambda: bench_separable(ofa, I, torch, stream, flush),
+            "separable": lambda: bench_separable(
+                ofa, I, torch, stream, flush,
+                grids=(args.separable_grid,) if args.separable_grid else SEPARABLE_GRIDS),
             "configs": lambda: [bench_config(ofa, I, torch, stream, flush,
                                              "pupil256_grid100_uniform", ("fp32", "f16x3"))]}
         print(json.dumps({"section": args.only, args.only: sections[args.only]()}),
