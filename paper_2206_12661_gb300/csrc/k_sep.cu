@@ -373,15 +373,17 @@ __global__ void __launch_bounds__(SEP_THREADS) sep_sum_focal_kernel(
 }
 
 // Separable form on the tensor cores, Theta from the forward's product G (contraction
-// parts [parts][ux][ny], parts <= TCT_MAX_PARTS): block (ix, g) sums the parts of
-// column ix in fixed order into shared memory (chunks of TCT_CHUNK rows; all parts of a
-// row loaded before any is added), warp w forms T[iy][ix] = sum_n Fyu[iy][n] G[n][ix]
-// for the grid row iy = 16 g + w (lanes strided over n, eight loads in flight, fixed
-// shuffle tree) and writes Theta_k = T at the focus of that grid point (every focus
-// sits on one).  The blocks also copy the weights to wprev, which the focal step reads
-// while it writes the new ones.
-constexpr int TCT_THREADS = 512, TCT_WARPS = TCT_THREADS / 32, TCT_CHUNK = 2048;
-constexpr int TCT_MAX_PARTS = 32;
+// parts [parts][ux][ny], parts <= TCT_MAX_PARTS): warp w of block (ix, g) takes grid row
+// iy = 16 g + w and loads its Fy_u row into registers (lane + 32 u: TCT_FV values, the
+// rows of one chunk) before it waits for the forward; the block then sums the parts of
+// column ix in fixed order into shared memory (chunks of TCT_CHUNK rows, all parts of a
+// row loaded before any is added), each warp forms T[iy][ix] = sum_n Fy_u[iy][n] G[n][ix]
+// from registers and shared memory (fixed shuffle tree) and writes Theta_k = T at the
+// focus of that grid point (every focus sits on one).  The blocks also copy the weights
+// to wprev, which the focal step reads while it writes the new ones.
+constexpr int TCT_THREADS = 512, TCT_WARPS = TCT_THREADS / 32, TCT_FV = 32;
+constexpr int TCT_CHUNK = 32 * TCT_FV;   // rows per chunk (one Fy_u value per lane and u)
+constexpr int TCT_MAX_PARTS = 16;
 __global__ void __launch_bounds__(TCT_THREADS) sep_tc_theta_kernel(
     const float2* __restrict__ gt, int parts, const float2* __restrict__ fyu,
     const int* __restrict__ gridk, int ny, int ux, int uy, int K, float2* __restrict__ theta,
@@ -391,6 +393,16 @@ __global__ void __launch_bounds__(TCT_THREADS) sep_tc_theta_kernel(
   __shared__ int skip;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ix = blockIdx.x;
   const int iy = blockIdx.y * TCT_WARPS + warp;
+  const float2* fr = fyu + (size_t)min(iy, uy - 1) * ny;
+  auto load_fv = [&](float2 (&fv)[TCT_FV], int n0) {
+#pragma unroll
+    for (int u = 0; u < TCT_FV; ++u) {
+      const int i = n0 + u * 32 + lane;
+      fv[u] = iy < uy && i < ny ? __ldg(fr + i) : make_float2(0.f, 0.f);
+    }
+  };
+  float2 fv[TCT_FV];
+  load_fv(fv, 0);   // constant over the loop: before the wait
   pdl_wait();
   if (tid == 0) skip = done != nullptr && __ldcg(done);
   __syncthreads();
@@ -401,10 +413,10 @@ __global__ void __launch_bounds__(TCT_THREADS) sep_tc_theta_kernel(
   }
   const size_t slice = (size_t)ux * ny;
   const float2* col = gt + (size_t)ix * ny;
-  const float2* fr = fyu + (size_t)min(iy, uy - 1) * ny;
   float2 acc = make_float2(0.f, 0.f);
   for (int n0 = 0; n0 < ny; n0 += TCT_CHUNK) {
     const int nn = min(TCT_CHUNK, ny - n0);
+    if (n0 > 0) load_fv(fv, n0);
     __syncthreads();  // the previous chunk is consumed
     for (int i = tid; i < nn; i += TCT_THREADS) {
       float2 v[TCT_MAX_PARTS];
@@ -421,20 +433,11 @@ __global__ void __launch_bounds__(TCT_THREADS) sep_tc_theta_kernel(
       g[i] = a;
     }
     __syncthreads();
-    if (iy < uy)
-      for (int i0 = 0; i0 < nn; i0 += 8 * 32) {
-        float2 fv[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int i = i0 + u * 32 + lane;
-          fv[u] = i < nn ? __ldg(fr + n0 + i) : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int i = i0 + u * 32 + lane;
-          if (i < nn) cmac(acc, fv[u], g[i]);
-        }
-      }
+    for (int u = 0; u < TCT_FV; ++u) {
+      const int i = u * 32 + lane;
+      if (i < nn) cmac(acc, fv[u], g[i]);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

@@ -279,7 +279,8 @@ int sep_tc_split(const ofa_plan* p, const TcOperands& t, int sms) {
   const int tiles = (p->nyp / 128) * (2 * t.kp / t.fwd_bn);
   const int kb_fwd = (2 * p->nxp * t.elem_bytes) / t.fwd_rb;
   int split = 1;
-  while (split < 32 && tiles * split * 2 <= sms && kb_fwd / (split * 2) >= 2) split *= 2;
+  while (split < SEP_TC_MAX_PARTS && tiles * split * 2 <= sms && kb_fwd / (split * 2) >= 2)
+    split *= 2;
   return split;
 }
 

@@ -311,9 +311,9 @@ void launch_sep_focal_u(const float2* theta, const float* t, const float* wprev,
                         float2* c, double* hist, OfaDevState* st, int weighting, const int2* ixy,
                         int K, const float2* fyu, const int* done, int ny, int ux, int uy,
                         int kpad, int prec, void* hi, void* lo, cudaStream_t s);
-constexpr int SEP_TC_MAX_UX = 128, SEP_TC_MAX_UY = 128, SEP_TC_MAX_PARTS = 32;
+constexpr int SEP_TC_MAX_UX = 128, SEP_TC_MAX_UY = 128, SEP_TC_MAX_PARTS = 16;
 // Separable form on the tensor cores: Theta_k = T[iy_k][ix_k] with T = Fyu G from the
-// forward's contraction parts gt [parts][ux][ny] (parts <= 32, summed in fixed order),
+// forward's contraction parts gt [parts][ux][ny] (parts <= 16, summed in fixed order),
 // into theta [K]; the blocks also copy w [K] to wprev (nullable) for the focal step.
 void launch_sep_tc_theta(const float2* gt, int parts, const float2* fyu, const int* gridk, int ny,
                          int ux, int uy, int K, float2* theta, const float* w, float* wprev,
