@@ -808,22 +808,42 @@ __global__ void __launch_bounds__(SEP_U_THREADS) sep_focal_u_kernel(
     st->c_scale = scale;
   }
   __syncthreads();
-  float2 acc[4];
+  // two accumulators per column (even and odd grid rows, added at the end): twice the
+  // independent FMA chains
+  float2 acc[4], acc2[4];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) acc[r] = make_float2(0.f, 0.f);
+  for (int r = 0; r < 4; ++r) acc[r] = acc2[r] = make_float2(0.f, 0.f);
   const int R = pitch / 32;
-  for (int iy = 0; iy < uy; ++iy) {
-    const float2 g = fy[iy][warp];
+  auto cmac_u = [](float2& a, float2 g, float2 v) {
+    a.x = fmaf(g.x, v.x, a.x);
+    a.x = fmaf(-g.y, v.y, a.x);
+    a.y = fmaf(g.x, v.y, a.y);
+    a.y = fmaf(g.y, v.x, a.y);
+  };
+  int iy = 0;
+  for (; iy + 1 < uy; iy += 2) {
+    const float2 g0 = fy[iy][warp], g1 = fy[iy + 1][warp];
     const float2* row = cg + iy * pitch + lane;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       if (r >= R) break;
-      const float2 v = row[32 * r];
-      acc[r].x = fmaf(g.x, v.x, acc[r].x);
-      acc[r].x = fmaf(-g.y, v.y, acc[r].x);
-      acc[r].y = fmaf(g.x, v.y, acc[r].y);
-      acc[r].y = fmaf(g.y, v.x, acc[r].y);
+      cmac_u(acc[r], g0, row[32 * r]);
+      cmac_u(acc2[r], g1, row[pitch + 32 * r]);
     }
+  }
+  if (iy < uy) {
+    const float2 g0 = fy[iy][warp];
+    const float2* row = cg + iy * pitch + lane;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (r >= R) break;
+      cmac_u(acc[r], g0, row[32 * r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    acc[r].x += acc2[r].x;
+    acc[r].y += acc2[r].y;
   }
   const int n = n0 + warp;
   if (n >= ny) return;
