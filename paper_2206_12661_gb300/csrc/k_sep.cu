@@ -384,6 +384,7 @@ __global__ void __launch_bounds__(SEP_THREADS) sep_sum_focal_kernel(
 constexpr int TCT_THREADS = 512, TCT_WARPS = TCT_THREADS / 32, TCT_FV = 32;
 constexpr int TCT_CHUNK = 32 * TCT_FV;   // rows per chunk (one Fy_u value per lane and u)
 constexpr int TCT_MAX_PARTS = 16;
+static_assert(TCT_MAX_PARTS >= SEP_TC_MAX_PARTS, "the forward's parts must fit the part sum");
 __global__ void __launch_bounds__(TCT_THREADS) sep_tc_theta_kernel(
     const float2* __restrict__ gt, int parts, const float2* __restrict__ fyu,
     const int* __restrict__ gridk, int ny, int ux, int uy, int K, float2* __restrict__ theta,
