@@ -197,14 +197,15 @@ def test_separable_loop_one_step(ofa, dev, name, loop):
     assert cfg["fused_loop"] == loop
 
 
-@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3", "tf32", "bf16"])
 @pytest.mark.parametrize("name", ["grid13x41_333x250", "table1_grid9x9", "table1_grid20x20",
                                   "table1_grid45x47"])
 def test_separable_tc_one_step(ofa, dev, name, prec):
     """The separable form's iteration on the tensor cores (forced), one step from the
     oracle's iterate 5: G = E Fx_u^T per contraction part, Theta and the new weights from
     it, U = conj(Fy_u)^T C and the inverse product with the phase projection, within the
-    form's tolerances; on a ragged pupil and on grids of 9 to 47 distinct coordinates."""
+    form's tolerances; on a ragged pupil and on grids of 9 to 47 distinct coordinates, in
+    every tensor-core precision (TF32: four-byte operand planes)."""
     cfg = check_plan(ofa, name, prec, j=5, separable=1, separable_tc=1)
     assert cfg["fwd_bn"] == 128 and cfg["fused_loop"] == 0, cfg
 
