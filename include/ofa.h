@@ -51,7 +51,8 @@ typedef enum ofa_status {
 } ofa_status;
 
 /* Arithmetic of the two matrix products of the loop.  Every form accumulates
- * in FP32; the DFT phase arguments are always formed and reduced in FP64. */
+ * in FP32; the DFT phase arguments are always reduced modulo one turn before the
+ * FP32 sincos (exactly, in 64-bit fixed point, for a plan's DFT rows). */
 typedef enum ofa_precision {
   OFA_PREC_FP32 = 0,    /* FP32 FMA on the CUDA cores                              */
   OFA_PREC_TF32 = 1,    /* tensor cores, TF32 operands, one product                */
