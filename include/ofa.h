@@ -229,15 +229,16 @@ ofa_status ofa_get_phase(const ofa_plan* plan, float* phi_out, int out_mem_space
 
 /* Release every resource of the plan.  NULL-safe.  The plan's device buffers live
  * in one allocation; the library keeps the last one released on each device (the
- * larger, if it already holds one), the pinned state mirror and up to eight idle
- * streams for the next plan of similar size to reuse, so a create/destroy loop
- * allocates once.  ofa_trim frees what is kept. */
+ * larger, if it already holds one), the pinned state mirror, up to eight idle streams
+ * and up to eight iteration-graph executables for the next plan of similar size to
+ * reuse, so a create/destroy loop allocates once and refreshes graph executables
+ * instead of instantiating them.  ofa_trim frees what is kept. */
 ofa_status ofa_destroy(ofa_plan* plan);
 
-/* Free the device memory, pinned host memory and streams that destroyed plans left
- * for reuse on the current device (at most one plan arena, one state mirror and
- * eight streams).  Plans still alive are not affected.  OFA_OK, or OFA_ERR_CUDA if a
- * free fails. */
+/* Free the device memory, pinned host memory, streams and graph executables that
+ * destroyed plans left for reuse on the current device (at most one plan arena, one
+ * state mirror, eight streams and eight executables).  Plans still alive are not
+ * affected.  OFA_OK, or OFA_ERR_CUDA if a free fails. */
 ofa_status ofa_trim(void);
 
 /* Statistics of one forward at the current phase (runs that forward; host output). */

@@ -10,6 +10,7 @@
 // flag that makes the rest of a launch skip); the host checks it between
 // chunks only when a threshold is set.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -61,10 +62,21 @@ cudaError_t dalloc(T** p, size_t count) {
 
 // Per-device reuse of what plan creation and destruction cost most on the host:
 // the device attributes, the kernels' shared-memory opt-in (once per precision),
-// one plan arena, one pinned state mirror and a few idle streams.  A process that
-// creates and destroys plans in a loop then calls cudaMalloc / cudaMallocHost /
-// cudaStreamCreate once; ofa_trim releases what is cached.
+// one plan arena, one pinned state mirror, a few idle streams and the iteration
+// graphs' executables of destroyed plans.  A process that creates and destroys plans
+// in a loop then calls cudaMalloc / cudaMallocHost / cudaStreamCreate once and
+// refreshes a graph executable instead of instantiating one; ofa_trim releases what
+// is cached.
 constexpr int OFA_CACHED_STREAMS = 8;
+constexpr int OFA_CACHED_EXECS = 8;
+// What fixes an iteration graph's nodes, kernels and launch attributes: only an
+// executable of the same key is refreshed for another plan (whose graph then differs
+// in kernel arguments alone).
+using ExecKey = std::array<int, 24>;
+struct CachedExec {
+  cudaGraphExec_t exec;
+  ExecKey key;
+};
 struct DeviceCache {
   bool attrs = false;
   int cc = 0, sms = 0;
@@ -74,6 +86,8 @@ struct DeviceCache {
   OfaDevState* st_host = nullptr;
   cudaStream_t streams[OFA_CACHED_STREAMS] = {};
   int n_streams = 0;
+  CachedExec execs[OFA_CACHED_EXECS] = {};
+  int n_execs = 0;
 };
 constexpr int OFA_MAX_DEVICES = 64;
 std::mutex g_cache_mu;
@@ -171,6 +185,36 @@ void give_back_stream(int dev, cudaStream_t s) {
     }
   }
   cudaStreamDestroy(s);
+}
+
+// A cached graph executable of this key (the most recently kept), or null.
+cudaGraphExec_t take_cached_exec(int dev, const ExecKey& key) {
+  if (dev < 0 || dev >= OFA_MAX_DEVICES) return nullptr;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  DeviceCache& c = g_cache[dev];
+  for (int i = c.n_execs - 1; i >= 0; --i)
+    if (c.execs[i].key == key) {
+      const cudaGraphExec_t x = c.execs[i].exec;
+      for (int j = i; j + 1 < c.n_execs; ++j) c.execs[j] = c.execs[j + 1];
+      --c.n_execs;
+      return x;
+    }
+  return nullptr;
+}
+
+// Keep the executable of a destroyed plan (its stream has been synchronised), or
+// destroy it when the cache is full.
+void give_back_exec(int dev, cudaGraphExec_t x, const ExecKey& key) {
+  if (!x) return;
+  if (dev >= 0 && dev < OFA_MAX_DEVICES) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    DeviceCache& c = g_cache[dev];
+    if (c.n_execs < OFA_CACHED_EXECS) {
+      c.execs[c.n_execs++] = {x, key};
+      return;
+    }
+  }
+  cudaGraphExecDestroy(x);
 }
 
 OfaDevState* take_cached_st_host(int dev) {
@@ -307,9 +351,18 @@ ofa_status alloc_tc(ofa_plan* p, TcOperands& t, bool with_static) {
   return ok ? OFA_OK : OFA_ERR_OOM;
 }
 
+// The key of a plan's graph of `iters` iterations: sizes, form, precision and tiles.
+ExecKey exec_key(const ofa_plan* p, int iters) {
+  const TcOperands& t = p->tc;
+  return {iters,       p->precision, p->nx,      p->ny,      p->K,        p->kp,
+          p->nxp,      p->nyp,       p->sep,     p->sep_fast, p->sep_tc,  p->ux,
+          p->uy,       p->weighting, p->sm_count, t.kp,     t.fwd_bn,    t.fwd_split,
+          t.fwd_cg,    t.bwd_bn,     t.bwd_cg,  t.fwd_rb,   t.bwd_rb,    t.npass};
+}
+
 void destroy_graphs(ofa_plan* p) {
-  if (p->chunk_exec) cudaGraphExecDestroy(p->chunk_exec);
-  if (p->one_exec) cudaGraphExecDestroy(p->one_exec);
+  give_back_exec(p->device, p->chunk_exec, exec_key(p, p->chunk_iters));
+  give_back_exec(p->device, p->one_exec, exec_key(p, 1));
   p->chunk_exec = p->one_exec = nullptr;
 }
 
@@ -441,6 +494,18 @@ ofa_status build_graph(ofa_plan* p, int iters, cudaGraphExec_t* exec) {
   for (int i = 0; i < iters; ++i) enqueue_iteration(p, p->cap_stream);
   e = cudaStreamEndCapture(p->cap_stream, &g);
   if (e != cudaSuccess) return ofa_cuda_check(p, e, "cudaStreamEndCapture");
+  // an executable that a destroyed plan of the same key left takes this graph's kernel
+  // arguments (the update also checks that nodes and kernels match); else instantiate
+  if (cudaGraphExec_t cached = take_cached_exec(p->device, exec_key(p, iters))) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(cached, g, &info) == cudaSuccess) {
+      cudaGraphDestroy(g);
+      *exec = cached;
+      return OFA_OK;
+    }
+    cudaGetLastError();   // the refused update leaves no error behind
+    cudaGraphExecDestroy(cached);
+  }
   e = cudaGraphInstantiate(exec, g, 0);
   cudaGraphDestroy(g);
   return ofa_cuda_check(p, e, "cudaGraphInstantiate");
@@ -1795,6 +1860,8 @@ ofa_status ofa_trim(void) {
   OfaDevState* h = nullptr;
   cudaStream_t streams[OFA_CACHED_STREAMS];
   int n_streams = 0;
+  CachedExec execs[OFA_CACHED_EXECS];
+  int n_execs = 0;
   if (dev >= 0 && dev < OFA_MAX_DEVICES) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     DeviceCache& c = g_cache[dev];
@@ -1806,6 +1873,9 @@ ofa_status ofa_trim(void) {
     n_streams = c.n_streams;
     for (int i = 0; i < n_streams; ++i) streams[i] = c.streams[i];
     c.n_streams = 0;
+    n_execs = c.n_execs;
+    for (int i = 0; i < n_execs; ++i) execs[i] = c.execs[i];
+    c.n_execs = 0;
   }
   if (arena) e = cudaFree(arena);
   if (h) {
@@ -1814,6 +1884,10 @@ ofa_status ofa_trim(void) {
   }
   for (int i = 0; i < n_streams; ++i) {
     const cudaError_t e2 = cudaStreamDestroy(streams[i]);
+    if (e == cudaSuccess) e = e2;
+  }
+  for (int i = 0; i < n_execs; ++i) {
+    const cudaError_t e2 = cudaGraphExecDestroy(execs[i].exec);
     if (e == cudaSuccess) e = e2;
   }
   if (e != cudaSuccess) return ofa_cuda_check(nullptr, e, "releasing cached memory");
