@@ -397,6 +397,29 @@ def test_resume_is_bitwise(ofa, dev, prec):
     assert np.array_equal(phi_a, phi_b)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_graph_executable_reuse_is_bitwise(ofa, dev, prec):
+    """Plans of one configuration refresh the iteration-graph executables that a
+    destroyed plan left (cudaGraphExecUpdate) instead of instantiating them: the run
+    must be bit for bit the one from freshly instantiated executables (the cache is
+    emptied first), also after two refreshes through a plan of other foci."""
+    w_a = custom(256, 256, 100, seed=5, targets="random")
+    w_b = custom(256, 256, 100, seed=6)
+    ofa.ofa_trim()
+    a = ofa.Plan.from_workload(w_a, precision=prec, separable=0)
+    a.iterate(20)
+    phi_fresh = a.phase()
+    a.close()
+    b = ofa.Plan.from_workload(w_b, precision=prec, separable=0)
+    b.iterate(5)
+    b.close()
+    c = ofa.Plan.from_workload(w_a, precision=prec, separable=0)
+    c.iterate(20)
+    phi_reuse = c.phase()
+    c.close()
+    assert np.array_equal(phi_fresh, phi_reuse)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "f16x3", "bf16"])
 def test_deterministic(ofa, dev, prec):
     w = I.named("pupil256_grid100_uniform")
