@@ -16,9 +16,9 @@
 #include <cstring>
 #include <mutex>
 #include <string>
-#include <unordered_set>
 #include <vector>
 
+#include "ofa_host.h"
 #include "ofa_internal.cuh"
 
 namespace {
@@ -849,19 +849,10 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
     const double bound = (c_gen / gain - (double)n_foci * (nx + ny)) / npix_d;
     const size_t limit = opt.separable == 1 ? (size_t)n_foci
                          : bound < 1.0 ? 0 : (size_t)std::min(bound, (double)n_foci);
-    auto distinct = [&](int c, size_t lim, std::vector<double>& out) {
-      std::unordered_set<double> seen;  // -0.0 == 0.0: one value
-      seen.reserve(std::min((size_t)n_foci, lim + 1));
-      for (int k = 0; k < n_foci; ++k) {
-        seen.insert(xy[2 * (size_t)k + c]);
-        if (seen.size() > lim) return false;
-      }
-      out.assign(seen.begin(), seen.end());
-      std::sort(out.begin(), out.end());
-      return true;
-    };
-    bool fits = distinct(0, limit, xs);
-    if (fits) fits = distinct(1, opt.separable == 1 ? limit : limit - xs.size(), ys);
+    bool fits = ofa_host::distinct_coords(xy.data(), n_foci, 0, limit, xs);
+    if (fits)
+      fits = ofa_host::distinct_coords(xy.data(), n_foci, 1,
+                                       opt.separable == 1 ? limit : limit - xs.size(), ys);
     if (fits && opt.separable != 1) {
       const double c_sep = npix_d * ((double)xs.size() + (double)ys.size()) +
                            (double)n_foci * (nx + ny);
@@ -884,12 +875,7 @@ ofa_status ofa_plan_create(ofa_plan** out, int nx, int ny, double pitch_x, doubl
   if (p->sep && opt.separable_tc != 0) {
     bool ok = prec_is_tc(opt.precision) && p->ux <= SEP_TC_MAX_UX && p->uy <= SEP_TC_MAX_UY &&
               sep_focal_u_fits(p->ux, p->uy, n_foci);
-    if (ok) {
-      std::vector<std::pair<double, double>> pts(n_foci);
-      for (int k = 0; k < n_foci; ++k) pts[k] = {xy[2 * (size_t)k], xy[2 * (size_t)k + 1]};
-      std::sort(pts.begin(), pts.end());
-      ok = std::adjacent_find(pts.begin(), pts.end()) == pts.end();
-    }
+    if (ok) ok = ofa_host::one_focus_per_point(xy.data(), n_foci);
     if (!ok && opt.separable_tc == 1) {
       delete p;
       return ofa_fail(nullptr, OFA_ERR_UNSUPPORTED,
