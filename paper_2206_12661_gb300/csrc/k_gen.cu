@@ -212,30 +212,32 @@ __global__ void transpose_fy_kernel(const float2* __restrict__ fy, int K, int ny
   }
 }
 
-// Real block form of the complex factor, one output element per thread.
+// Real block form of the complex factor.  Thread (a, b) reads one complex entry and
+// writes the 2 x 2 real block it becomes, as two pairs of adjacent elements:
 //  forward (inverse == 0): B[2k+h][2m+g], rows give Re/Im of G = E Fx^T:
 //     h=0: ( Fr, -Fi )   h=1: ( Fi,  Fr )
 //  inverse (inverse == 1): Q[2m+h][2k+g], rows give Re/Im of E' = P conj(Fx):
 //     h=0: ( Fr,  Fi )   h=1: (-Fi,  Fr )
+// a runs along the rows of the block form (m for the forward, k for the inverse), b over
+// its row pairs; entries beyond K foci or nx samples give zeros.
 __global__ void pack_fx_kernel(const float2* __restrict__ fx, int K, int nx, int kp, int nxp,
                                int inverse, int prec, void* hi, void* lo) {
-  size_t rows = inverse ? 2 * (size_t)nxp : 2 * (size_t)kp;
-  size_t cols = inverse ? 2 * (size_t)kp : 2 * (size_t)nxp;
-  size_t total = rows * cols;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    size_t r = i / cols, cidx = i % cols;
-    int h = (int)(r & 1), g = (int)(cidx & 1);
-    int k = inverse ? (int)(cidx >> 1) : (int)(r >> 1);
-    int m = inverse ? (int)(r >> 1) : (int)(cidx >> 1);
-    float v = 0.f;
-    if (k < K && m < nx) {
-      float2 f = fx[(size_t)k * nx + m];
-      if (!inverse) v = h == 0 ? (g == 0 ? f.x : -f.y) : (g == 0 ? f.y : f.x);
-      else          v = h == 0 ? (g == 0 ? f.x : f.y) : (g == 0 ? -f.y : f.x);
+  const int A = inverse ? kp : nxp;   // complex columns of a row pair
+  const int B = inverse ? nxp : kp;   // row pairs
+  const size_t cols = 2 * (size_t)A;
+  for (int b = blockIdx.y; b < B; b += gridDim.y)
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < A; a += gridDim.x * blockDim.x) {
+      const int k = inverse ? a : b, m = inverse ? b : a;
+      const float2 f = k < K && m < nx ? fx[(size_t)k * nx + m] : make_float2(0.f, 0.f);
+      const size_t e = 2 * (size_t)b * cols + 2 * (size_t)a;   // element (2b, 2a)
+      if (!inverse) {
+        split_store2(prec, hi, lo, e, f.x, -f.y);
+        split_store2(prec, hi, lo, e + cols, f.y, f.x);
+      } else {
+        split_store2(prec, hi, lo, e, f.x, f.y);
+        split_store2(prec, hi, lo, e + cols, -f.y, f.x);
+      }
     }
-    split_store(prec, hi, lo, i, v);
-  }
 }
 
 // E = A exp(i phi) as interleaved operand planes [nyp][2 nxp] (padding untouched).
@@ -300,8 +302,9 @@ void launch_transpose_fy(const float2* fy, int K, int ny, int kp, int nyp, float
 
 void launch_pack_fx(const float2* fx, int K, int nx, int kp, int nxp, int inverse, int prec,
                     void* hi, void* lo, cudaStream_t s) {
-  size_t total = 4 * (size_t)kp * nxp;
-  pack_fx_kernel<<<grid_for(total), 256, 0, s>>>(fx, K, nx, kp, nxp, inverse, prec, hi, lo);
+  const int A = inverse ? kp : nxp, B = inverse ? nxp : kp;
+  const dim3 grid((unsigned)((A + 255) / 256), (unsigned)(B < 65535 ? B : 65535));
+  pack_fx_kernel<<<grid, 256, 0, s>>>(fx, K, nx, kp, nxp, inverse, prec, hi, lo);
 }
 
 void launch_field_planes(const float* phi, const float* amp, int nx, int ny, int nxp, int prec,
